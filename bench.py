@@ -1,0 +1,397 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the stereo surface-normal chain on GB300.
+
+Workload: 2048x1024 driving-like scenes (ground plane, two facades, 20 boxes;
+f = 2260 px, B = 0.21 m, sigma = 0.3 px, 8 % invalid), FP32 disparity, the
+plain chain: range-gated 5x5 denoise, star-fill covered-depth support
+(8 directions x 10 steps, k = 0.1), two-pass affine fit and normal, point
+cloud, 4-connected min-index components.  One step = sn_run_frame over a
+batch of frames already resident in HBM.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead, on the host cores, on the same workload (a band of rows per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "driving_2048x1024"
+METRIC = "MPix/s (2048x1024 stereo normals chain)"
+# algorithmic bytes per pixel of each launch of sn_run_frame (compulsory
+# reads and writes of that kernel)
+ALGO_BYTES = {
+    "denoise": 4 + 4 + 1,                 # disp in; den, mask out
+    "affine_normals": 4 + 4 + 1 + 12 + 1,  # disp, den, mask in; normals, mask out
+    "pointcloud": 4 + 1 + 12,             # den, mask in; points out
+    "ccl_local": 4 + 4,                   # disp in; labels out
+    "ccl_merge": 0,                       # tile borders only
+    "ccl_flatten": 4 + 4,                 # labels in and out
+}
+FRAME_ALGO_BYTES = 33                      # disp 4 + normals 12 + points 12 + labels 4 + mask 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames", type=int, default=16, help="frames per step")
+    ap.add_argument("--distinct", type=int, default=8, help="distinct input frames")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id_for(device_index: int) -> str:
+    import torch
+    try:
+        props = torch.cuda.get_device_properties(device_index)
+        uuid = str(getattr(props, "uuid", "") or "")
+        if uuid:
+            return uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip()]
+    return ids[device_index] if device_index < len(ids) else str(device_index)
+
+
+# ---------------------------------------------------------------- helpers
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def make_inputs(n_distinct: int, rank: int):
+    from scenes import make_scene
+    return [make_scene(WORKLOAD, frame=rank * n_distinct + i) for i in range(n_distinct)]
+
+
+def cpu_baseline(scenes, seconds: float):
+    """The FP64 oracle as it stands, all host cores, on whole frames of the
+    same workload until `seconds` of CPU work have been spent."""
+    import oracle
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    oracle.build()
+    px, n = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        s = scenes[n % len(scenes)]
+        oracle.run_frame(s.disp, s.camera)
+        px += s.W * s.H
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": px / dt / 1e6, "unit": "MPix/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle",
+            "sample": f"{n} whole {WORKLOAD} frames (FP32 input, full chain), {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from scenes import make_scene
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    oracle.build()
+    s = make_scene(WORKLOAD, frame=0)
+    band = 128
+    H = s.H
+    bands = [s.disp[y:y + band] for y in range(0, H, band)]
+
+    def step(i):
+        b = bands[i % len(bands)]
+        oracle.run_frame(b, s.camera)
+        return b.shape[0] * b.shape[1]
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    px = sum(step(i) for i in range(args.steps))
+    dt = time.perf_counter() - t0
+    v = px / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "MPix/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: FP64 CPU oracle, one 2048x{band} band of the frame per step"},
+        "cpu_baseline": {"value": v, "unit": "MPix/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
+                         "kind": "oracle", "sample": f"{args.steps} bands of {band} rows"},
+        "e2e": {"value": v, "unit": "MPix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2504_15121_gb300 import Pipeline, sn
+
+    scenes = make_inputs(args.distinct, rank)
+    s0 = scenes[0]
+    W, H, cam = s0.W, s0.H, s0.camera
+    pipe = Pipeline(cam, W, H)
+    disp = [pipe.upload(s.disp) for s in scenes]
+    F = args.frames
+    outs = [pipe.buffers() for _ in range(F)]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for f in range(F):
+            pipe.run_frame(disp[f % len(disp)], outs[f], stream=stream, write_den=False)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sn.sn_check_device(pipe.ctx)
+
+    # ---- timed region (device time, CUDA events on the launching stream)
+    sn.sn_set_profiling(pipe.ctx, True)
+    sn.sn_stage_times(pipe.ctx)
+    launches0 = sn.sn_launch_count(pipe.ctx)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_id_for(dev)) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        t_start.record(stream)
+        for _ in range(args.steps):
+            step()
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = sn.sn_launch_count(pipe.ctx) - launches0
+    elapsed_ms = t_start.elapsed_time(t_end)
+    stage_ms, nframes, frame_ms = sn.sn_stage_times(pipe.ctx, cap=args.steps * F)
+    sn.sn_set_profiling(pipe.ctx, False)
+    sn.sn_check_device(pipe.ctx)
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    px_total = world * args.steps * F * W * H
+    value = px_total / (elapsed_ms / 1e3) / 1e6
+
+    # ---- roofline of the dominant kernel (live event times of the timed region)
+    peaks, peak_kind = load_peaks()
+    avg = {k: v / max(nframes, 1) for k, v in stage_ms.items()}
+    dom = max(avg, key=avg.get)
+    achieved = ALGO_BYTES[dom] * W * H / (avg[dom] / 1e3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    traffic = load_traffic(dom)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(pipe, scenes, args, world, dist)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(scenes, args.cpu_seconds)
+
+    if rank == 0:
+        fm = sorted(frame_ms)
+        pct = lambda q: fm[min(len(fm) - 1, int(round(q * (len(fm) - 1))))] if fm else None
+        line = {
+            "metric": METRIC, "value": value, "unit": "MPix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {
+                "workload": f"{WORKLOAD}: plain chain, FP32 disparity in, FP32 normals/points out, "
+                            f"star-fill CD s10 d8 k0.1, 5x5 denoise; {F} frames per step "
+                            f"({args.distinct} distinct seeded scenes)",
+                "frames_per_step": F, "W": W, "H": H,
+                "l2": "inputs+outputs per step "
+                      f"{F * W * H * (4 + FRAME_ALGO_BYTES - 4) / 1e9:.2f} GB >> 129 MB L2 (no flush needed)",
+                "parallelism": f"replicas x{world}",
+            },
+            "frame_ms": {"p50": pct(0.5), "p99": pct(0.99), "max": fm[-1] if fm else None,
+                         "source": "CUDA events around each sn_run_frame in the timed region"},
+            "stage_ms_per_frame": {k: round(v, 5) for k, v in avg.items()},
+            "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind,
+                         "algo_bytes_per_px": ALGO_BYTES[dom],
+                         "frame_frac": FRAME_ALGO_BYTES * W * H / (elapsed_ms / 1e3 / (args.steps * F)) / 1e9 / peak},
+            "gpu_launches": int(launches),
+            "clocks": clocks.summary(),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    pipe.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def load_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it covers the
+    current build of this kernel (profiles/traffic.json)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        return t.get(kernel)
+    except Exception:
+        return None
+
+
+def run_e2e(pipe, scenes, args, world, dist):
+    import torch
+    from paper_2504_15121_gb300 import sn
+    W, H = pipe.W, pipe.H
+    F = args.frames
+    host_in = []
+    for s in scenes:
+        t = torch.from_numpy(s.disp).pin_memory()
+        host_in.append(t)
+    outs = [pipe.buffers() for _ in range(2)]
+    dins = [sn.empty_image(H, W, torch.float32) for _ in range(2)]
+    host_out = [dict(normals=torch.empty((3, H, W), dtype=torch.float32).pin_memory(),
+                     points=torch.empty((3, H, W), dtype=torch.float32).pin_memory(),
+                     labels=torch.empty((H, W), dtype=torch.int32).pin_memory(),
+                     mask=torch.empty((H, W), dtype=torch.uint8).pin_memory()) for _ in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    h2d = W * H * 4
+    d2h = W * H * (12 + 12 + 4 + 1)
+
+    def frame(f):
+        i = f % 2
+        st = streams[i]
+        with torch.cuda.stream(st):
+            dins[i].copy_(host_in[f % len(host_in)], non_blocking=True)
+            pipe.run_frame(dins[i], outs[i], stream=st)
+            o, ho = outs[i], host_out[i]
+            ho["normals"].copy_(o.normals, non_blocking=True)
+            ho["points"].copy_(o.points, non_blocking=True)
+            ho["labels"].copy_(o.labels, non_blocking=True)
+            ho["mask"].copy_(o.mask, non_blocking=True)
+
+    steps = max(3, args.steps // 4)
+    for f in range(2 * F):
+        frame(f)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for f in range(F):
+            frame(f)
+        torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([dt], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    px = world * steps * F * W * H
+    return {"value": px / dt / 1e6, "unit": "MPix/s", "h2d_bytes_per_step": F * h2d,
+            "d2h_bytes_per_step": F * d2h, "steps": steps,
+            "how": "pinned host disparity -> device, sn_run_frame, normals/points/labels/mask -> "
+                   "pinned host; 2 streams alternating frames; host wall clock with a device sync "
+                   "per step"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

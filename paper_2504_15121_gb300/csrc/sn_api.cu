@@ -1,0 +1,409 @@
+// C ABI of the surface-normal library: argument checks, context and
+// workspace management, and the stage entry points declared in sn.h.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "sn_internal.h"
+
+namespace {
+constexpr int kStages = 6;         // kernel launches of one sn_run_frame
+constexpr int kProfFrames = 4096;  // frames recorded between two sn_stage_times calls
+const char* const kStageNames[kStages] = {"denoise", "affine_normals", "pointcloud",
+                                          "ccl_local", "ccl_merge", "ccl_flatten"};
+}  // namespace
+
+struct sn_ctx {
+    sn_camera cam;
+    int W, H;
+    sn_params p;
+    int device;
+    sn::Geo geo;
+    sn::StarTable star;
+    sn::Workspace ws;
+    unsigned long long launches;
+    bool prof;
+    cudaEvent_t* ev;  // kProfFrames x (kStages + 1)
+    int prof_frames;
+    char msg[512];
+};
+
+namespace {
+
+int kfix(float k) { return (int)nearbyint((double)k * 65536.0); }
+
+sn_status fail(sn_ctx* c, sn_status st, const char* what) {
+    if (c) snprintf(c->msg, sizeof(c->msg), "%s", what);
+    return st;
+}
+
+sn_status cuda_fail(sn_ctx* c, cudaError_t e, const char* where) {
+    if (c) snprintf(c->msg, sizeof(c->msg), "%s: %s", where, cudaGetErrorString(e));
+    return SN_ECUDA;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+sn_status check_buf(sn_ctx* c, const void* p, size_t pitch, size_t elem, const char* name) {
+    if (!p) return fail(c, SN_EINVAL, name);
+    if (!aligned16(p) || (pitch & 15u) != 0 || pitch < (size_t)c->W * elem) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "%s: pointer must be 16-byte aligned, pitch a multiple of 16 and >= %zu bytes",
+                 name, (size_t)c->W * elem);
+        return fail(c, SN_EINVAL, buf);
+    }
+    return SN_OK;
+}
+
+size_t in_elem(int dtype) { return dtype == SN_IN_F32 ? 4 : 2; }
+size_t nrm_elem(int fmt) { return fmt == SN_NORMALS_F32X3 ? 4 : 8; }
+
+// Star-fill offsets: direction j at angle 2 pi j / M, step k at
+// (round(k cos), round(k sin)) with halves away from zero (C round()).
+void star_offsets(int M, int s, int8_t* ou, int8_t* ov) {
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int j = 0; j < M; j++) {
+        const double th = two_pi * (double)j / (double)M;
+        const double c = cos(th), sn_ = sin(th);
+        for (int k = 1; k <= s; k++) {
+            ou[j * s + k - 1] = (int8_t)round(k * c);
+            ov[j * s + k - 1] = (int8_t)round(k * sn_);
+        }
+    }
+}
+
+// Classifies every table entry for the kernels (see sn::StarTable).
+bool build_star(int M, int s, sn::StarTable& T) {
+    memset(&T, 0, sizeof(T));
+    T.n = M * s;
+    star_offsets(M, s, T.ou, T.ov);
+    for (int e = 0; e < T.n; e++) {
+        const int j = e / s, k = e % s;
+        if (k > 0 && T.ou[e] == T.ou[e - 1] && T.ov[e] == T.ov[e - 1]) {
+            T.cls[e] = 0;
+            continue;
+        }
+        // rays (other than j) that reach the same offset
+        bool shared = false;
+        for (int f = 0; f < T.n; f++)
+            if (f / s != j && T.ou[f] == T.ou[e] && T.ov[f] == T.ov[e]) shared = true;
+        if (!shared) {
+            T.cls[e] = 1;
+            continue;
+        }
+        int b = -1;
+        for (int q = 0; q < T.nshared; q++)
+            if (T.sou[q] == T.ou[e] && T.sov[q] == T.ov[e]) b = q;
+        if (b < 0) {
+            if (T.nshared >= sn::kMaxShared) return false;
+            b = T.nshared++;
+            T.sou[b] = T.ou[e];
+            T.sov[b] = T.ov[e];
+        }
+        T.cls[e] = 2;
+        T.bit[e] = (uint8_t)b;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sn_version(void) { return (0 << 16) | 3; }
+
+void sn_default_params(sn_params* p) {
+    if (!p) return;
+    p->r_denoise = 2;
+    p->r_affine = 4;
+    p->support = SN_SUPPORT_STARFILL_CD;
+    p->dirs = 8;
+    p->steps = 10;
+    p->k_cd = 0.1f;
+    p->k_pair = 0.05f;
+    p->k_range = 0.05f;
+    p->tau = 0.9f;
+    p->in_dtype = SN_IN_F32;
+    p->normal_fmt = SN_NORMALS_F32X3;
+    p->learned = 0;
+}
+
+const char* sn_status_string(sn_status s) {
+    switch (s) {
+        case SN_OK: return "ok";
+        case SN_EINVAL: return "invalid argument";
+        case SN_ENOMEM: return "out of device memory";
+        case SN_ECUDA: return "CUDA error";
+        case SN_ETIMEOUT: return "bounded device wait gave up";
+        case SN_EBUSY: return "busy (admission refused)";
+        case SN_ENOTSUP: return "not supported";
+    }
+    return "unknown status";
+}
+
+const char* sn_last_error(const sn_ctx* c) { return c ? c->msg : "null context"; }
+
+int sn_star_offsets(int dirs, int steps, int8_t* ou, int8_t* ov) {
+    if (dirs < 1 || dirs > sn::kMaxDirs || steps < 1 || steps > sn::kMaxSteps || !ou || !ov) return -1;
+    star_offsets(dirs, steps, ou, ov);
+    return dirs * steps;
+}
+
+sn_status sn_create(const sn_camera* cam, int W, int H, const sn_params* pin, sn_ctx** out) {
+    if (!out) return SN_EINVAL;
+    *out = nullptr;
+    if (!cam || W < 1 || H < 1 || W > 16384 || H > 16384) return SN_EINVAL;
+    if (!(cam->fx > 0) || !(cam->fy > 0) || !(cam->baseline > 0) || !isfinite(cam->cx) || !isfinite(cam->cy) ||
+        !isfinite(cam->fx) || !isfinite(cam->fy) || !isfinite(cam->baseline))
+        return SN_EINVAL;
+    sn_params p;
+    if (pin)
+        p = *pin;
+    else
+        sn_default_params(&p);
+    if (p.r_denoise < 1 || p.r_denoise > 4 || p.r_affine < 1 || p.r_affine > 15) return SN_EINVAL;
+    if (p.support != SN_SUPPORT_FIXED && p.support != SN_SUPPORT_STARFILL_CD) return SN_EINVAL;
+    if (p.dirs < 4 || p.dirs > sn::kMaxDirs || p.steps < 1 || p.steps > sn::kMaxSteps) return SN_EINVAL;
+    if (!(p.k_cd >= 0 && p.k_cd <= 1) || !(p.k_pair >= 0 && p.k_pair <= 1) || !(p.k_range >= 0 && p.k_range <= 1) ||
+        !(p.tau >= 0 && p.tau <= 1))
+        return SN_EINVAL;
+    if (p.in_dtype < SN_IN_F32 || p.in_dtype > SN_IN_U16X256) return SN_EINVAL;
+    if (p.normal_fmt != SN_NORMALS_F32X3 && p.normal_fmt != SN_NORMALS_SNORM16X4) return SN_EINVAL;
+    if (p.learned) return SN_ENOTSUP;
+
+    sn_ctx* c = new (std::nothrow) sn_ctx();
+    if (!c) return SN_ENOMEM;
+    c->cam = *cam;
+    c->W = W;
+    c->H = H;
+    c->p = p;
+    cudaGetDevice(&c->device);
+    if (!build_star(p.dirs, p.steps, c->star)) {
+        delete c;
+        return SN_ENOTSUP;
+    }
+    sn::Geo& g = c->geo;
+    g.W = W;
+    g.H = H;
+    g.in_dtype = p.in_dtype;
+    g.r_d = p.r_denoise;
+    g.r_a = p.r_affine;
+    g.support = p.support;
+    g.dirs = p.dirs;
+    g.steps = p.steps;
+    g.K_cd = kfix(p.k_cd);
+    g.K_pair = kfix(p.k_pair);
+    g.K_range = kfix(p.k_range);
+    g.normal_fmt = p.normal_fmt;
+    g.fx = (float)cam->fx;
+    g.fy = (float)cam->fy;
+    g.cx = (float)cam->cx;
+    g.cy = (float)cam->cy;
+    g.B = (float)cam->baseline;
+    g.fy_over_fx = (float)(cam->fy / cam->fx);
+    g.inv_fx = (float)(1.0 / cam->fx);
+    g.B_fx_over_fy = (float)(cam->baseline * cam->fx / cam->fy);
+    g.fxB = (float)(cam->fx * cam->baseline);
+    g.dfx = cam->fx;
+    g.dfy = cam->fy;
+    g.dcx = cam->cx;
+    g.dcy = cam->cy;
+    g.dB = cam->baseline;
+
+    cudaError_t e = cudaMalloc(&c->ws.err, 2 * sizeof(int));
+    if (e == cudaSuccess) {
+        c->ws.count = c->ws.err + 1;
+        e = cudaMemset(c->ws.err, 0, 2 * sizeof(int));
+    }
+    if (e == cudaSuccess) {
+        c->ws.den_pitch = ((size_t)W * 4 + 15) & ~(size_t)15;
+        e = cudaMalloc(&c->ws.den, c->ws.den_pitch * H);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        sn_destroy(c);
+        return SN_ENOMEM;
+    }
+    g.err = c->ws.err;
+    snprintf(c->msg, sizeof(c->msg), "ok");
+    *out = c;
+    return SN_OK;
+}
+
+sn_status sn_destroy(sn_ctx* c) {
+    if (!c) return SN_OK;
+    if (c->ev) {
+        for (int i = 0; i < kProfFrames * (kStages + 1); i++) cudaEventDestroy(c->ev[i]);
+        delete[] c->ev;
+    }
+    if (c->ws.err) cudaFree(c->ws.err);
+    if (c->ws.den) cudaFree(c->ws.den);
+    delete c;
+    return SN_OK;
+}
+
+sn_status sn_denoise(sn_ctx* c, const void* disp, size_t dpitch, float* den, size_t denp, uint8_t* mask,
+                     size_t mp, sn_stream stream) {
+    if (!c) return SN_EINVAL;
+    sn_status st;
+    if ((st = check_buf(c, disp, dpitch, in_elem(c->p.in_dtype), "disp")) != SN_OK) return st;
+    if ((st = check_buf(c, den, denp, 4, "den")) != SN_OK) return st;
+    if ((st = check_buf(c, mask, mp, 1, "mask")) != SN_OK) return st;
+    sn::Marks mk;
+    cudaError_t e = sn::launch_denoise(c->geo, disp, dpitch, den, denp, mask, mp, stream, mk);
+    c->launches += mk.launches;
+    return e == cudaSuccess ? SN_OK : cuda_fail(c, e, "sn_denoise");
+}
+
+sn_status sn_affine_normals(sn_ctx* c, const void* disp, size_t dpitch, const float* den, size_t denp,
+                            void* nrm, size_t np, uint8_t* mask, size_t mp, sn_stream stream) {
+    if (!c) return SN_EINVAL;
+    sn_status st;
+    if ((st = check_buf(c, disp, dpitch, in_elem(c->p.in_dtype), "disp")) != SN_OK) return st;
+    if ((st = check_buf(c, den, denp, 4, "den")) != SN_OK) return st;
+    if ((st = check_buf(c, nrm, np, nrm_elem(c->p.normal_fmt), "normals")) != SN_OK) return st;
+    if ((st = check_buf(c, mask, mp, 1, "mask")) != SN_OK) return st;
+    sn::Marks mk;
+    cudaError_t e = sn::launch_affine(c->geo, c->star, disp, dpitch, den, denp, nrm, np, mask, mp, false, stream, mk);
+    c->launches += mk.launches;
+    return e == cudaSuccess ? SN_OK : cuda_fail(c, e, "sn_affine_normals");
+}
+
+sn_status sn_components(sn_ctx* c, const void* disp, size_t dpitch, int32_t* labels, size_t lp, int32_t* ncomp,
+                        sn_stream stream) {
+    if (!c) return SN_EINVAL;
+    sn_status st;
+    if ((st = check_buf(c, disp, dpitch, in_elem(c->p.in_dtype), "disp")) != SN_OK) return st;
+    if ((st = check_buf(c, labels, lp, 4, "labels")) != SN_OK) return st;
+    if (ncomp && ((uintptr_t)ncomp & 3u)) return fail(c, SN_EINVAL, "num_components: misaligned");
+    sn::Marks mk;
+    cudaError_t e = sn::launch_components(c->geo, disp, dpitch, labels, lp, ncomp, stream, mk);
+    c->launches += mk.launches;
+    return e == cudaSuccess ? SN_OK : cuda_fail(c, e, "sn_components");
+}
+
+sn_status sn_pointcloud(sn_ctx* c, const float* den, size_t denp, const uint8_t* mask, size_t mp, float* pts,
+                        size_t pp, sn_stream stream) {
+    if (!c) return SN_EINVAL;
+    sn_status st;
+    if ((st = check_buf(c, den, denp, 4, "den")) != SN_OK) return st;
+    if ((st = check_buf(c, mask, mp, 1, "mask")) != SN_OK) return st;
+    if ((st = check_buf(c, pts, pp, 4, "points")) != SN_OK) return st;
+    sn::Marks mk;
+    cudaError_t e = sn::launch_points(c->geo, den, denp, mask, mp, pts, pp, stream, mk);
+    c->launches += mk.launches;
+    return e == cudaSuccess ? SN_OK : cuda_fail(c, e, "sn_pointcloud");
+}
+
+sn_status sn_run_frame(sn_ctx* c, const sn_frame_in* in, sn_frame_out* out, sn_stream stream) {
+    if (!c || !in || !out) return SN_EINVAL;
+    sn_status st;
+    if ((st = check_buf(c, in->disp, in->disp_pitch, in_elem(c->p.in_dtype), "disp")) != SN_OK) return st;
+    float* den = out->den;
+    size_t denp = out->den_pitch;
+    if (den) {
+        if ((st = check_buf(c, den, denp, 4, "den")) != SN_OK) return st;
+    } else {
+        den = c->ws.den;
+        denp = c->ws.den_pitch;
+    }
+    if ((st = check_buf(c, out->normals, out->normals_pitch, nrm_elem(c->p.normal_fmt), "normals")) != SN_OK) return st;
+    if ((st = check_buf(c, out->points, out->points_pitch, 4, "points")) != SN_OK) return st;
+    if ((st = check_buf(c, out->labels, out->labels_pitch, 4, "labels")) != SN_OK) return st;
+    if ((st = check_buf(c, out->mask, out->mask_pitch, 1, "mask")) != SN_OK) return st;
+    if (out->num_components && ((uintptr_t)out->num_components & 3u))
+        return fail(c, SN_EINVAL, "num_components: misaligned");
+    sn::Marks mk;
+    if (c->prof && c->prof_frames < kProfFrames) {
+        mk.ev = c->ev + (size_t)c->prof_frames * (kStages + 1);
+        cudaEventRecord(mk.ev[0], stream);
+        mk.n = 1;
+        c->prof_frames++;
+    }
+    cudaError_t e = sn::launch_denoise(c->geo, in->disp, in->disp_pitch, den, denp, out->mask, out->mask_pitch, stream, mk);
+    if (e == cudaSuccess)
+        e = sn::launch_affine(c->geo, c->star, in->disp, in->disp_pitch, den, denp, out->normals, out->normals_pitch,
+                              out->mask, out->mask_pitch, true, stream, mk);
+    if (e == cudaSuccess)
+        e = sn::launch_points(c->geo, den, denp, out->mask, out->mask_pitch, out->points, out->points_pitch, stream, mk);
+    if (e == cudaSuccess)
+        e = sn::launch_components(c->geo, in->disp, in->disp_pitch, out->labels, out->labels_pitch,
+                                  out->num_components, stream, mk);
+    c->launches += mk.launches;
+    return e == cudaSuccess ? SN_OK : cuda_fail(c, e, "sn_run_frame");
+}
+
+sn_status sn_load_gate_weights(sn_ctx* c, const void* blob, size_t bytes) {
+    (void)blob;
+    (void)bytes;
+    return fail(c, SN_ENOTSUP, "learned gate not enabled in this context");
+}
+
+sn_status sn_set_profiling(sn_ctx* c, int on) {
+    if (!c) return SN_EINVAL;
+    if (on && !c->ev) {
+        const int n = kProfFrames * (kStages + 1);
+        c->ev = new (std::nothrow) cudaEvent_t[n]();
+        if (!c->ev) return fail(c, SN_ENOMEM, "profiling events");
+        for (int i = 0; i < n; i++) {
+            cudaError_t e = cudaEventCreate(&c->ev[i]);
+            if (e != cudaSuccess) return cuda_fail(c, e, "sn_set_profiling");
+        }
+    }
+    c->prof = on != 0;
+    c->prof_frames = 0;
+    return SN_OK;
+}
+
+int sn_stage_count(const sn_ctx* c) { return c ? kStages : 0; }
+
+const char* sn_stage_name(const sn_ctx* c, int i) {
+    return (c && i >= 0 && i < kStages) ? kStageNames[i] : nullptr;
+}
+
+sn_status sn_stage_times(sn_ctx* c, double* ms, int n, int* frames, double* frame_ms, int cap) {
+    if (!c || !ms || n < kStages) return SN_EINVAL;
+    for (int i = 0; i < kStages; i++) ms[i] = 0.0;
+    const int nf = c->prof_frames;
+    for (int f = 0; f < nf; f++) {
+        cudaEvent_t* e = c->ev + (size_t)f * (kStages + 1);
+        cudaError_t err = cudaEventSynchronize(e[kStages]);
+        if (err != cudaSuccess) return cuda_fail(c, err, "sn_stage_times");
+        for (int i = 0; i < kStages; i++) {
+            float t = 0.0f;
+            err = cudaEventElapsedTime(&t, e[i], e[i + 1]);
+            if (err != cudaSuccess) return cuda_fail(c, err, "sn_stage_times");
+            ms[i] += t;
+        }
+        if (frame_ms && f < cap) {
+            float t = 0.0f;
+            err = cudaEventElapsedTime(&t, e[0], e[kStages]);
+            if (err != cudaSuccess) return cuda_fail(c, err, "sn_stage_times");
+            frame_ms[f] = t;
+        }
+    }
+    if (frames) *frames = nf;
+    c->prof_frames = 0;
+    return SN_OK;
+}
+
+uint64_t sn_launch_count(const sn_ctx* c) { return c ? (uint64_t)c->launches : 0; }
+
+sn_status sn_check_device(sn_ctx* c, sn_stream stream) {
+    if (!c) return SN_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sn_check_device");
+    int err = 0;
+    e = cudaMemcpy(&err, c->ws.err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sn_check_device");
+    if (err) {
+        cudaMemset(c->ws.err, 0, sizeof(int));
+        snprintf(c->msg, sizeof(c->msg), "device error bits 0x%x", err);
+        return SN_ETIMEOUT;
+    }
+    return SN_OK;
+}
+
+}  // extern "C"

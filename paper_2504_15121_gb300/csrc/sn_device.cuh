@@ -1,0 +1,295 @@
+// Device helpers shared by the kernels: ingest to the integer disparity
+// grid, shared-memory tile loads, the exact integer predicates, the
+// per-pixel least-squares pieces and the union-find primitives.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "sn_internal.h"
+
+namespace sn {
+
+constexpr int kFindLimit = 1 << 22;   // > any parent chain of a 16384^2 frame
+constexpr int kUnionLimit = 1 << 20;  // retries of one lock-free union
+
+// ---------------------------------------------------------------- ingest
+// D = rint(256 d) (ties to even) if d is finite, d > 0 and 1 <= D <= 131071,
+// else 0 (invalid).  256 d is exact in binary floating point, so the
+// comparisons below decide exactly the same as the definition.
+__device__ __forceinline__ int code_from_float(float d) {
+    const float x = d * 256.0f;
+    return (x > 0.5f && x < 131071.5f) ? __float2int_rn(x) : 0;
+}
+
+template <int IN>
+__device__ __forceinline__ int load_code(const char* __restrict__ base, size_t pitch, int x, int y,
+                                         int W, int H) {
+    if ((unsigned)x >= (unsigned)W || (unsigned)y >= (unsigned)H) return 0;
+    const char* row = base + (size_t)y * pitch;
+    if constexpr (IN == SN_IN_F32) {
+        return code_from_float(__ldg(reinterpret_cast<const float*>(row) + x));
+    } else if constexpr (IN == SN_IN_F16) {
+        return code_from_float(__half2float(__ldg(reinterpret_cast<const __half*>(row) + x)));
+    } else {
+        return __ldg(reinterpret_cast<const unsigned short*>(row) + x);
+    }
+}
+
+// Loads the integer codes of the rectangle [gx0, gx0 + TWR) x [gy0, gy0 + THR)
+// into `tile` (row-major, row length TWR); outside the image: 0.
+template <int IN>
+__device__ __forceinline__ void load_tile(int* tile, int TWR, int THR, const char* disp, size_t pitch,
+                                          int gx0, int gy0, int W, int H) {
+    const int n = TWR * THR;
+    const int nt = blockDim.x * blockDim.y;
+    for (int i = threadIdx.y * blockDim.x + threadIdx.x; i < n; i += nt) {
+        const int ly = i / TWR;
+        const int lx = i - ly * TWR;
+        tile[i] = load_code<IN>(disp, pitch, gx0 + lx, gy0 + ly, W, H);
+    }
+}
+
+// ---------------------------------------------------------------- predicates
+// 2^16 |a - b| <= K min(a, b), both valid
+__device__ __forceinline__ bool pair_edge(int a, int b, int K) {
+    if (a <= 0 || b <= 0) return false;
+    const unsigned diff = (unsigned)abs(a - b);
+    const unsigned mn = (unsigned)min(a, b);
+    return ((unsigned long long)diff << 16) <= (unsigned long long)(unsigned)K * mn;
+}
+
+// covered-depth stop: (nmax - nmin) Dc 2^16 > K nmin nmax
+__device__ __forceinline__ bool cd_stop(int nmin, int nmax, int Dc, int K) {
+    const unsigned long long lhs = ((unsigned long long)(unsigned)(nmax - nmin) * (unsigned)Dc) << 16;
+    const unsigned long long rhs =
+        (unsigned long long)(unsigned)K * ((unsigned long long)(unsigned)nmin * (unsigned)nmax);
+    return lhs > rhs;
+}
+
+// ---------------------------------------------------------------- denoise
+// Least-squares plane c + g . o over the range-gated window around the
+// centre `c` of a shared-memory tile with row stride TWR.  The sums are of
+// integers (exact); the 3x3 solve for the intercept uses exact int64
+// cofactors, and only the final quotient is rounded.  Returns den in pixels.
+__device__ __forceinline__ float denoise_at(const int* c, int TWR, int R, int Dc, int K_range,
+                                            bool& fit) {
+    const int thr = (int)(((unsigned long long)(unsigned)K_range * (unsigned)Dc) >> 16);
+    int n = 0, Su = 0, Sv = 0, Suu = 0, Suv = 0, Svv = 0, b0 = 0, b1 = 0, b2 = 0;
+    for (int ov = -R; ov <= R; ov++) {
+        const int* row = c + ov * TWR;
+        for (int ou = -R; ou <= R; ou++) {
+            const int Di = row[ou];
+            const int dd = Di - Dc;
+            if (Di > 0 && abs(dd) <= thr) {
+                n++;
+                Su += ou;
+                Sv += ov;
+                Suu += ou * ou;
+                Suv += ou * ov;
+                Svv += ov * ov;
+                b0 += dd;
+                b1 += ou * dd;
+                b2 += ov * dd;
+            }
+        }
+    }
+    // cofactor expansion of det(A) and of det(A with column 0 := b) along
+    // column 0; A = [[n, Su, Sv], [Su, Suu, Suv], [Sv, Suv, Svv]]
+    const long long M00 = (long long)Suu * Svv - (long long)Suv * Suv;
+    const long long M10 = (long long)Su * Svv - (long long)Sv * Suv;
+    const long long M20 = (long long)Su * Suv - (long long)Sv * Suu;
+    const long long det = n * M00 - Su * M10 + Sv * M20;
+    const long long num = b0 * M00 - b1 * M10 + b2 * M20;  // intercept - Dc, times det
+    fit = det > 0 && (long long)Dc * det + num > 0;
+    if (!fit) return (float)Dc * (1.0f / 256.0f);
+    const float dc = (float)num / (float)det;
+    return ((float)Dc + dc) * (1.0f / 256.0f);
+}
+
+// ---------------------------------------------------------------- affine
+// Pass-1 moments and pass-2 data sums over the support (all integers).
+struct AffSums {
+    int N, Su, Sv, Suu, Suv, Svv, Bu, Bv;
+};
+
+__device__ __forceinline__ void aff_zero(AffSums& s) {
+    s.N = s.Su = s.Sv = s.Suu = s.Suv = s.Svv = s.Bu = s.Bv = 0;
+}
+
+__device__ __forceinline__ void aff_add(AffSums& s, int ou, int ov, int dd) {
+    s.N++;
+    s.Su += ou;
+    s.Sv += ov;
+    s.Suu += ou * ou;
+    s.Suv += ou * ov;
+    s.Svv += ov * ov;
+    s.Bu += ou * dd;
+    s.Bv += ov * dd;
+}
+
+__device__ __forceinline__ void fixed_support(const int* c, int TWR, int R, int Dc, AffSums& s) {
+    aff_zero(s);
+    for (int ov = -R; ov <= R; ov++) {
+        const int* row = c + ov * TWR;
+        for (int ou = -R; ou <= R; ou++) {
+            const int Di = row[ou];
+            if (Di > 0 && (ou | ov) != 0) aff_add(s, ou, ov, Di - Dc);
+        }
+    }
+}
+
+// Star-fill with the covered-depth stop.  All threads of a warp walk the
+// same table entry in lock step (the table index is uniform).
+__device__ __forceinline__ void star_support(const int* c, int TWR, int Dc, int K,
+                                             const StarTable& T, int dirs, int steps, AffSums& s) {
+    aff_zero(s);
+    unsigned long long bits = 0ull;
+    for (int j = 0; j < dirs; j++) {
+        int dmin = Dc, dmax = Dc;
+        const int e0 = j * steps;
+        for (int k = 0; k < steps; k++) {
+            const int e = e0 + k;
+            const int cls = T.cls[e];
+            if (cls == 0) continue;  // same pixel as the previous step: cannot stop the ray
+            const int ou = T.ou[e], ov = T.ov[e];
+            const int Di = c[ov * TWR + ou];
+            if (Di <= 0) break;
+            const int nmin = min(dmin, Di), nmax = max(dmax, Di);
+            if (cd_stop(nmin, nmax, Dc, K)) break;
+            dmin = nmin;
+            dmax = nmax;
+            if (cls == 1)
+                aff_add(s, ou, ov, Di - Dc);
+            else
+                bits |= 1ull << T.bit[e];
+        }
+    }
+    for (int b = 0; b < T.nshared; b++) {
+        if ((bits >> b) & 1ull) {
+            const int ou = T.sou[b], ov = T.sov[b];
+            aff_add(s, ou, ov, c[ov * TWR + ou] - Dc);
+        }
+    }
+}
+
+// Solves the 2x2 system of pass 2 (anchored at the denoised centre, dtil in
+// pixels) and turns (g_u, g_v) into the camera-facing unit normal.
+// Returns false if the support does not determine the gradient.
+__device__ __forceinline__ bool solve_normal(const AffSums& s, int Dc, float dtil, int x, int y,
+                                             const Geo& g, float n[3], bool& fp64) {
+    fp64 = false;
+    if (s.N < 3) return false;
+    const long long a = s.Suu, b = s.Suv, gm = s.Svv;
+    const long long det = a * gm - b * b;
+    if (det <= 0) return false;
+    fp64 = 1024ll * det < a * gm;
+    // exact parts of gamma b_u - beta b_v and alpha b_v - beta b_u with the
+    // data anchored at the integer centre; the anchor shift to dtil enters
+    // through the (small) first moments only
+    const long long nu_i = gm * s.Bu - b * s.Bv;
+    const long long nv_i = a * s.Bv - b * s.Bu;
+    const long long cu = gm * s.Su - b * s.Sv;
+    const long long cv = a * s.Sv - b * s.Su;
+    if (!fp64) {
+        const float dcf = dtil * 256.0f - (float)Dc;
+        const float inv = 1.0f / (256.0f * (float)det);
+        const float gu = fmaf(-dcf, (float)cu, (float)nu_i) * inv;
+        const float gv = fmaf(-dcf, (float)cv, (float)nv_i) * inv;
+        const float mx = gu;
+        const float my = gv * g.fy_over_fx;
+        const float mz = (dtil - gu * ((float)x - g.cx) - gv * ((float)y - g.cy)) / g.fx;
+        const float r = rsqrtf(fmaf(mx, mx, fmaf(my, my, mz * mz)));
+        n[0] = -mx * r;
+        n[1] = -my * r;
+        n[2] = -mz * r;
+    } else {
+        const double dd = (double)dtil;
+        const double dcf = dd * 256.0 - (double)Dc;
+        const double inv = 1.0 / (256.0 * (double)det);
+        const double gu = ((double)nu_i - dcf * (double)cu) * inv;
+        const double gv = ((double)nv_i - dcf * (double)cv) * inv;
+        const double mx = gu;
+        const double my = gv * g.dfy / g.dfx;
+        const double mz = (dd - gu * ((double)x - g.dcx) - gv * ((double)y - g.dcy)) / g.dfx;
+        const double r = 1.0 / sqrt(mx * mx + my * my + mz * mz);
+        n[0] = (float)(-mx * r);
+        n[1] = (float)(-my * r);
+        n[2] = (float)(-mz * r);
+    }
+    return true;
+}
+
+__device__ __forceinline__ short snorm16(float v) {
+    return (short)__float2int_rn(32767.0f * fminf(fmaxf(v, -1.0f), 1.0f));
+}
+
+// ---------------------------------------------------------------- union-find
+// Parent arrays hold row-major pixel indices; parent[i] <= i always, so a
+// root is the smallest index of its tree.
+
+__device__ __forceinline__ int find_s(volatile int* L, int x) {
+    for (int it = 0; it < 4096; it++) {
+        const int p = L[x];
+        if (p == x) return x;
+        x = p;
+    }
+    return x;
+}
+
+// lock-free union on a shared-memory parent array: link the larger root
+// below the smaller one with atomicMin and retry on interference
+__device__ __forceinline__ void union_s(int* L, int a, int b, int* err) {
+    for (int it = 0; it < kUnionLimit; it++) {
+        a = find_s(L, a);
+        b = find_s(L, b);
+        if (a == b) return;
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicMin(&L[a], b);
+        if (old == a) return;
+        a = old;
+    }
+    atomicOr(err, kErrUnionLimit);
+}
+
+struct LabelIndex {
+    int W;
+    size_t pitch_elems;
+    __device__ __forceinline__ size_t addr(int i) const {
+        const int v = i / W;
+        return (size_t)v * pitch_elems + (size_t)(i - v * W);
+    }
+};
+
+__device__ __forceinline__ int find_g(const int* L, const LabelIndex& li, int x, int* err) {
+    for (int it = 0; it < kFindLimit; it++) {
+        const int p = __ldcg(L + li.addr(x));
+        if (p == x) return x;
+        x = p;
+    }
+    atomicOr(err, kErrFindLimit);
+    return x;
+}
+
+__device__ __forceinline__ void union_g(int* L, const LabelIndex& li, int a, int b, int* err) {
+    for (int it = 0; it < kUnionLimit; it++) {
+        a = find_g(L, li, a, err);
+        b = find_g(L, li, b, err);
+        if (a == b) return;
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicMin(L + li.addr(a), b);
+        if (old == a) return;
+        a = old;
+    }
+    atomicOr(err, kErrUnionLimit);
+}
+
+}  // namespace sn

@@ -1,0 +1,82 @@
+// Internal declarations shared by the C-ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sn.h"
+
+namespace sn {
+
+constexpr int kDMax = 131071;       // largest integer disparity code (d < 512 px)
+constexpr int kMaxDirs = 16;
+constexpr int kMaxSteps = 30;
+constexpr int kMaxStar = kMaxDirs * kMaxSteps;
+constexpr int kMaxShared = 64;      // offsets reached by more than one ray
+constexpr int kCclTile = 32;        // CCL tiles are 32 x 32 pixels
+
+// error bits written to the context's device error word
+constexpr int kErrFindLimit = 1;    // a union-find walk exceeded its bound
+constexpr int kErrUnionLimit = 2;   // a union retry loop exceeded its bound
+constexpr int kErrBarrier = 4;      // a grid barrier wait exceeded its bound
+
+// Per-context constants read by every kernel (passed by value).
+struct Geo {
+    int W, H;
+    int in_dtype;
+    int r_d, r_a, support, dirs, steps;
+    int K_cd, K_pair, K_range;
+    int normal_fmt;
+    float fx, fy, cx, cy, B;
+    float fy_over_fx, inv_fx, B_fx_over_fy, fxB;
+    double dfx, dfy, dcx, dcy, dB;
+    int* err;  // device error word
+};
+
+// Star-fill table.  cls: 0 = repeats the previous step of its ray (never
+// stops the ray, adds nothing), 1 = offset reached by this ray only
+// (accumulated when reached), 2 = offset reached by several rays (sets bit
+// `bit`; accumulated once after all rays).
+struct StarTable {
+    int n;
+    int nshared;
+    int8_t ou[kMaxStar];
+    int8_t ov[kMaxStar];
+    uint8_t cls[kMaxStar];
+    uint8_t bit[kMaxStar];
+    int8_t sou[kMaxShared];
+    int8_t sov[kMaxShared];
+};
+
+struct Workspace {
+    int* err = nullptr;        // device error word
+    float* den = nullptr;      // W x H floats, used by run_frame when the caller passes no den
+    size_t den_pitch = 0;
+    int32_t* count = nullptr;  // component counter when the caller passes none
+};
+
+// Counts kernel launches and, when `ev` is set, records one event after
+// each stage slot (a slot whose kernel is not needed still gets its event).
+struct Marks {
+    cudaEvent_t* ev = nullptr;
+    int n = 0;
+    unsigned long long launches = 0;
+    void after(cudaStream_t s, bool launched = true) {
+        if (launched) launches++;
+        if (ev) cudaEventRecord(ev[n++], s);
+    }
+};
+
+// Launchers (return cudaGetLastError() of their launches).
+cudaError_t launch_denoise(const Geo& g, const void* disp, size_t dp, float* den, size_t denp,
+                           uint8_t* mask, size_t mp, cudaStream_t s, Marks& mk);
+cudaError_t launch_affine(const Geo& g, const StarTable& t, const void* disp, size_t dp,
+                          const float* den, size_t denp, void* nrm, size_t np, uint8_t* mask,
+                          size_t mp, bool mask_or, cudaStream_t s, Marks& mk);
+cudaError_t launch_points(const Geo& g, const float* den, size_t denp, const uint8_t* mask,
+                          size_t mp, float* pts, size_t pp, cudaStream_t s, Marks& mk);
+// three stage slots: tile-local union-find, border merge, flatten
+cudaError_t launch_components(const Geo& g, const void* disp, size_t dp, int32_t* labels,
+                              size_t lp, int32_t* count, cudaStream_t s, Marks& mk);
+
+}  // namespace sn

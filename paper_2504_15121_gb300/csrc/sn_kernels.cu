@@ -1,0 +1,268 @@
+// Stage kernels of the surface-normal chain, one kernel per C-ABI stage:
+// denoise, affine + normal, point cloud, and the three passes of the
+// connected-component labelling (tile-local union-find in shared memory,
+// border merge with global atomics, flatten).
+#include "sn_device.cuh"
+
+namespace sn {
+
+constexpr int kTW = 32;  // tile width  (one warp per tile row)
+constexpr int kTH = 8;   // tile height (8 warps per block)
+
+// ---------------------------------------------------------------- denoise
+template <int IN>
+__global__ void __launch_bounds__(kTW* kTH)
+    k_denoise(const Geo g, const char* __restrict__ disp, size_t dp, float* __restrict__ den,
+              size_t denp, uint8_t* __restrict__ mask, size_t mp) {
+    extern __shared__ int tile[];
+    const int R = g.r_d;
+    const int TWR = kTW + 2 * R, THR = kTH + 2 * R;
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+    load_tile<IN>(tile, TWR, THR, disp, dp, x0 - R, y0 - R, g.W, g.H);
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= g.W || y >= g.H) return;
+    const int* c = tile + (threadIdx.y + R) * TWR + threadIdx.x + R;
+    const int Dc = c[0];
+    float out = 0.0f;
+    uint8_t m = 0;
+    if (Dc > 0) {
+        bool fit;
+        out = denoise_at(c, TWR, R, Dc, g.K_range, fit);
+        m = SN_MASK_VALID | (fit ? SN_MASK_DENOISED : 0);
+    }
+    reinterpret_cast<float*>(reinterpret_cast<char*>(den) + (size_t)y * denp)[x] = out;
+    mask[(size_t)y * mp + x] = m;
+}
+
+// ---------------------------------------------------------------- affine + normal
+template <int IN, int SUP>
+__global__ void __launch_bounds__(kTW* kTH)
+    k_affine(const Geo g, const __grid_constant__ StarTable T, const char* __restrict__ disp,
+             size_t dp, const float* __restrict__ den, size_t denp, char* __restrict__ nrm,
+             size_t np, uint8_t* __restrict__ mask, size_t mp, int mask_or) {
+    extern __shared__ int tile[];
+    const int R = SUP == SN_SUPPORT_FIXED ? g.r_a : g.steps;
+    const int TWR = kTW + 2 * R, THR = kTH + 2 * R;
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+    load_tile<IN>(tile, TWR, THR, disp, dp, x0 - R, y0 - R, g.W, g.H);
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= g.W || y >= g.H) return;
+    const int* c = tile + (threadIdx.y + R) * TWR + threadIdx.x + R;
+    const int Dc = c[0];
+    float n[3] = {0.0f, 0.0f, 0.0f};
+    uint8_t m = 0;
+    if (Dc > 0) {
+        m = SN_MASK_VALID;
+        const float dtil =
+            __ldg(reinterpret_cast<const float*>(reinterpret_cast<const char*>(den) + (size_t)y * denp) + x);
+        AffSums s;
+        if (SUP == SN_SUPPORT_FIXED)
+            fixed_support(c, TWR, R, Dc, s);
+        else
+            star_support(c, TWR, Dc, g.K_cd, T, g.dirs, g.steps, s);
+        bool fp64;
+        if (solve_normal(s, Dc, dtil, x, y, g, n, fp64)) m |= SN_MASK_NORMAL | (fp64 ? SN_MASK_FP64 : 0);
+    }
+    if (g.normal_fmt == SN_NORMALS_F32X3) {
+        const size_t plane = (size_t)g.H * np;
+        float* p0 = reinterpret_cast<float*>(nrm + (size_t)y * np) + x;
+        p0[0] = n[0];
+        *reinterpret_cast<float*>(reinterpret_cast<char*>(p0) + plane) = n[1];
+        *reinterpret_cast<float*>(reinterpret_cast<char*>(p0) + 2 * plane) = n[2];
+    } else {
+        short4 q;
+        q.x = snorm16(n[0]);
+        q.y = snorm16(n[1]);
+        q.z = snorm16(n[2]);
+        q.w = 0;
+        reinterpret_cast<short4*>(nrm + (size_t)y * np)[x] = q;
+    }
+    uint8_t* mo = mask + (size_t)y * mp + x;
+    *mo = mask_or ? (uint8_t)(*mo | m) : m;
+}
+
+// ---------------------------------------------------------------- points
+__global__ void __launch_bounds__(kTW* kTH)
+    k_points(const Geo g, const float* __restrict__ den, size_t denp, const uint8_t* __restrict__ mask,
+             size_t mp, float* __restrict__ pts, size_t pp) {
+    const int x = blockIdx.x * kTW + threadIdx.x, y = blockIdx.y * kTH + threadIdx.y;
+    if (x >= g.W || y >= g.H) return;
+    const float d = __ldg(reinterpret_cast<const float*>(reinterpret_cast<const char*>(den) + (size_t)y * denp) + x);
+    const uint8_t m = __ldg(mask + (size_t)y * mp + x);
+    float X = 0.0f, Y = 0.0f, Z = 0.0f;
+    if (m & SN_MASK_VALID) {
+        X = g.B * ((float)x - g.cx) / d;
+        Y = g.B_fx_over_fy * ((float)y - g.cy) / d;
+        Z = g.fxB / d;
+    }
+    const size_t plane = (size_t)g.H * pp;
+    char* p0 = reinterpret_cast<char*>(pts) + (size_t)y * pp + (size_t)x * 4;
+    *reinterpret_cast<float*>(p0) = X;
+    *reinterpret_cast<float*>(p0 + plane) = Y;
+    *reinterpret_cast<float*>(p0 + 2 * plane) = Z;
+}
+
+// ---------------------------------------------------------------- components
+// Pass 1: union-find inside each 32 x 32 tile (shared memory); every pixel
+// receives the global index of its tile-local root (the smallest index of
+// its tile-local component).
+template <int IN>
+__global__ void __launch_bounds__(kCclTile * 8)
+    k_ccl_local(const Geo g, const char* __restrict__ disp, size_t dp, int* __restrict__ labels,
+                size_t lpe, int* __restrict__ count) {
+    __shared__ int Ds[kCclTile * kCclTile];
+    __shared__ int Ls[kCclTile * kCclTile];
+    const int x0 = blockIdx.x * kCclTile, y0 = blockIdx.y * kCclTile;
+    const int tx = threadIdx.x;
+    if (count && blockIdx.x == 0 && blockIdx.y == 0 && tx == 0 && threadIdx.y == 0) *count = 0;
+    for (int r = threadIdx.y; r < kCclTile; r += 8) {
+        const int i = r * kCclTile + tx;
+        const int D = load_code<IN>(disp, dp, x0 + tx, y0 + r, g.W, g.H);
+        Ds[i] = D;
+        Ls[i] = D > 0 ? i : -1;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < kCclTile; r += 8) {
+        const int i = r * kCclTile + tx;
+        const int D = Ds[i];
+        if (D <= 0) continue;
+        if (tx + 1 < kCclTile && pair_edge(D, Ds[i + 1], g.K_pair)) union_s(Ls, i, i + 1, g.err);
+        if (r + 1 < kCclTile && pair_edge(D, Ds[i + kCclTile], g.K_pair)) union_s(Ls, i, i + kCclTile, g.err);
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < kCclTile; r += 8) {
+        const int x = x0 + tx, y = y0 + r;
+        if (x >= g.W || y >= g.H) continue;
+        const int i = r * kCclTile + tx;
+        int out = -1;
+        if (Ds[i] > 0) {
+            const int root = find_s(Ls, i);
+            out = (y0 + root / kCclTile) * g.W + x0 + (root % kCclTile);
+        }
+        labels[(size_t)y * lpe + x] = out;
+    }
+}
+
+// Pass 2: join components across tile borders (global atomicMin union).
+template <int IN>
+__global__ void __launch_bounds__(256)
+    k_ccl_merge(const Geo g, const char* __restrict__ disp, size_t dp, int* labels, size_t lpe,
+                int nbx, int nby) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nV = (long long)(nbx - 1) * g.H;
+    int px, py, qx, qy;
+    if (t < nV) {
+        const int k = (int)(t / g.H) + 1;
+        py = qy = (int)(t - (long long)(k - 1) * g.H);
+        qx = k * kCclTile;
+        px = qx - 1;
+    } else {
+        const long long t2 = t - nV;
+        if (t2 >= (long long)(nby - 1) * g.W) return;
+        const int k = (int)(t2 / g.W) + 1;
+        px = qx = (int)(t2 - (long long)(k - 1) * g.W);
+        qy = k * kCclTile;
+        py = qy - 1;
+    }
+    const int Dp = load_code<IN>(disp, dp, px, py, g.W, g.H);
+    const int Dq = load_code<IN>(disp, dp, qx, qy, g.W, g.H);
+    if (!pair_edge(Dp, Dq, g.K_pair)) return;
+    const LabelIndex li{g.W, lpe};
+    union_g(labels, li, py * g.W + px, qy * g.W + qx, g.err);
+}
+
+// Pass 3: every pixel points at its global root, which is the smallest
+// index of its component; roots are counted.
+__global__ void __launch_bounds__(kTW* kTH)
+    k_ccl_flatten(const Geo g, int* labels, size_t lpe, int* count) {
+    const int x = blockIdx.x * kTW + threadIdx.x, y = blockIdx.y * kTH + threadIdx.y;
+    if (x >= g.W || y >= g.H) return;
+    int* a = labels + (size_t)y * lpe + x;
+    const int l = __ldcg(a);
+    if (l < 0) return;
+    const LabelIndex li{g.W, lpe};
+    const int r = find_g(labels, li, l, g.err);
+    if (r != l) __stcg(a, r);
+    if (count && r == y * g.W + x) atomicAdd(count, 1);
+}
+
+// ---------------------------------------------------------------- launchers
+static dim3 grid2(const Geo& g) { return dim3((g.W + kTW - 1) / kTW, (g.H + kTH - 1) / kTH); }
+
+cudaError_t launch_denoise(const Geo& g, const void* disp, size_t dp, float* den, size_t denp,
+                           uint8_t* mask, size_t mp, cudaStream_t s, Marks& mk) {
+    const int R = g.r_d;
+    const size_t smem = sizeof(int) * (kTW + 2 * R) * (kTH + 2 * R);
+    const char* d = static_cast<const char*>(disp);
+    switch (g.in_dtype) {
+        case SN_IN_F32: k_denoise<SN_IN_F32><<<grid2(g), dim3(kTW, kTH), smem, s>>>(g, d, dp, den, denp, mask, mp); break;
+        case SN_IN_F16: k_denoise<SN_IN_F16><<<grid2(g), dim3(kTW, kTH), smem, s>>>(g, d, dp, den, denp, mask, mp); break;
+        default: k_denoise<SN_IN_U16X256><<<grid2(g), dim3(kTW, kTH), smem, s>>>(g, d, dp, den, denp, mask, mp); break;
+    }
+    mk.after(s);
+    return cudaGetLastError();
+}
+
+template <int IN>
+static void affine_dispatch(const Geo& g, const StarTable& t, const char* d, size_t dp, const float* den,
+                            size_t denp, char* nrm, size_t np, uint8_t* mask, size_t mp, int mor,
+                            size_t smem, cudaStream_t s) {
+    if (g.support == SN_SUPPORT_FIXED)
+        k_affine<IN, SN_SUPPORT_FIXED><<<grid2(g), dim3(kTW, kTH), smem, s>>>(g, t, d, dp, den, denp, nrm, np, mask, mp, mor);
+    else
+        k_affine<IN, SN_SUPPORT_STARFILL_CD><<<grid2(g), dim3(kTW, kTH), smem, s>>>(g, t, d, dp, den, denp, nrm, np, mask, mp, mor);
+}
+
+cudaError_t launch_affine(const Geo& g, const StarTable& t, const void* disp, size_t dp,
+                          const float* den, size_t denp, void* nrm, size_t np, uint8_t* mask,
+                          size_t mp, bool mask_or, cudaStream_t s, Marks& mk) {
+    const int R = g.support == SN_SUPPORT_FIXED ? g.r_a : g.steps;
+    const size_t smem = sizeof(int) * (kTW + 2 * R) * (kTH + 2 * R);
+    const char* d = static_cast<const char*>(disp);
+    char* n = static_cast<char*>(nrm);
+    switch (g.in_dtype) {
+        case SN_IN_F32: affine_dispatch<SN_IN_F32>(g, t, d, dp, den, denp, n, np, mask, mp, mask_or, smem, s); break;
+        case SN_IN_F16: affine_dispatch<SN_IN_F16>(g, t, d, dp, den, denp, n, np, mask, mp, mask_or, smem, s); break;
+        default: affine_dispatch<SN_IN_U16X256>(g, t, d, dp, den, denp, n, np, mask, mp, mask_or, smem, s); break;
+    }
+    mk.after(s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_points(const Geo& g, const float* den, size_t denp, const uint8_t* mask, size_t mp,
+                          float* pts, size_t pp, cudaStream_t s, Marks& mk) {
+    k_points<<<grid2(g), dim3(kTW, kTH), 0, s>>>(g, den, denp, mask, mp, pts, pp);
+    mk.after(s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_components(const Geo& g, const void* disp, size_t dp, int32_t* labels, size_t lp,
+                              int32_t* count, cudaStream_t s, Marks& mk) {
+    const int nbx = (g.W + kCclTile - 1) / kCclTile, nby = (g.H + kCclTile - 1) / kCclTile;
+    const size_t lpe = lp / sizeof(int32_t);
+    const char* d = static_cast<const char*>(disp);
+    const long long pairs = (long long)(nbx - 1) * g.H + (long long)(nby - 1) * g.W;
+    const unsigned mblocks = (unsigned)((pairs + 255) / 256);
+    const dim3 lg(nbx, nby), lb(kCclTile, 8);
+    switch (g.in_dtype) {
+        case SN_IN_F32: k_ccl_local<SN_IN_F32><<<lg, lb, 0, s>>>(g, d, dp, labels, lpe, count); break;
+        case SN_IN_F16: k_ccl_local<SN_IN_F16><<<lg, lb, 0, s>>>(g, d, dp, labels, lpe, count); break;
+        default: k_ccl_local<SN_IN_U16X256><<<lg, lb, 0, s>>>(g, d, dp, labels, lpe, count); break;
+    }
+    mk.after(s);
+    if (pairs > 0) {
+        switch (g.in_dtype) {
+            case SN_IN_F32: k_ccl_merge<SN_IN_F32><<<mblocks, 256, 0, s>>>(g, d, dp, labels, lpe, nbx, nby); break;
+            case SN_IN_F16: k_ccl_merge<SN_IN_F16><<<mblocks, 256, 0, s>>>(g, d, dp, labels, lpe, nbx, nby); break;
+            default: k_ccl_merge<SN_IN_U16X256><<<mblocks, 256, 0, s>>>(g, d, dp, labels, lpe, nbx, nby); break;
+        }
+    }
+    mk.after(s, pairs > 0);
+    k_ccl_flatten<<<grid2(g), dim3(kTW, kTH), 0, s>>>(g, labels, lpe, count);
+    mk.after(s);
+    return cudaGetLastError();
+}
+
+}  // namespace sn

@@ -1,0 +1,295 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances are in tests/parity.py.  Inputs are seeded: scenes from the
+generator (the benchmark workloads at full size included), ragged and tiny
+images, adversarial component shapes and constructed ill-conditioned
+supports.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from scenes import Camera, make_scene
+from parity import compare_frame, compare_normals, oracle_params, run_gpu, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_15121_gb300 as P
+    return P
+
+
+CAM = Camera(fx=300.0, fy=280.0, cx=21.5, cy=14.0, baseline=0.12)
+
+
+def chain(P, disp, cam, **params):
+    H, W = disp.shape
+    pipe = P.Pipeline(cam, W, H, **params)
+    try:
+        g = run_gpu(pipe, disp)
+        ref = oracle.run_frame(disp, cam, oracle_params(pipe.params))
+    finally:
+        pipe.close()
+    return g, ref
+
+
+def codes_to_f32(D):
+    return (D.astype(np.float64) / 256.0).astype(np.float32)
+
+
+# ------------------------------------------------------------ scenes
+@pytest.mark.parametrize("frame", [0, 1, 2])
+@pytest.mark.parametrize("support", [1, 0])
+def test_scene_320x240(P, frame, support):
+    s = make_scene("planes_320x240", frame=frame)
+    g, ref = chain(P, s.disp, s.camera, support=support)
+    compare_frame(g, ref)
+
+
+@pytest.mark.parametrize("name", ["planes_640x480", "mixed_1482x994", "driving_2048x1024"])
+def test_scene_full_size(P, name):
+    s = make_scene(name, frame=0)
+    g, ref = chain(P, s.disp, s.camera)
+    mean, mx = compare_frame(g, ref)
+    print(f"{name}: normals mean {mean:.2e} max {mx:.2e} deg, {ref.n_components} components")
+
+
+def test_driving_u16_and_f16_inputs(P):
+    s = make_scene("driving_2048x1024", frame=1)
+    for arr, dt in ((s.disp_u16, P.sn.SN_IN_U16X256), (s.disp_f16, P.sn.SN_IN_F16)):
+        g, ref = chain(P, arr, s.camera, in_dtype=dt)
+        compare_frame(g, ref)
+
+
+def test_snorm16_output(P):
+    s = make_scene("planes_640x480", frame=3)
+    H, W = s.disp.shape
+    pipe32 = P.Pipeline(s.camera, W, H)
+    pipe16 = P.Pipeline(s.camera, W, H, normal_fmt=P.sn.SN_NORMALS_SNORM16X4)
+    try:
+        g32 = run_gpu(pipe32, s.disp)
+        g16 = run_gpu(pipe16, s.disp)
+    finally:
+        pipe32.close()
+        pipe16.close()
+    q = g16["normals"].astype(np.int64)
+    assert (q[..., 3] == 0).all()
+    # the code is rint(32767 n) of the FP32 normal, decided in FP32 as on the GPU
+    n32 = torch.from_numpy(g32["normals"].astype(np.float32))
+    want = torch.round(32767.0 * n32.clamp(-1, 1)).to(torch.int64).numpy()
+    assert np.array_equal(q[..., :3], want)
+    ref = oracle.run_frame(s.disp, s.camera)
+    ok = (ref.mask & oracle.M_NORMAL) > 0
+    assert np.abs(q[..., :3][ok] - 32767.0 * ref.normals[ok]).max() <= 1.0
+    assert np.array_equal(g16["mask"], ref.mask)
+
+
+# ------------------------------------------------------------ tiny and ragged
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 7), (7, 1), (5, 7), (17, 33), (40, 65), (9, 129)])
+@pytest.mark.parametrize("support", [1, 0])
+def test_ragged_random(P, H, W, support):
+    rng = np.random.default_rng(H * 1000 + W)
+    base = rng.integers(4000, 4400, (H, W))
+    blocks = rng.integers(0, 3, (H // 3 + 1, W // 3 + 1)).repeat(3, 0).repeat(3, 1)[:H, :W]
+    D = (base * (1 + 0.25 * blocks)).astype(np.int32)
+    D[rng.random((H, W)) < 0.2] = 0
+    cam = Camera(300.0, 300.0, W / 2, H / 2, 0.1)
+    g, ref = chain(P, codes_to_f32(D), cam, support=support)
+    compare_frame(g, ref)
+
+
+def test_all_invalid(P):
+    disp = np.zeros((37, 45), np.float32)
+    disp[3, 4] = np.nan
+    disp[5, 6] = -3.0
+    disp[7, 8] = np.inf
+    disp[9, 9] = 1.0 / 1024
+    g, ref = chain(P, disp, CAM)
+    compare_frame(g, ref)
+    assert ref.n_components == 0 and (g["labels"] == -1).all() and (g["mask"] == 0).all()
+
+
+def test_constant_and_planes(P):
+    D = np.full((48, 70), 9000, np.int32)
+    g, ref = chain(P, codes_to_f32(D), CAM)
+    compare_frame(g, ref)
+    u = np.arange(70)[None, :]
+    v = np.arange(48)[:, None]
+    D = (30000 - 120 * u + 64 * v).astype(np.int32)
+    g, ref = chain(P, codes_to_f32(D), CAM)
+    compare_frame(g, ref)
+
+
+# ------------------------------------------------------------ parameters
+@pytest.mark.parametrize("params", [
+    dict(support=1, dirs=16, steps=30),
+    dict(support=1, dirs=16, steps=6),
+    dict(support=1, dirs=4, steps=3, k_cd=0.02),
+    dict(support=1, dirs=12, steps=7, k_cd=0.3),
+    dict(support=0, r_affine=1),
+    dict(support=0, r_affine=7),
+    dict(support=0, r_affine=15),
+    dict(r_denoise=1, k_range=0.01),
+    dict(r_denoise=4, k_range=0.2),
+    dict(k_pair=0.0),
+    dict(k_pair=1.0),
+])
+def test_parameter_sweep(P, params):
+    s = make_scene("planes_320x240", frame=5)
+    g, ref = chain(P, s.disp, s.camera, **params)
+    compare_frame(g, ref)
+
+
+def test_fp64_fallback_support(P):
+    # support = the digital line (2k, k), k = -7..7, plus (1, 0): 1024 det < alpha gamma
+    D = np.zeros((41, 41), np.int32)
+    for k in range(-7, 8):
+        D[20 + k, 20 + 2 * k] = 6000 + 10 * k
+    D[20, 21] = 6003
+    g, ref = chain(P, codes_to_f32(D), CAM, support=0, r_affine=15)
+    assert ref.mask[20, 20] & oracle.M_FP64
+    compare_frame(g, ref)
+
+
+# ------------------------------------------------------------ components
+def spiral(n):
+    """A one-pixel corridor winding inwards, laps separated by one-pixel
+    walls: a single component whose min-index label must travel through
+    every tile of the frame."""
+    D = np.zeros((n, n), np.int32)
+    dirs = [(1, 0), (0, 1), (-1, 0), (0, -1)]
+    x = y = k = 0
+    D[0, 0] = 5000
+    stuck = 0
+    while stuck < 2:
+        dx, dy = dirs[k]
+        nx, ny, fx, fy = x + dx, y + dy, x + 2 * dx, y + 2 * dy
+        inside = 0 <= nx < n and 0 <= ny < n
+        blocked = 0 <= fx < n and 0 <= fy < n and D[fy, fx] != 0
+        if inside and D[ny, nx] == 0 and not blocked:
+            x, y = nx, ny
+            D[y, x] = 5000
+            stuck = 0
+        else:
+            k = (k + 1) % 4
+            stuck += 1
+    return D
+
+
+@pytest.mark.parametrize("shape", ["spiral", "comb", "checker", "stripes", "random_steps"])
+def test_components_adversarial(P, shape):
+    rng = np.random.default_rng(11)
+    if shape == "spiral":
+        D = spiral(131)
+    elif shape == "comb":
+        D = np.zeros((100, 150), np.int32)
+        D[:, ::2] = 7000
+        D[0, :] = 7000
+        D[99, 1::4] = 7000
+    elif shape == "checker":
+        D = ((np.indices((70, 90)).sum(0) % 2) * 6000).astype(np.int32)
+        D[::7] = 6000
+    elif shape == "stripes":
+        D = np.full((96, 96), 8000, np.int32)
+        D[:, 31::32] = 16000       # steps exactly on tile borders
+        D[31::32, :] = 4000
+    else:
+        D = rng.choice([0, 1000, 1030, 1049, 1051, 1200, 3000], size=(150, 200)).astype(np.int32)
+    H, W = D.shape
+    cam = Camera(300.0, 300.0, W / 2, H / 2, 0.1)
+    pipe = P.Pipeline(cam, W, H)
+    try:
+        disp = pipe.upload(codes_to_f32(D))
+        labels = P.sn.empty_image(H, W, torch.int32)
+        nc = torch.zeros(1, dtype=torch.int32, device="cuda")
+        P.sn.sn_components(pipe.ctx, disp, labels, nc)
+        torch.cuda.synchronize()
+        P.sn.sn_check_device(pipe.ctx)
+        lab, n = oracle.components(D, oracle_params(pipe.params))
+        assert np.array_equal(labels.cpu().numpy(), lab)
+        assert int(nc.item()) == n
+    finally:
+        pipe.close()
+
+
+# ------------------------------------------------------------ stage entry points
+def test_stage_entry_points(P):
+    s = make_scene("mixed_1482x994", frame=2)
+    H, W = s.disp.shape
+    pipe = P.Pipeline(s.camera, W, H)
+    sn = P.sn
+    try:
+        disp = pipe.upload(s.disp)
+        den = sn.empty_image(H, W, torch.float32)
+        m1 = sn.empty_image(H, W, torch.uint8)
+        sn.sn_denoise(pipe.ctx, disp, den, m1)
+        nrm = sn.empty_planes(3, H, W)
+        m2 = sn.empty_image(H, W, torch.uint8)
+        sn.sn_affine_normals(pipe.ctx, disp, den, nrm, m2)
+        pts = sn.empty_planes(3, H, W)
+        sn.sn_pointcloud(pipe.ctx, den, m1, pts)
+        lab = sn.empty_image(H, W, torch.int32)
+        sn.sn_components(pipe.ctx, disp, lab, None)
+        torch.cuda.synchronize()
+        sn.sn_check_device(pipe.ctx)
+        op = oracle_params(pipe.params)
+        D = oracle.ingest(s.disp)
+        den_o, fit = oracle.denoise(D, op)
+        g_den = den.cpu().numpy().astype(np.float64)
+        assert (np.abs(g_den - den_o) <= 1e-6 * den_o).all()
+        want1 = (D > 0).astype(np.uint8) * oracle.M_VALID | fit * oracle.M_DENOISED
+        assert np.array_equal(m1.cpu().numpy(), want1)
+        nrm_o, mask_o = oracle.affine_normals(D, den_o, s.camera, op)
+        assert np.array_equal(m2.cpu().numpy(), mask_o)
+        compare_normals(nrm.permute(1, 2, 0).cpu().numpy().astype(np.float64), nrm_o, mask_o)
+        pts_o = oracle.points(den_o, want1, s.camera)
+        perr = np.linalg.norm(pts.permute(1, 2, 0).cpu().numpy() - pts_o, axis=-1)
+        assert (perr <= 1e-6 * np.linalg.norm(pts_o, axis=-1) + 1e-30).all()
+        lab_o, _ = oracle.components(D, op)
+        assert np.array_equal(lab.cpu().numpy(), lab_o)
+    finally:
+        pipe.close()
+
+
+def test_repeatable_and_den_optional(P):
+    s = make_scene("planes_640x480", frame=7)
+    H, W = s.disp.shape
+    pipe = P.Pipeline(s.camera, W, H)
+    try:
+        disp = pipe.upload(s.disp)
+        a, b = pipe.buffers(), pipe.buffers()
+        pipe.run_frame(disp, a)
+        pipe.run_frame(disp, b, write_den=False)
+        torch.cuda.synchronize()
+        ha, hb = to_host(a), to_host(b)
+        for k in ("normals", "points", "labels", "mask"):
+            assert np.array_equal(ha[k], hb[k]), k
+    finally:
+        pipe.close()
+
+
+def test_argument_errors_on_device(P):
+    s = make_scene("planes_320x240", frame=0)
+    H, W = s.disp.shape
+    pipe = P.Pipeline(s.camera, W, H)
+    sn = P.sn
+    try:
+        disp = pipe.upload(s.disp)
+        out = pipe.buffers()
+        bad = torch.empty((H, W), dtype=torch.float32, device="cuda")   # pitch 1280: fine
+        odd = torch.empty((H, W + 1), dtype=torch.float32, device="cuda")[:, :W]  # pitch 1284
+        with pytest.raises(sn.SnError) as ei:
+            sn.sn_denoise(pipe.ctx, disp, odd, out.mask)
+        assert ei.value.status == sn.SN_EINVAL
+        small = sn.empty_image(H, W - 8, torch.float32)
+        with pytest.raises(sn.SnError):
+            sn.sn_denoise(pipe.ctx, disp, small, out.mask)
+        sn.sn_denoise(pipe.ctx, disp, bad, out.mask)
+        torch.cuda.synchronize()
+    finally:
+        pipe.close()

@@ -1,0 +1,71 @@
+"""Host-side checks of libsn.so that need no GPU: exported symbols against
+include/sn.h, the star-fill table against the oracle's, defaults and
+argument validation (errors returned before any CUDA call)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from scenes import Camera
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sn():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2504_15121_gb300 import sn as m
+    return m
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "sn.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sn_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(sn):
+    names = declared_functions()
+    assert "sn_run_frame" in names and len(names) >= 14
+    lib = C.CDLL(sn.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(sn.EXPORTS)
+
+
+@pytest.mark.parametrize("M,s", [(8, 10), (16, 30), (4, 1), (12, 7), (16, 6)])
+def test_star_table_matches_oracle(sn, M, s):
+    ou, ov = sn.star_offsets(M, s)
+    ou_o, ov_o = oracle.star_offsets(M, s)
+    assert np.array_equal(ou, ou_o) and np.array_equal(ov, ov_o)
+
+
+def test_defaults(sn):
+    p = sn.default_params()
+    assert (p.r_denoise, p.r_affine, p.support, p.dirs, p.steps) == (2, 4, sn.SN_SUPPORT_STARFILL_CD, 8, 10)
+    assert abs(p.k_cd - 0.1) < 1e-7 and abs(p.k_pair - 0.05) < 1e-7 and abs(p.tau - 0.9) < 1e-7
+    assert (p.in_dtype, p.normal_fmt, p.learned) == (sn.SN_IN_F32, sn.SN_NORMALS_F32X3, 0)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(W=0), dict(H=-1), dict(W=20000), dict(r_denoise=0), dict(r_denoise=5), dict(r_affine=16),
+    dict(dirs=3), dict(dirs=17), dict(steps=31), dict(k_cd=-0.1), dict(k_pair=1.5), dict(support=7),
+    dict(in_dtype=9), dict(normal_fmt=3), dict(fx=0.0), dict(baseline=-1.0)])
+def test_create_rejects_bad_arguments(sn, bad):
+    bad = dict(bad)
+    W, H = bad.pop("W", 64), bad.pop("H", 48)
+    cam = Camera(bad.pop("fx", 300.0), 300.0, 32.0, 24.0, bad.pop("baseline", 0.1))
+    p = sn.default_params(**bad)
+    with pytest.raises(sn.SnError) as ei:
+        sn.sn_create(cam, W, H, p)
+    assert ei.value.status == sn.SN_EINVAL
+
+
+def test_status_strings(sn):
+    for st in range(7):
+        assert sn.lib.sn_status_string(st)
+    assert sn.lib.sn_star_offsets(17, 3, None, None) == -1
