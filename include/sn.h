@@ -197,6 +197,28 @@ typedef struct {
  * all their bits.  Enqueued as a few fused kernels on `stream`. */
 sn_status sn_run_frame(sn_ctx *ctx, const sn_frame_in *in, sn_frame_out *out, sn_stream stream);
 
+/* Allocation-free denoise + normals.  The paper has no counterpart: this is
+ * for callers that cannot call cudaMalloc -- a plugin whose host application
+ * owns all device memory through its own pool, or a real-time loop that must
+ * not call it because it can synchronise the device and take unbounded time.
+ * It needs no context (sn_create allocates): camera, parameters (NULL =
+ * defaults) and size are passed directly, and the results are those of
+ * sn_denoise followed by sn_affine_normals on the same input (normals and
+ * mask with SN_MASK_VALID | SN_MASK_NORMAL | SN_MASK_FP64).
+ * The denoised plane lives in a static device array of the library, sized for
+ * frames with H * (W rounded up to a multiple of 4) <= 2048 * 1024 elements
+ * (8 MiB, held on every GPU that loads the library until the process exits);
+ * larger frames return SN_EINVAL before anything is enqueued.  Nothing is
+ * allocated by this call.  The first call on a device resolves the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls on a device share the
+ * array: calls whose work overlaps on the GPU (different streams without
+ * ordering) race and give undefined results.  Buffers follow the rules at the
+ * top of this header. */
+sn_status sn_normals_noalloc(const sn_camera *cam, const sn_params *p, int W, int H, const void *disp,
+                             size_t disp_pitch, void *normals, size_t normals_pitch, uint8_t *mask,
+                             size_t mask_pitch, sn_stream stream);
+
 /* Loads the learned gate's weights (format version, BF16 weights, FP32
  * biases; see the package's gate module).  Copies synchronously. */
 sn_status sn_load_gate_weights(sn_ctx *ctx, const void *blob, size_t bytes);

@@ -110,6 +110,58 @@ bool build_star(int M, int s, sn::StarTable& T) {
 
 }  // namespace
 
+namespace sn {
+
+// Validates camera, size and parameters like sn_create and fills the kernel
+// constants, without touching the device (used by the allocation-free entry
+// point; err is left null for the caller to set).
+sn_status prepare_constants(const sn_camera* cam, int W, int H, const sn_params* p, Geo* g, StarTable* t) {
+    if (!cam || !p || !g || !t || W < 1 || H < 1 || W > 16384 || H > 16384) return SN_EINVAL;
+    if (!(cam->fx > 0) || !(cam->fy > 0) || !(cam->baseline > 0) || !isfinite(cam->cx) || !isfinite(cam->cy) ||
+        !isfinite(cam->fx) || !isfinite(cam->fy) || !isfinite(cam->baseline))
+        return SN_EINVAL;
+    if (p->r_denoise < 1 || p->r_denoise > 4 || p->r_affine < 1 || p->r_affine > 15) return SN_EINVAL;
+    if (p->support != SN_SUPPORT_FIXED && p->support != SN_SUPPORT_STARFILL_CD) return SN_EINVAL;
+    if (p->dirs < 4 || p->dirs > kMaxDirs || p->steps < 1 || p->steps > kMaxSteps) return SN_EINVAL;
+    if (!(p->k_cd >= 0 && p->k_cd <= 1) || !(p->k_pair >= 0 && p->k_pair <= 1) ||
+        !(p->k_range >= 0 && p->k_range <= 1) || !(p->tau >= 0 && p->tau <= 1))
+        return SN_EINVAL;
+    if (p->in_dtype < SN_IN_F32 || p->in_dtype > SN_IN_U16X256) return SN_EINVAL;
+    if (p->normal_fmt != SN_NORMALS_F32X3 && p->normal_fmt != SN_NORMALS_SNORM16X4) return SN_EINVAL;
+    if (p->learned) return SN_ENOTSUP;
+    if (!build_star(p->dirs, p->steps, *t)) return SN_ENOTSUP;
+    memset(g, 0, sizeof(*g));
+    g->W = W;
+    g->H = H;
+    g->in_dtype = p->in_dtype;
+    g->r_d = p->r_denoise;
+    g->r_a = p->r_affine;
+    g->support = p->support;
+    g->dirs = p->dirs;
+    g->steps = p->steps;
+    g->K_cd = kfix(p->k_cd);
+    g->K_pair = kfix(p->k_pair);
+    g->K_range = kfix(p->k_range);
+    g->normal_fmt = p->normal_fmt;
+    g->fx = (float)cam->fx;
+    g->fy = (float)cam->fy;
+    g->cx = (float)cam->cx;
+    g->cy = (float)cam->cy;
+    g->B = (float)cam->baseline;
+    g->fy_over_fx = (float)(cam->fy / cam->fx);
+    g->inv_fx = (float)(1.0 / cam->fx);
+    g->B_fx_over_fy = (float)(cam->baseline * cam->fx / cam->fy);
+    g->fxB = (float)(cam->fx * cam->baseline);
+    g->dfx = cam->fx;
+    g->dfy = cam->fy;
+    g->dcx = cam->cx;
+    g->dcy = cam->cy;
+    g->dB = cam->baseline;
+    return SN_OK;
+}
+
+}  // namespace sn
+
 extern "C" {
 
 int sn_version(void) { return (0 << 16) | 3; }

@@ -67,6 +67,10 @@ struct Marks {
     }
 };
 
+// Checks camera, size and parameters and fills the kernel constants without
+// touching the device.
+sn_status prepare_constants(const sn_camera* cam, int W, int H, const sn_params* p, Geo* g, StarTable* t);
+
 // Launchers (return cudaGetLastError() of their launches).
 cudaError_t launch_denoise(const Geo& g, const void* disp, size_t dp, float* den, size_t denp,
                            uint8_t* mask, size_t mp, cudaStream_t s, Marks& mk);

@@ -87,6 +87,8 @@ def _load():
         "sn_stage_name": ([vp, i], C.c_char_p),
         "sn_stage_times": ([vp, C.POINTER(C.c_double), i, C.POINTER(C.c_int), C.POINTER(C.c_double), i], i),
         "sn_launch_count": ([vp], C.c_uint64),
+        "sn_normals_noalloc": ([C.POINTER(sn_camera), C.POINTER(sn_params), i, i, vp, sz, vp, sz, vp,
+                                sz, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -102,7 +104,7 @@ EXPORTS = ("sn_version", "sn_default_params", "sn_create", "sn_destroy", "sn_den
            "sn_affine_normals", "sn_components", "sn_pointcloud", "sn_run_frame",
            "sn_load_gate_weights", "sn_star_offsets", "sn_check_device", "sn_status_string",
            "sn_last_error", "sn_set_profiling", "sn_stage_count", "sn_stage_name",
-           "sn_stage_times", "sn_launch_count")
+           "sn_stage_times", "sn_launch_count", "sn_normals_noalloc")
 
 
 # ---------------------------------------------------------------- helpers
@@ -268,3 +270,16 @@ def sn_stage_times(ctx, cap: int = 4096):
 
 def sn_launch_count(ctx) -> int:
     return int(lib.sn_launch_count(ctx))
+
+
+def sn_normals_noalloc(cam, params, disp, normals, mask, stream=None):
+    """Denoise + normals with the library's static device scratch (no
+    allocation, no context).  `params` None = defaults."""
+    c = sn_camera(cam.fx, cam.fy, cam.cx, cam.cy, cam.baseline)
+    H, W = disp.shape[0], disp.shape[1]
+    d, dp = _img(disp)
+    n, np_ = _img(normals)
+    m, mp = _img(mask)
+    st = lib.sn_normals_noalloc(C.byref(c), C.byref(params) if params is not None else None, W, H,
+                                d, dp, n, np_, m, mp, _stream(stream))
+    _check(None, st)
