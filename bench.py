@@ -30,10 +30,7 @@ METRIC = "MPix/s (2048x1024 stereo normals chain)"
 # algorithmic bytes per pixel of each launch of sn_run_frame (compulsory
 # reads and writes of that kernel)
 ALGO_BYTES = {
-    "denoise": 4 + 4 + 1,                 # disp in; den, mask out
-    "affine_normals": 4 + 4 + 1 + 12 + 1,  # disp, den, mask in; normals, mask out
-    "pointcloud": 4 + 1 + 12,             # den, mask in; points out
-    "ccl_local": 4 + 4,                   # disp in; labels out
+    "frame": 4 + 12 + 12 + 1 + 4,         # disp in; normals, points, mask, tile-local labels out
     "ccl_merge": 0,                       # tile borders only
     "ccl_flatten": 4 + 4,                 # labels in and out
 }

@@ -9,10 +9,9 @@
 #include "sn_internal.h"
 
 namespace {
-constexpr int kStages = 6;         // kernel launches of one sn_run_frame
+constexpr int kStages = 3;         // kernel launches of one sn_run_frame
 constexpr int kProfFrames = 4096;  // frames recorded between two sn_stage_times calls
-const char* const kStageNames[kStages] = {"denoise", "affine_normals", "pointcloud",
-                                          "ccl_local", "ccl_merge", "ccl_flatten"};
+const char* const kStageNames[kStages] = {"frame", "ccl_merge", "ccl_flatten"};
 }  // namespace
 
 struct sn_ctx {
@@ -24,6 +23,7 @@ struct sn_ctx {
     sn::StarTable star;
     sn::Workspace ws;
     unsigned long long launches;
+    bool star8;  // the star table is the compile-time M = 8, s = 10 ray set
     bool prof;
     cudaEvent_t* ev;  // kProfFrames x (kStages + 1)
     int prof_frames;
@@ -112,6 +112,22 @@ bool build_star(int M, int s, sn::StarTable& T) {
 
 namespace sn {
 
+// With w = fl(1/D) and thr = fl(K 2^-16 / Dc), the computed spread
+// fl(w_hi - w_lo) differs from 1/Dmin - 1/Dmax by at most
+// 2^-24 (2 (1 + kappa) / kappa + 2) thr near the threshold (kappa = K/2^16;
+// near the threshold Dmin >= Dc / (1 + kappa)).  The band is four times that.
+void cd_band(int K, float* hi, float* lo) {
+    if (K <= 0) {
+        *hi = 1.0f;
+        *lo = 1.0f;
+        return;
+    }
+    const double kappa = K / 65536.0;
+    const double e = 4.0 * ldexp(1.0, -24) * (2.0 * (1.0 + kappa) / kappa + 2.0);
+    *hi = (float)(1.0 + e);
+    *lo = (float)(1.0 - e);
+}
+
 // Validates camera, size and parameters like sn_create and fills the kernel
 // constants, without touching the device (used by the allocation-free entry
 // point; err is left null for the caller to set).
@@ -142,6 +158,7 @@ sn_status prepare_constants(const sn_camera* cam, int W, int H, const sn_params*
     g->K_cd = kfix(p->k_cd);
     g->K_pair = kfix(p->k_pair);
     g->K_range = kfix(p->k_range);
+    cd_band(g->K_cd, &g->cd_hi, &g->cd_lo);
     g->normal_fmt = p->normal_fmt;
     g->fx = (float)cam->fx;
     g->fy = (float)cam->fy;
@@ -236,6 +253,7 @@ sn_status sn_create(const sn_camera* cam, int W, int H, const sn_params* pin, sn
         delete c;
         return SN_ENOTSUP;
     }
+    c->star8 = sn::star_is_m8(c->star, p.dirs, p.steps);
     sn::Geo& g = c->geo;
     g.W = W;
     g.H = H;
@@ -248,6 +266,7 @@ sn_status sn_create(const sn_camera* cam, int W, int H, const sn_params* pin, sn
     g.K_cd = kfix(p.k_cd);
     g.K_pair = kfix(p.k_pair);
     g.K_range = kfix(p.k_range);
+    sn::cd_band(g.K_cd, &g.cd_hi, &g.cd_lo);
     g.normal_fmt = p.normal_fmt;
     g.fx = (float)cam->fx;
     g.fy = (float)cam->fy;
@@ -374,15 +393,21 @@ sn_status sn_run_frame(sn_ctx* c, const sn_frame_in* in, sn_frame_out* out, sn_s
         mk.n = 1;
         c->prof_frames++;
     }
-    cudaError_t e = sn::launch_denoise(c->geo, in->disp, in->disp_pitch, den, denp, out->mask, out->mask_pitch, stream, mk);
-    if (e == cudaSuccess)
-        e = sn::launch_affine(c->geo, c->star, in->disp, in->disp_pitch, den, denp, out->normals, out->normals_pitch,
-                              out->mask, out->mask_pitch, true, stream, mk);
-    if (e == cudaSuccess)
-        e = sn::launch_points(c->geo, den, denp, out->mask, out->mask_pitch, out->points, out->points_pitch, stream, mk);
-    if (e == cudaSuccess)
-        e = sn::launch_components(c->geo, in->disp, in->disp_pitch, out->labels, out->labels_pitch,
-                                  out->num_components, stream, mk);
+    sn::FrameOut fo;
+    fo.den = out->den;
+    fo.denp = out->den_pitch;
+    fo.nrm = out->normals;
+    fo.np = out->normals_pitch;
+    fo.pts = out->points;
+    fo.pp = out->points_pitch;
+    fo.labels = out->labels;
+    fo.lp = out->labels_pitch;
+    fo.mask = out->mask;
+    fo.mp = out->mask_pitch;
+    fo.count = out->num_components;
+    (void)den;
+    (void)denp;
+    cudaError_t e = sn::launch_frame(c->geo, c->star, c->star8, in->disp, in->disp_pitch, fo, stream, mk);
     c->launches += mk.launches;
     return e == cudaSuccess ? SN_OK : cuda_fail(c, e, "sn_run_frame");
 }

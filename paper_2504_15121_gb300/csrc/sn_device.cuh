@@ -173,26 +173,26 @@ __device__ __forceinline__ void star_support(const int* c, int TWR, int Dc, int 
     }
 }
 
-// Solves the 2x2 system of pass 2 (anchored at the denoised centre, dtil in
-// pixels) and turns (g_u, g_v) into the camera-facing unit normal.
-// Returns false if the support does not determine the gradient.
-__device__ __forceinline__ bool solve_normal(const AffSums& s, int Dc, float dtil, int x, int y,
-                                             const Geo& g, float n[3], bool& fp64) {
+// Solves the 2x2 system of pass 2 and turns (g_u, g_v) into the
+// camera-facing unit normal.  The data sums are anchored at the integer
+// centre Dc; the anchor shift to the denoised centre (dcf in FP32, dcd in
+// FP64, both in code units) enters through the first moments only.  dtil is
+// the denoised disparity in pixels.  Returns false if the support does not
+// determine the gradient.
+__device__ __forceinline__ bool solve_normal_dc(const AffSums& s, int Dc, float dcf, double dcd, float dtil,
+                                                int x, int y, const Geo& g, float n[3], bool& fp64) {
     fp64 = false;
     if (s.N < 3) return false;
     const long long a = s.Suu, b = s.Suv, gm = s.Svv;
     const long long det = a * gm - b * b;
     if (det <= 0) return false;
     fp64 = 1024ll * det < a * gm;
-    // exact parts of gamma b_u - beta b_v and alpha b_v - beta b_u with the
-    // data anchored at the integer centre; the anchor shift to dtil enters
-    // through the (small) first moments only
+    // exact parts of gamma b_u - beta b_v and alpha b_v - beta b_u
     const long long nu_i = gm * s.Bu - b * s.Bv;
     const long long nv_i = a * s.Bv - b * s.Bu;
     const long long cu = gm * s.Su - b * s.Sv;
     const long long cv = a * s.Sv - b * s.Su;
     if (!fp64) {
-        const float dcf = dtil * 256.0f - (float)Dc;
         const float inv = 1.0f / (256.0f * (float)det);
         const float gu = fmaf(-dcf, (float)cu, (float)nu_i) * inv;
         const float gv = fmaf(-dcf, (float)cv, (float)nv_i) * inv;
@@ -204,11 +204,10 @@ __device__ __forceinline__ bool solve_normal(const AffSums& s, int Dc, float dti
         n[1] = -my * r;
         n[2] = -mz * r;
     } else {
-        const double dd = (double)dtil;
-        const double dcf = dd * 256.0 - (double)Dc;
+        const double dd = ((double)Dc + dcd) * (1.0 / 256.0);
         const double inv = 1.0 / (256.0 * (double)det);
-        const double gu = ((double)nu_i - dcf * (double)cu) * inv;
-        const double gv = ((double)nv_i - dcf * (double)cv) * inv;
+        const double gu = ((double)nu_i - dcd * (double)cu) * inv;
+        const double gv = ((double)nv_i - dcd * (double)cv) * inv;
         const double mx = gu;
         const double my = gv * g.dfy / g.dfx;
         const double mz = (dd - gu * ((double)x - g.dcx) - gv * ((double)y - g.dcy)) / g.dfx;
@@ -218,6 +217,14 @@ __device__ __forceinline__ bool solve_normal(const AffSums& s, int Dc, float dti
         n[2] = (float)(-mz * r);
     }
     return true;
+}
+
+// Same, with the anchor taken from a denoised disparity dtil (pixels).
+__device__ __forceinline__ bool solve_normal(const AffSums& s, int Dc, float dtil, int x, int y,
+                                             const Geo& g, float n[3], bool& fp64) {
+    const float dcf = dtil * 256.0f - (float)Dc;
+    const double dcd = (double)dtil * 256.0 - (double)Dc;
+    return solve_normal_dc(s, Dc, dcf, dcd, dtil, x, y, g, n, fp64);
 }
 
 __device__ __forceinline__ short snorm16(float v) {

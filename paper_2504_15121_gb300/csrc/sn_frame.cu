@@ -1,0 +1,355 @@
+// Fused frame kernel: one pass over 32 x 16 pixel tiles computes the
+// denoised disparity, the support (fixed window or star-fill), the affine
+// fit, the normal, the point, the mask and the tile-local component labels.
+// The tile and its halo are staged once in shared memory as (D, 1/D) pairs:
+// D is the exact integer disparity code used by every sum and decision,
+// 1/D (FP32, correctly rounded; +inf for invalid) carries the covered-depth
+// test, which in reciprocal form reads 1/Dmin - 1/Dmax > K / (2^16 Dc).
+#include "sn_device.cuh"
+
+namespace sn {
+
+namespace {
+
+constexpr int kTW = kFrameTW, kTH = kFrameTH, kThreads = kTW * kTH;
+
+// distinct pixels of an M = 8 diagonal ray of s steps: round(s / sqrt 2),
+// i.e. the r with (2r - 1)^2 < 2 s^2 < (2r + 1)^2
+__host__ __device__ constexpr int diag_len(int s) {
+    int r = 0;
+    while ((2 * r + 1) * (2 * r + 1) < 2 * s * s) r++;
+    return r;
+}
+
+// Covered-depth thresholds of one centre pixel.  `hi`/`lo` bracket the exact
+// threshold K / (2^16 Dc) by the worst-case rounding of the FP32 reciprocals:
+// above hi the exact test surely stops the ray, below lo it surely does not,
+// in between the exact integer test decides.
+struct Thr {
+    float hi, lo;
+    int K;
+};
+
+__device__ __forceinline__ Thr make_thr(const Geo& g, int Dc) {
+    Thr t;
+    t.K = g.K_cd;
+    if (g.K_cd == 0) {
+        t.hi = 0.0f;                          // any spread stops; zero spread never
+        t.lo = __int_as_float(0x7f800000);
+    } else {
+        const float thr = __fdiv_rn((float)g.K_cd * (1.0f / 65536.0f), (float)Dc);
+        t.hi = thr * g.cd_hi;
+        t.lo = thr * g.cd_lo;
+    }
+    return t;
+}
+
+// Exact decision from the two extreme reciprocals (w = fl(1/D) with
+// D < 2^17, so rint(1/w) recovers D exactly).
+__device__ __noinline__ bool cd_stop_from_w(float wlo, float whi, int Dc, int K) {
+    const int Dmax = __float2int_rn(__frcp_rn(wlo));
+    const int Dmin = __float2int_rn(__frcp_rn(whi));
+    return cd_stop(Dmin, Dmax, Dc, K);
+}
+
+// One ray of the M = 8 star with direction (SU, SV) and L distinct pixels
+// t (SU, SV), t = 1..L.  The data enters as A = sum t D over the included
+// pixels; the moments of the included prefix 1..n are closed forms.
+template <int SU, int SV, int L, int STRIDE>
+__device__ __forceinline__ void ray8(const int2* __restrict__ c, int Dc, float wc, const Thr& th, AffSums& s) {
+    float wlo = wc, whi = wc;
+    int A = 0, n = 0;
+#pragma unroll
+    for (int t = 1; t <= L; t++) {
+        const int2 e = c[(SV * t) * STRIDE + SU * t];
+        const float w = __int_as_float(e.y);
+        const float lo = fminf(wlo, w), hi = fmaxf(whi, w);
+        const float diff = hi - lo;
+        if (diff > th.hi) break;
+        if (diff >= th.lo && cd_stop_from_w(lo, hi, Dc, th.K)) break;
+        wlo = lo;
+        whi = hi;
+        A += t * e.x;
+        n = t;
+    }
+    const int T1 = (n * (n + 1)) >> 1;
+    const int T2 = (n * (n + 1) * (2 * n + 1)) / 6;
+    const int Ad = A - Dc * T1;
+    s.N += n;
+    if (SU != 0) {
+        s.Su += SU * T1;
+        s.Suu += T2;
+        s.Bu += SU * Ad;
+    }
+    if (SV != 0) {
+        s.Sv += SV * T1;
+        s.Svv += T2;
+        s.Bv += SV * Ad;
+    }
+    if (SU != 0 && SV != 0) s.Suv += SU * SV * T2;
+}
+
+template <int S, int STRIDE>
+__device__ __forceinline__ void star8(const int2* c, int Dc, float wc, const Thr& th, AffSums& s) {
+    constexpr int LD = diag_len(S);
+    aff_zero(s);
+    ray8<1, 0, S, STRIDE>(c, Dc, wc, th, s);
+    ray8<1, 1, LD, STRIDE>(c, Dc, wc, th, s);
+    ray8<0, 1, S, STRIDE>(c, Dc, wc, th, s);
+    ray8<-1, 1, LD, STRIDE>(c, Dc, wc, th, s);
+    ray8<-1, 0, S, STRIDE>(c, Dc, wc, th, s);
+    ray8<-1, -1, LD, STRIDE>(c, Dc, wc, th, s);
+    ray8<0, -1, S, STRIDE>(c, Dc, wc, th, s);
+    ray8<1, -1, LD, STRIDE>(c, Dc, wc, th, s);
+}
+
+// Any star table (union of rays, see StarTable), on the packed tile.
+__device__ __forceinline__ void star_table(const int2* c, int stride, int Dc, float wc, const Thr& th,
+                                           const StarTable& T, int dirs, int steps, AffSums& s) {
+    aff_zero(s);
+    unsigned long long bits = 0ull;
+    for (int j = 0; j < dirs; j++) {
+        float wlo = wc, whi = wc;
+        const int e0 = j * steps;
+        for (int k = 0; k < steps; k++) {
+            const int e = e0 + k;
+            const int cls = T.cls[e];
+            if (cls == 0) continue;
+            const int ou = T.ou[e], ov = T.ov[e];
+            const int2 v = c[ov * stride + ou];
+            const float w = __int_as_float(v.y);
+            const float lo = fminf(wlo, w), hi = fmaxf(whi, w);
+            const float diff = hi - lo;
+            if (diff > th.hi) break;
+            if (diff >= th.lo && cd_stop_from_w(lo, hi, Dc, th.K)) break;
+            wlo = lo;
+            whi = hi;
+            if (cls == 1)
+                aff_add(s, ou, ov, v.x - Dc);
+            else
+                bits |= 1ull << T.bit[e];
+        }
+    }
+    for (int b = 0; b < T.nshared; b++) {
+        if ((bits >> b) & 1ull) {
+            const int ou = T.sou[b], ov = T.sov[b];
+            aff_add(s, ou, ov, c[ov * stride + ou].x - Dc);
+        }
+    }
+}
+
+__device__ __forceinline__ void fixed_packed(const int2* c, int stride, int R, int Dc, AffSums& s) {
+    aff_zero(s);
+    for (int ov = -R; ov <= R; ov++) {
+        const int2* row = c + ov * stride;
+        for (int ou = -R; ou <= R; ou++) {
+            const int Di = row[ou].x;
+            if (Di > 0 && (ou | ov) != 0) aff_add(s, ou, ov, Di - Dc);
+        }
+    }
+}
+
+// Denoise with exact intercept: returns fit and (num, det) with
+// intercept = Dc + num / det (integer codes).  RD > 0 fixes the radius at
+// compile time.
+template <int RD>
+__device__ __forceinline__ bool denoise_exact(const int2* c, int stride, int rd_rt, int Dc, int K_range,
+                                              long long& num, long long& det) {
+    const int R = RD > 0 ? RD : rd_rt;
+    // -lo <= dd <= thr with lo = min(thr, Dc - 1): an invalid sample
+    // (D = 0, dd = -Dc) never passes, whatever K_range is
+    const int thr = (int)(((unsigned long long)(unsigned)K_range * (unsigned)Dc) >> 16);
+    const int lo = min(thr, Dc - 1);
+    const unsigned span = (unsigned)lo + (unsigned)thr;
+    int n = 0, Su = 0, Sv = 0, Suu = 0, Suv = 0, Svv = 0, b0 = 0, b1 = 0, b2 = 0;
+#pragma unroll
+    for (int ov = -R; ov <= R; ov++) {
+#pragma unroll
+        for (int ou = -R; ou <= R; ou++) {
+            const int dd = c[ov * stride + ou].x - Dc;
+            if ((unsigned)(dd + lo) <= span) {
+                n++;
+                Su += ou;
+                Sv += ov;
+                Suu += ou * ou;
+                Suv += ou * ov;
+                Svv += ov * ov;
+                b0 += dd;
+                b1 += ou * dd;
+                b2 += ov * dd;
+            }
+        }
+    }
+    const long long M00 = (long long)Suu * Svv - (long long)Suv * Suv;
+    const long long M10 = (long long)Su * Svv - (long long)Sv * Suv;
+    const long long M20 = (long long)Su * Suv - (long long)Sv * Suu;
+    det = n * M00 - Su * M10 + Sv * M20;
+    num = b0 * M00 - b1 * M10 + b2 * M20;
+    return det > 0 && (long long)Dc * det + num > 0;
+}
+
+// VAR: 0 fixed window, 1 star table, 2 compile-time M = 8, s = 10 star.
+// R: halo radius at compile time (0 = runtime).  RD: denoise radius (0 = runtime).
+template <int IN, int VAR, int R, int RD>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_frame(const Geo g, const __grid_constant__ StarTable T, const char* __restrict__ disp, size_t dp,
+            const FrameOut o) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : g.steps);
+    const int TWR = kTW + 2 * Rr, THR = kTH + 2 * Rr;
+    int2* tile = reinterpret_cast<int2*>(smem);
+    int* Ls = reinterpret_cast<int*>(smem + sizeof(int2) * (size_t)TWR * THR);
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+    const int tid = threadIdx.y * kTW + threadIdx.x;
+    if (o.count && (blockIdx.x | blockIdx.y | tid) == 0) *o.count = 0;
+
+    // ---- stage the tile and its halo: (D, 1/D)
+    const int n = TWR * THR;
+    for (int i = tid; i < n; i += kThreads) {
+        const int ly = i / TWR;
+        const int lx = i - ly * TWR;
+        const int D = load_code<IN>(disp, dp, x0 - Rr + lx, y0 - Rr + ly, g.W, g.H);
+        const float w = D > 0 ? __frcp_rn((float)D) : __int_as_float(0x7f800000);
+        tile[i] = make_int2(D, __float_as_int(w));
+    }
+    __syncthreads();
+
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const bool inside = x < g.W && y < g.H;
+    const int2* c = tile + (threadIdx.y + Rr) * TWR + threadIdx.x + Rr;
+    const int2 cc = c[0];
+    const int Dc = cc.x;  // 0 outside the image
+    Ls[tid] = Dc > 0 ? tid : -1;
+
+    if (inside) {
+        float nrm[3] = {0.0f, 0.0f, 0.0f};
+        float P[3] = {0.0f, 0.0f, 0.0f};
+        float dtil = 0.0f;
+        uint8_t m = 0;
+        if (Dc > 0) {
+            m = SN_MASK_VALID;
+            long long num, det;
+            const bool fit = denoise_exact<RD>(c, TWR, g.r_d, Dc, g.K_range, num, det);
+            const float dcf = fit ? (float)num / (float)det : 0.0f;
+            if (fit) m |= SN_MASK_DENOISED;
+            dtil = ((float)Dc + dcf) * (1.0f / 256.0f);
+            AffSums s;
+            if constexpr (VAR == 2) {
+                static_assert(R == 10, "the M = 8, s = 10 star needs a halo of 10");
+                star8<10, kTW + 2 * R>(c, Dc, __int_as_float(cc.y), make_thr(g, Dc), s);
+            } else if constexpr (VAR == 1) {
+                star_table(c, TWR, Dc, __int_as_float(cc.y), make_thr(g, Dc), T, g.dirs, g.steps, s);
+            } else {
+                fixed_packed(c, TWR, g.r_a, Dc, s);
+            }
+            bool fp64;
+            const double dcd = fit ? (double)num / (double)det : 0.0;
+            if (solve_normal_dc(s, Dc, dcf, dcd, dtil, x, y, g, nrm, fp64))
+                m |= SN_MASK_NORMAL | (fp64 ? SN_MASK_FP64 : 0);
+            P[0] = g.B * ((float)x - g.cx) / dtil;
+            P[1] = g.B_fx_over_fy * ((float)y - g.cy) / dtil;
+            P[2] = g.fxB / dtil;
+        }
+        if (o.den) reinterpret_cast<float*>(reinterpret_cast<char*>(o.den) + (size_t)y * o.denp)[x] = dtil;
+        if (g.normal_fmt == SN_NORMALS_F32X3) {
+            char* p0 = static_cast<char*>(o.nrm) + (size_t)y * o.np + (size_t)x * 4;
+            const size_t plane = (size_t)g.H * o.np;
+            *reinterpret_cast<float*>(p0) = nrm[0];
+            *reinterpret_cast<float*>(p0 + plane) = nrm[1];
+            *reinterpret_cast<float*>(p0 + 2 * plane) = nrm[2];
+        } else {
+            short4 q;
+            q.x = snorm16(nrm[0]);
+            q.y = snorm16(nrm[1]);
+            q.z = snorm16(nrm[2]);
+            q.w = 0;
+            reinterpret_cast<short4*>(static_cast<char*>(o.nrm) + (size_t)y * o.np)[x] = q;
+        }
+        {
+            char* p0 = reinterpret_cast<char*>(o.pts) + (size_t)y * o.pp + (size_t)x * 4;
+            const size_t plane = (size_t)g.H * o.pp;
+            *reinterpret_cast<float*>(p0) = P[0];
+            *reinterpret_cast<float*>(p0 + plane) = P[1];
+            *reinterpret_cast<float*>(p0 + 2 * plane) = P[2];
+        }
+        o.mask[(size_t)y * o.mp + x] = m;
+    }
+
+    // ---- tile-local components (union-find over the tile's own pixels)
+    __syncthreads();
+    if (Dc > 0) {
+        if (threadIdx.x + 1 < kTW && pair_edge(Dc, c[1].x, g.K_pair)) union_s(Ls, tid, tid + 1, g.err);
+        if (threadIdx.y + 1 < kTH && pair_edge(Dc, c[TWR].x, g.K_pair)) union_s(Ls, tid, tid + kTW, g.err);
+    }
+    __syncthreads();
+    if (inside) {
+        int lab = -1;
+        if (Dc > 0) {
+            const int r = find_s(Ls, tid);
+            lab = (y0 + r / kTW) * g.W + x0 + (r % kTW);
+        }
+        o.labels[(size_t)y * (o.lp / 4) + x] = lab;
+    }
+}
+
+template <int VAR, int R, int RD>
+cudaError_t launch_var(const Geo& g, const StarTable& t, const void* disp, size_t dp, const FrameOut& o,
+                       cudaStream_t s) {
+    const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : g.steps);
+    const size_t smem = sizeof(int2) * (size_t)(kTW + 2 * Rr) * (kTH + 2 * Rr) + sizeof(int) * kThreads;
+    const dim3 grid((g.W + kTW - 1) / kTW, (g.H + kTH - 1) / kTH), block(kTW, kTH);
+    const char* d = static_cast<const char*>(disp);
+    cudaError_t e = cudaSuccess;
+    switch (g.in_dtype) {
+        case SN_IN_F32:
+            e = cudaFuncSetAttribute(k_frame<SN_IN_F32, VAR, R, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) k_frame<SN_IN_F32, VAR, R, RD><<<grid, block, smem, s>>>(g, t, d, dp, o);
+            break;
+        case SN_IN_F16:
+            e = cudaFuncSetAttribute(k_frame<SN_IN_F16, VAR, R, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) k_frame<SN_IN_F16, VAR, R, RD><<<grid, block, smem, s>>>(g, t, d, dp, o);
+            break;
+        default:
+            e = cudaFuncSetAttribute(k_frame<SN_IN_U16X256, VAR, R, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) k_frame<SN_IN_U16X256, VAR, R, RD><<<grid, block, smem, s>>>(g, t, d, dp, o);
+            break;
+    }
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+}  // namespace
+
+bool star_is_m8(const StarTable& t, int dirs, int steps) {
+    if (dirs != 8 || steps != 10) return false;
+    const int su[8] = {1, 1, 0, -1, -1, -1, 0, 1};
+    const int sv[8] = {0, 1, 1, 1, 0, -1, -1, -1};
+    const int len[8] = {10, diag_len(10), 10, diag_len(10), 10, diag_len(10), 10, diag_len(10)};
+    for (int j = 0; j < 8; j++) {
+        int tpos = 0;
+        for (int k = 0; k < steps; k++) {
+            const int e = j * steps + k;
+            if (t.cls[e] == 0) continue;
+            if (t.cls[e] != 1) return false;
+            tpos++;
+            if (t.ou[e] != su[j] * tpos || t.ov[e] != sv[j] * tpos) return false;
+        }
+        if (tpos != len[j]) return false;
+    }
+    return true;
+}
+
+cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const void* disp, size_t dp,
+                         const FrameOut& o, cudaStream_t s, Marks& mk) {
+    cudaError_t e;
+    if (g.support == SN_SUPPORT_STARFILL_CD && star8)
+        e = g.r_d == 2 ? launch_var<2, 10, 2>(g, t, disp, dp, o, s) : launch_var<2, 10, 0>(g, t, disp, dp, o, s);
+    else if (g.support == SN_SUPPORT_STARFILL_CD)
+        e = launch_var<1, 0, 0>(g, t, disp, dp, o, s);
+    else
+        e = launch_var<0, 0, 0>(g, t, disp, dp, o, s);
+    mk.after(s);
+    if (e != cudaSuccess) return e;
+    return launch_ccl_merge_flatten(g, disp, dp, o.labels, o.lp, o.count, kTW, kTH, s, mk);
+}
+
+}  // namespace sn

@@ -26,6 +26,8 @@ struct Geo {
     int in_dtype;
     int r_d, r_a, support, dirs, steps;
     int K_cd, K_pair, K_range;
+    // relative guard band of the FP32 covered-depth test (1 + e, 1 - e)
+    float cd_hi, cd_lo;
     int normal_fmt;
     float fx, fy, cx, cy, B;
     float fy_over_fx, inv_fx, B_fx_over_fy, fxB;
@@ -67,6 +69,10 @@ struct Marks {
     }
 };
 
+// Guard band factors (1 + e, 1 - e) of the FP32 reciprocal covered-depth test
+// for K = rint(2^16 k).
+void cd_band(int K, float* hi, float* lo);
+
 // Checks camera, size and parameters and fills the kernel constants without
 // touching the device.
 sn_status prepare_constants(const sn_camera* cam, int W, int H, const sn_params* p, Geo* g, StarTable* t);
@@ -82,5 +88,32 @@ cudaError_t launch_points(const Geo& g, const float* den, size_t denp, const uin
 // three stage slots: tile-local union-find, border merge, flatten
 cudaError_t launch_components(const Geo& g, const void* disp, size_t dp, int32_t* labels,
                               size_t lp, int32_t* count, cudaStream_t s, Marks& mk);
+// two stage slots: border merge between tw x th tiles, flatten
+cudaError_t launch_ccl_merge_flatten(const Geo& g, const void* disp, size_t dp, int32_t* labels,
+                                     size_t lp, int32_t* count, int tw, int th, cudaStream_t s,
+                                     Marks& mk);
+
+// Fused frame kernel (denoise, support, affine, normal, points, mask and
+// tile-local components in one pass over 32 x 16 tiles).  Star-fill with
+// M = 8, s = 10 uses compile-time rays when `star8` is set (the host checks
+// that the context's table is exactly that ray set).
+struct FrameOut {
+    float* den;  // may be null
+    size_t denp;
+    void* nrm;
+    size_t np;
+    float* pts;
+    size_t pp;
+    int32_t* labels;
+    size_t lp;
+    uint8_t* mask;
+    size_t mp;
+    int32_t* count;
+};
+constexpr int kFrameTW = 32;
+constexpr int kFrameTH = 16;
+cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const void* disp, size_t dp,
+                         const FrameOut& o, cudaStream_t s, Marks& mk);
+bool star_is_m8(const StarTable& t, int dirs, int steps);
 
 }  // namespace sn

@@ -146,24 +146,26 @@ __global__ void __launch_bounds__(kCclTile * 8)
 }
 
 // Pass 2: join components across tile borders (global atomicMin union).
+// Tiles are tw x th pixels; thread t handles one 4-neighbour pair that
+// straddles a vertical (x = k tw) or horizontal (y = k th) tile border.
 template <int IN>
 __global__ void __launch_bounds__(256)
     k_ccl_merge(const Geo g, const char* __restrict__ disp, size_t dp, int* labels, size_t lpe,
-                int nbx, int nby) {
+                int nbx, int nby, int tw, int th) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nV = (long long)(nbx - 1) * g.H;
     int px, py, qx, qy;
     if (t < nV) {
         const int k = (int)(t / g.H) + 1;
         py = qy = (int)(t - (long long)(k - 1) * g.H);
-        qx = k * kCclTile;
+        qx = k * tw;
         px = qx - 1;
     } else {
         const long long t2 = t - nV;
         if (t2 >= (long long)(nby - 1) * g.W) return;
         const int k = (int)(t2 / g.W) + 1;
         px = qx = (int)(t2 - (long long)(k - 1) * g.W);
-        qy = k * kCclTile;
+        qy = k * th;
         py = qy - 1;
     }
     const int Dp = load_code<IN>(disp, dp, px, py, g.W, g.H);
@@ -238,13 +240,31 @@ cudaError_t launch_points(const Geo& g, const float* den, size_t denp, const uin
     return cudaGetLastError();
 }
 
+cudaError_t launch_ccl_merge_flatten(const Geo& g, const void* disp, size_t dp, int32_t* labels, size_t lp,
+                                     int32_t* count, int tw, int th, cudaStream_t s, Marks& mk) {
+    const int nbx = (g.W + tw - 1) / tw, nby = (g.H + th - 1) / th;
+    const size_t lpe = lp / sizeof(int32_t);
+    const char* d = static_cast<const char*>(disp);
+    const long long pairs = (long long)(nbx - 1) * g.H + (long long)(nby - 1) * g.W;
+    const unsigned mblocks = (unsigned)((pairs + 255) / 256);
+    if (pairs > 0) {
+        switch (g.in_dtype) {
+            case SN_IN_F32: k_ccl_merge<SN_IN_F32><<<mblocks, 256, 0, s>>>(g, d, dp, labels, lpe, nbx, nby, tw, th); break;
+            case SN_IN_F16: k_ccl_merge<SN_IN_F16><<<mblocks, 256, 0, s>>>(g, d, dp, labels, lpe, nbx, nby, tw, th); break;
+            default: k_ccl_merge<SN_IN_U16X256><<<mblocks, 256, 0, s>>>(g, d, dp, labels, lpe, nbx, nby, tw, th); break;
+        }
+    }
+    mk.after(s, pairs > 0);
+    k_ccl_flatten<<<grid2(g), dim3(kTW, kTH), 0, s>>>(g, labels, lpe, count);
+    mk.after(s);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_components(const Geo& g, const void* disp, size_t dp, int32_t* labels, size_t lp,
                               int32_t* count, cudaStream_t s, Marks& mk) {
     const int nbx = (g.W + kCclTile - 1) / kCclTile, nby = (g.H + kCclTile - 1) / kCclTile;
     const size_t lpe = lp / sizeof(int32_t);
     const char* d = static_cast<const char*>(disp);
-    const long long pairs = (long long)(nbx - 1) * g.H + (long long)(nby - 1) * g.W;
-    const unsigned mblocks = (unsigned)((pairs + 255) / 256);
     const dim3 lg(nbx, nby), lb(kCclTile, 8);
     switch (g.in_dtype) {
         case SN_IN_F32: k_ccl_local<SN_IN_F32><<<lg, lb, 0, s>>>(g, d, dp, labels, lpe, count); break;
@@ -252,17 +272,9 @@ cudaError_t launch_components(const Geo& g, const void* disp, size_t dp, int32_t
         default: k_ccl_local<SN_IN_U16X256><<<lg, lb, 0, s>>>(g, d, dp, labels, lpe, count); break;
     }
     mk.after(s);
-    if (pairs > 0) {
-        switch (g.in_dtype) {
-            case SN_IN_F32: k_ccl_merge<SN_IN_F32><<<mblocks, 256, 0, s>>>(g, d, dp, labels, lpe, nbx, nby); break;
-            case SN_IN_F16: k_ccl_merge<SN_IN_F16><<<mblocks, 256, 0, s>>>(g, d, dp, labels, lpe, nbx, nby); break;
-            default: k_ccl_merge<SN_IN_U16X256><<<mblocks, 256, 0, s>>>(g, d, dp, labels, lpe, nbx, nby); break;
-        }
-    }
-    mk.after(s, pairs > 0);
-    k_ccl_flatten<<<grid2(g), dim3(kTW, kTH), 0, s>>>(g, labels, lpe, count);
-    mk.after(s);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_ccl_merge_flatten(g, disp, dp, labels, lp, count, kCclTile, kCclTile, s, mk);
 }
 
 }  // namespace sn

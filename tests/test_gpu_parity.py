@@ -136,6 +136,8 @@ def test_constant_and_planes(P):
     dict(support=0, r_affine=15),
     dict(r_denoise=1, k_range=0.01),
     dict(r_denoise=4, k_range=0.2),
+    dict(r_denoise=3, k_range=1.0, k_cd=1.0),
+    dict(k_cd=0.0),
     dict(k_pair=0.0),
     dict(k_pair=1.0),
 ])
