@@ -112,10 +112,12 @@ bool build_star(int M, int s, sn::StarTable& T) {
 
 namespace sn {
 
-// With w = fl(1/D) and thr = fl(K 2^-16 / Dc), the computed spread
-// fl(w_hi - w_lo) differs from 1/Dmin - 1/Dmax by at most
-// 2^-24 (2 (1 + kappa) / kappa + 2) thr near the threshold (kappa = K/2^16;
-// near the threshold Dmin >= Dc / (1 + kappa)).  The band is four times that.
+// With w within 1 ulp (2^-23 relative) of 1/D and thr = fl(K 2^-16 / Dc),
+// the computed spread fl(w_hi - w_lo) differs from 1/Dmin - 1/Dmax by at
+// most 2^-23 (1/Dmin + 1/Dmax) + 2^-24 (spread + thr).  Near the threshold
+// (spread ~ thr = kappa / Dc with kappa = K / 2^16) Dmin >= Dc / (1 + kappa),
+// so the error is at most thr 2^-23 (2 (1 + kappa) / kappa + 1).  The band
+// is four times that.
 void cd_band(int K, float* hi, float* lo) {
     if (K <= 0) {
         *hi = 1.0f;
@@ -123,7 +125,7 @@ void cd_band(int K, float* hi, float* lo) {
         return;
     }
     const double kappa = K / 65536.0;
-    const double e = 4.0 * ldexp(1.0, -24) * (2.0 * (1.0 + kappa) / kappa + 2.0);
+    const double e = 4.0 * ldexp(1.0, -23) * (2.0 * (1.0 + kappa) / kappa + 1.0);
     *hi = (float)(1.0 + e);
     *lo = (float)(1.0 - e);
 }

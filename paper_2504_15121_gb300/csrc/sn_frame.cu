@@ -44,33 +44,49 @@ __device__ __forceinline__ Thr make_thr(const Geo& g, int Dc) {
     return t;
 }
 
-// Exact decision from the two extreme reciprocals (w = fl(1/D) with
-// D < 2^17, so rint(1/w) recovers D exactly).
+// Reciprocal with at most 1 ulp error (PTX rcp.approx); the inputs are
+// integer codes 1..131071, never denormal.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Exact decision from the two extreme reciprocals: w is within 1 ulp of 1/D
+// and D < 2^17, so rint(1/w) recovers D exactly.
 __device__ __noinline__ bool cd_stop_from_w(float wlo, float whi, int Dc, int K) {
-    const int Dmax = __float2int_rn(__frcp_rn(wlo));
-    const int Dmin = __float2int_rn(__frcp_rn(whi));
+    const int Dmax = __float2int_rn(rcp_approx(wlo));
+    const int Dmin = __float2int_rn(rcp_approx(whi));
     return cd_stop(Dmin, Dmax, Dc, K);
 }
 
 // One ray of the M = 8 star with direction (SU, SV) and L distinct pixels
-// t (SU, SV), t = 1..L.  The data enters as A = sum t D over the included
-// pixels; the moments of the included prefix 1..n are closed forms.
+// t (SU, SV), t = 1..L.  All L samples are loaded first; the walk is
+// predicated (a ray stays stopped once stopped) and branches only when the
+// spread falls inside the rounding band, where the exact test decides.  The
+// data enters as A = sum t D over the included pixels; the moments of the
+// included prefix 1..n are closed forms.
 template <int SU, int SV, int L, int STRIDE>
 __device__ __forceinline__ void ray8(const int2* __restrict__ c, int Dc, float wc, const Thr& th, AffSums& s) {
+    int2 e[L];
+#pragma unroll
+    for (int t = 1; t <= L; t++) e[t - 1] = c[(SV * t) * STRIDE + SU * t];
     float wlo = wc, whi = wc;
     int A = 0, n = 0;
+    bool alive = true;
 #pragma unroll
     for (int t = 1; t <= L; t++) {
-        const int2 e = c[(SV * t) * STRIDE + SU * t];
-        const float w = __int_as_float(e.y);
-        const float lo = fminf(wlo, w), hi = fmaxf(whi, w);
-        const float diff = hi - lo;
-        if (diff > th.hi) break;
-        if (diff >= th.lo && cd_stop_from_w(lo, hi, Dc, th.K)) break;
-        wlo = lo;
-        whi = hi;
-        A += t * e.x;
-        n = t;
+        const float w = __int_as_float(e[t - 1].y);
+        wlo = fminf(wlo, w);
+        whi = fmaxf(whi, w);
+        const float diff = whi - wlo;
+        bool stop = diff > th.hi;
+        if (alive && !stop && diff >= th.lo) stop = cd_stop_from_w(wlo, whi, Dc, th.K);
+        alive = alive && !stop;
+        if (alive) {
+            A += t * e[t - 1].x;
+            n = t;
+        }
     }
     const int T1 = (n * (n + 1)) >> 1;
     const int T2 = (n * (n + 1) * (2 * n + 1)) / 6;
@@ -152,6 +168,20 @@ __device__ __forceinline__ void fixed_packed(const int2* c, int stride, int R, i
 // Denoise with exact intercept: returns fit and (num, det) with
 // intercept = Dc + num / det (integer codes).  RD > 0 fixes the radius at
 // compile time.
+// bit (ov + 2) 5 + (ou + 2) of a 5x5 pass mask is set where q(ou, ov) == val,
+// q = ou (kind 0), ov (kind 1) or ou ov (kind 2)
+__host__ __device__ constexpr unsigned mask5(int kind, int val) {
+    unsigned m = 0;
+    for (int ov = -2; ov <= 2; ov++)
+        for (int ou = -2; ou <= 2; ou++) {
+            const int q = kind == 0 ? ou : (kind == 1 ? ov : ou * ov);
+            if (q == val) m |= 1u << ((ov + 2) * 5 + (ou + 2));
+        }
+    return m;
+}
+
+__device__ __forceinline__ int popc_and(unsigned m, unsigned k) { return __popc(m & k); }
+
 template <int RD>
 __device__ __forceinline__ bool denoise_exact(const int2* c, int stride, int rd_rt, int Dc, int K_range,
                                               long long& num, long long& det) {
@@ -162,6 +192,42 @@ __device__ __forceinline__ bool denoise_exact(const int2* c, int stride, int rd_
     const int lo = min(thr, Dc - 1);
     const unsigned span = (unsigned)lo + (unsigned)thr;
     int n = 0, Su = 0, Sv = 0, Suu = 0, Suv = 0, Svv = 0, b0 = 0, b1 = 0, b2 = 0;
+    if constexpr (RD == 2) {
+        // 5x5: record the passing samples in a bit mask and take the moments
+        // from population counts of column, row and product classes
+        unsigned m = 0;
+#pragma unroll
+        for (int ov = -2; ov <= 2; ov++) {
+#pragma unroll
+            for (int ou = -2; ou <= 2; ou++) {
+                const int dd = c[ov * stride + ou].x - Dc;
+                if ((unsigned)(dd + lo) <= span) {
+                    m |= 1u << ((ov + 2) * 5 + (ou + 2));
+                    b0 += dd;
+                    b1 += ou * dd;
+                    b2 += ov * dd;
+                }
+            }
+        }
+        n = __popc(m);
+        const int um2 = popc_and(m, mask5(0, -2)), um1 = popc_and(m, mask5(0, -1));
+        const int up1 = popc_and(m, mask5(0, 1)), up2 = popc_and(m, mask5(0, 2));
+        const int vm2 = popc_and(m, mask5(1, -2)), vm1 = popc_and(m, mask5(1, -1));
+        const int vp1 = popc_and(m, mask5(1, 1)), vp2 = popc_and(m, mask5(1, 2));
+        Su = 2 * (up2 - um2) + (up1 - um1);
+        Suu = 4 * (up2 + um2) + (up1 + um1);
+        Sv = 2 * (vp2 - vm2) + (vp1 - vm1);
+        Svv = 4 * (vp2 + vm2) + (vp1 + vm1);
+        Suv = (popc_and(m, mask5(2, 1)) - popc_and(m, mask5(2, -1))) +
+              2 * (popc_and(m, mask5(2, 2)) - popc_and(m, mask5(2, -2))) +
+              4 * (popc_and(m, mask5(2, 4)) - popc_and(m, mask5(2, -4)));
+        const long long M00 = (long long)Suu * Svv - (long long)Suv * Suv;
+        const long long M10 = (long long)Su * Svv - (long long)Sv * Suv;
+        const long long M20 = (long long)Su * Suv - (long long)Sv * Suu;
+        det = n * M00 - Su * M10 + Sv * M20;
+        num = b0 * M00 - b1 * M10 + b2 * M20;
+        return det > 0 && (long long)Dc * det + num > 0;
+    }
 #pragma unroll
     for (int ov = -R; ov <= R; ov++) {
 #pragma unroll
@@ -209,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int ly = i / TWR;
         const int lx = i - ly * TWR;
         const int D = load_code<IN>(disp, dp, x0 - Rr + lx, y0 - Rr + ly, g.W, g.H);
-        const float w = D > 0 ? __frcp_rn((float)D) : __int_as_float(0x7f800000);
+        const float w = D > 0 ? rcp_approx((float)D) : __int_as_float(0x7f800000);
         tile[i] = make_int2(D, __float_as_int(w));
     }
     __syncthreads();
@@ -246,9 +312,10 @@ __global__ void __launch_bounds__(kThreads, 2)
             const double dcd = fit ? (double)num / (double)det : 0.0;
             if (solve_normal_dc(s, Dc, dcf, dcd, dtil, x, y, g, nrm, fp64))
                 m |= SN_MASK_NORMAL | (fp64 ? SN_MASK_FP64 : 0);
-            P[0] = g.B * ((float)x - g.cx) / dtil;
-            P[1] = g.B_fx_over_fy * ((float)y - g.cy) / dtil;
-            P[2] = g.fxB / dtil;
+            const float inv = 1.0f / dtil;
+            P[0] = g.B * ((float)x - g.cx) * inv;
+            P[1] = g.B_fx_over_fy * ((float)y - g.cy) * inv;
+            P[2] = g.fxB * inv;
         }
         if (o.den) reinterpret_cast<float*>(reinterpret_cast<char*>(o.den) + (size_t)y * o.denp)[x] = dtil;
         if (g.normal_fmt == SN_NORMALS_F32X3) {
