@@ -173,14 +173,34 @@ __device__ __forceinline__ void star_support(const int* c, int TWR, int Dc, int 
     }
 }
 
+// FP64 solve for supports that trip the conditioning flag (rare; FP64 is a
+// slow pipe on this GPU, so nothing of it runs on the common path).
+__device__ __noinline__ void solve_normal_f64(long long nu_i, long long nv_i, long long cu, long long cv,
+                                              long long det, int Dc, double dcd, int x, int y, const Geo& g,
+                                              float n[3]) {
+    const double dd = ((double)Dc + dcd) * (1.0 / 256.0);
+    const double inv = 1.0 / (256.0 * (double)det);
+    const double gu = ((double)nu_i - dcd * (double)cu) * inv;
+    const double gv = ((double)nv_i - dcd * (double)cv) * inv;
+    const double mx = gu;
+    const double my = gv * g.dfy / g.dfx;
+    const double mz = (dd - gu * ((double)x - g.dcx) - gv * ((double)y - g.dcy)) / g.dfx;
+    const double r = 1.0 / sqrt(mx * mx + my * my + mz * mz);
+    n[0] = (float)(-mx * r);
+    n[1] = (float)(-my * r);
+    n[2] = (float)(-mz * r);
+}
+
 // Solves the 2x2 system of pass 2 and turns (g_u, g_v) into the
 // camera-facing unit normal.  The data sums are anchored at the integer
-// centre Dc; the anchor shift to the denoised centre (dcf in FP32, dcd in
-// FP64, both in code units) enters through the first moments only.  dtil is
-// the denoised disparity in pixels.  Returns false if the support does not
-// determine the gradient.
-__device__ __forceinline__ bool solve_normal_dc(const AffSums& s, int Dc, float dcf, double dcd, float dtil,
-                                                int x, int y, const Geo& g, float n[3], bool& fp64) {
+// centre Dc; the anchor shift to the denoised centre (dcf in FP32, and
+// anchor_f64() in FP64 when the conditioning flag trips, both in code units)
+// enters through the first moments only.  dtil is the denoised disparity in
+// pixels.  Returns false if the support does not determine the gradient.
+template <class AnchorF64>
+__device__ __forceinline__ bool solve_normal_dc(const AffSums& s, int Dc, float dcf, AnchorF64 anchor_f64,
+                                                float dtil, int x, int y, const Geo& g, float n[3],
+                                                bool& fp64) {
     fp64 = false;
     if (s.N < 3) return false;
     const long long a = s.Suu, b = s.Suv, gm = s.Svv;
@@ -192,7 +212,11 @@ __device__ __forceinline__ bool solve_normal_dc(const AffSums& s, int Dc, float 
     const long long nv_i = a * s.Bv - b * s.Bu;
     const long long cu = gm * s.Su - b * s.Sv;
     const long long cv = a * s.Sv - b * s.Su;
-    if (!fp64) {
+    if (fp64) {
+        solve_normal_f64(nu_i, nv_i, cu, cv, det, Dc, anchor_f64(), x, y, g, n);
+        return true;
+    }
+    {
         const float inv = 1.0f / (256.0f * (float)det);
         const float gu = fmaf(-dcf, (float)cu, (float)nu_i) * inv;
         const float gv = fmaf(-dcf, (float)cv, (float)nv_i) * inv;
@@ -203,18 +227,6 @@ __device__ __forceinline__ bool solve_normal_dc(const AffSums& s, int Dc, float 
         n[0] = -mx * r;
         n[1] = -my * r;
         n[2] = -mz * r;
-    } else {
-        const double dd = ((double)Dc + dcd) * (1.0 / 256.0);
-        const double inv = 1.0 / (256.0 * (double)det);
-        const double gu = ((double)nu_i - dcd * (double)cu) * inv;
-        const double gv = ((double)nv_i - dcd * (double)cv) * inv;
-        const double mx = gu;
-        const double my = gv * g.dfy / g.dfx;
-        const double mz = (dd - gu * ((double)x - g.dcx) - gv * ((double)y - g.dcy)) / g.dfx;
-        const double r = 1.0 / sqrt(mx * mx + my * my + mz * mz);
-        n[0] = (float)(-mx * r);
-        n[1] = (float)(-my * r);
-        n[2] = (float)(-mz * r);
     }
     return true;
 }
@@ -223,8 +235,8 @@ __device__ __forceinline__ bool solve_normal_dc(const AffSums& s, int Dc, float 
 __device__ __forceinline__ bool solve_normal(const AffSums& s, int Dc, float dtil, int x, int y,
                                              const Geo& g, float n[3], bool& fp64) {
     const float dcf = dtil * 256.0f - (float)Dc;
-    const double dcd = (double)dtil * 256.0 - (double)Dc;
-    return solve_normal_dc(s, Dc, dcf, dcd, dtil, x, y, g, n, fp64);
+    return solve_normal_dc(
+        s, Dc, dcf, [=] { return (double)dtil * 256.0 - (double)Dc; }, dtil, x, y, g, n, fp64);
 }
 
 __device__ __forceinline__ short snorm16(float v) {

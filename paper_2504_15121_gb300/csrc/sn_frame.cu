@@ -309,8 +309,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                 fixed_packed(c, TWR, g.r_a, Dc, s);
             }
             bool fp64;
-            const double dcd = fit ? (double)num / (double)det : 0.0;
-            if (solve_normal_dc(s, Dc, dcf, dcd, dtil, x, y, g, nrm, fp64))
+            if (solve_normal_dc(
+                    s, Dc, dcf, [=] { return fit ? (double)num / (double)det : 0.0; }, dtil, x, y, g, nrm, fp64))
                 m |= SN_MASK_NORMAL | (fp64 ? SN_MASK_FP64 : 0);
             const float inv = 1.0f / dtil;
             P[0] = g.B * ((float)x - g.cx) * inv;
