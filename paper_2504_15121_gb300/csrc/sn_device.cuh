@@ -175,7 +175,7 @@ __device__ __forceinline__ void star_support(const int* c, int TWR, int Dc, int 
 
 // FP64 solve for supports that trip the conditioning flag (rare; FP64 is a
 // slow pipe on this GPU, so nothing of it runs on the common path).
-__device__ __noinline__ void solve_normal_f64(long long nu_i, long long nv_i, long long cu, long long cv,
+static __device__ __noinline__ void solve_normal_f64(long long nu_i, long long nv_i, long long cu, long long cv,
                                               long long det, int Dc, double dcd, int x, int y, const Geo& g,
                                               float n[3]) {
     const double dd = ((double)Dc + dcd) * (1.0 / 256.0);
