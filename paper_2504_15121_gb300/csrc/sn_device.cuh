@@ -173,6 +173,15 @@ __device__ __forceinline__ void star_support(const int* c, int TWR, int Dc, int 
     }
 }
 
+// int64 -> float through two 32-bit conversions of |x| (the direct 64-bit
+// conversion uses the slow FP64 pipe): correctly rounded for |x| < 2^32, at
+// most ~1.5 ulp off above that (|x| < 2^55).
+__device__ __forceinline__ float i64_to_f32(long long x) {
+    const unsigned long long a = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+    const float f = fmaf((float)(unsigned)(a >> 32), 4294967296.0f, (float)(unsigned)a);
+    return x < 0 ? -f : f;
+}
+
 // FP64 solve for supports that trip the conditioning flag (rare; FP64 is a
 // slow pipe on this GPU, so nothing of it runs on the common path).
 static __device__ __noinline__ void solve_normal_f64(long long nu_i, long long nv_i, long long cu, long long cv,
@@ -217,9 +226,9 @@ __device__ __forceinline__ bool solve_normal_dc(const AffSums& s, int Dc, float 
         return true;
     }
     {
-        const float inv = 1.0f / (256.0f * (float)det);
-        const float gu = fmaf(-dcf, (float)cu, (float)nu_i) * inv;
-        const float gv = fmaf(-dcf, (float)cv, (float)nv_i) * inv;
+        const float inv = 1.0f / (256.0f * i64_to_f32(det));
+        const float gu = fmaf(-dcf, i64_to_f32(cu), i64_to_f32(nu_i)) * inv;
+        const float gv = fmaf(-dcf, i64_to_f32(cv), i64_to_f32(nv_i)) * inv;
         const float mx = gu;
         const float my = gv * g.fy_over_fx;
         const float mz = (dtil - gu * ((float)x - g.cx) - gv * ((float)y - g.cy)) / g.fx;

@@ -34,8 +34,9 @@ __device__ __forceinline__ Thr make_thr(const Geo& g, int Dc) {
     Thr t;
     t.K = g.K_cd;
     if (g.K_cd == 0) {
-        t.hi = 0.0f;                          // any spread stops; zero spread never
-        t.lo = __int_as_float(0x7f800000);
+        // any spread stops; a zero spread is left to the exact test
+        t.hi = 0.0f;
+        t.lo = 0.0f;
     } else {
         const float thr = __fdiv_rn((float)g.K_cd * (1.0f / 65536.0f), (float)Dc);
         t.hi = thr * g.cd_hi;
@@ -60,18 +61,44 @@ __device__ __noinline__ bool cd_stop_from_w(float wlo, float whi, int Dc, int K)
     return cd_stop(Dmin, Dmax, Dc, K);
 }
 
+// Continues a ray from its first unsure step n + 1 with the exact integer
+// test (taken only when a spread falls inside the rounding band).
+template <int SU, int SV, int L, int STRIDE>
+__device__ __noinline__ void ray8_exact_tail(const int2* __restrict__ c, int Dc, int K, int* n_io, int* A_io) {
+    int n = *n_io, A = *A_io;
+    int dmin = Dc, dmax = Dc;
+    for (int t = 1; t <= n; t++) {
+        const int D = c[(SV * t) * STRIDE + SU * t].x;
+        dmin = min(dmin, D);
+        dmax = max(dmax, D);
+    }
+    for (int t = n + 1; t <= L; t++) {
+        const int D = c[(SV * t) * STRIDE + SU * t].x;
+        if (D <= 0) break;
+        const int nmin = min(dmin, D), nmax = max(dmax, D);
+        if (cd_stop(nmin, nmax, Dc, K)) break;
+        dmin = nmin;
+        dmax = nmax;
+        A += t * D;
+        n = t;
+    }
+    *n_io = n;
+    *A_io = A;
+}
+
 // One ray of the M = 8 star with direction (SU, SV) and L distinct pixels
 // t (SU, SV), t = 1..L.  All L samples are loaded first; the walk is
-// predicated (a ray stays stopped once stopped) and branches only when the
-// spread falls inside the rounding band, where the exact test decides.  The
-// data enters as A = sum t D over the included pixels; the moments of the
-// included prefix 1..n are closed forms.
+// branch-free: a step is taken while the spread is surely below the
+// threshold, and the spread of the first step that is not is kept.  Only if
+// that spread lies inside the rounding band does the exact test decide (and
+// possibly continue the ray).  The data enters as A = sum t D over the
+// included pixels; the moments of the included prefix 1..n are closed forms.
 template <int SU, int SV, int L, int STRIDE>
 __device__ __forceinline__ void ray8(const int2* __restrict__ c, int Dc, float wc, const Thr& th, AffSums& s) {
     int2 e[L];
 #pragma unroll
     for (int t = 1; t <= L; t++) e[t - 1] = c[(SV * t) * STRIDE + SU * t];
-    float wlo = wc, whi = wc;
+    float wlo = wc, whi = wc, fdiff = 0.0f;
     int A = 0, n = 0;
     bool alive = true;
 #pragma unroll
@@ -80,14 +107,12 @@ __device__ __forceinline__ void ray8(const int2* __restrict__ c, int Dc, float w
         wlo = fminf(wlo, w);
         whi = fmaxf(whi, w);
         const float diff = whi - wlo;
-        bool stop = diff > th.hi;
-        if (alive && !stop && diff >= th.lo) stop = cd_stop_from_w(wlo, whi, Dc, th.K);
-        alive = alive && !stop;
-        if (alive) {
-            A += t * e[t - 1].x;
-            n = t;
-        }
+        fdiff = alive ? diff : fdiff;
+        alive = alive && diff < th.lo;
+        A += alive ? t * e[t - 1].x : 0;
+        n += alive ? 1 : 0;
     }
+    if (n < L && !(fdiff > th.hi)) ray8_exact_tail<SU, SV, L, STRIDE>(c, Dc, th.K, &n, &A);
     const int T1 = (n * (n + 1)) >> 1;
     const int T2 = (n * (n + 1) * (2 * n + 1)) / 6;
     const int Ad = A - Dc * T1;
@@ -296,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             m = SN_MASK_VALID;
             long long num, det;
             const bool fit = denoise_exact<RD>(c, TWR, g.r_d, Dc, g.K_range, num, det);
-            const float dcf = fit ? (float)num / (float)det : 0.0f;
+            const float dcf = fit ? i64_to_f32(num) / i64_to_f32(det) : 0.0f;
             if (fit) m |= SN_MASK_DENOISED;
             dtil = ((float)Dc + dcf) * (1.0f / 256.0f);
             AffSums s;
