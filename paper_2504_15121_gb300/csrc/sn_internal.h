@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/sn.h"
+#include "sn.h"  // include/ is on the include path
 
 namespace sn {
 
