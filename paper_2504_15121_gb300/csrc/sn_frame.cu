@@ -246,28 +246,23 @@ __device__ __forceinline__ bool denoise_exact(const int2* c, int stride, int rd_
         Suv = (popc_and(m, mask5(2, 1)) - popc_and(m, mask5(2, -1))) +
               2 * (popc_and(m, mask5(2, 2)) - popc_and(m, mask5(2, -2))) +
               4 * (popc_and(m, mask5(2, 4)) - popc_and(m, mask5(2, -4)));
-        const long long M00 = (long long)Suu * Svv - (long long)Suv * Suv;
-        const long long M10 = (long long)Su * Svv - (long long)Sv * Suv;
-        const long long M20 = (long long)Su * Suv - (long long)Sv * Suu;
-        det = n * M00 - Su * M10 + Sv * M20;
-        num = b0 * M00 - b1 * M10 + b2 * M20;
-        return det > 0 && (long long)Dc * det + num > 0;
-    }
+    } else {
 #pragma unroll
-    for (int ov = -R; ov <= R; ov++) {
+        for (int ov = -R; ov <= R; ov++) {
 #pragma unroll
-        for (int ou = -R; ou <= R; ou++) {
-            const int dd = c[ov * stride + ou].x - Dc;
-            if ((unsigned)(dd + lo) <= span) {
-                n++;
-                Su += ou;
-                Sv += ov;
-                Suu += ou * ou;
-                Suv += ou * ov;
-                Svv += ov * ov;
-                b0 += dd;
-                b1 += ou * dd;
-                b2 += ov * dd;
+            for (int ou = -R; ou <= R; ou++) {
+                const int dd = c[ov * stride + ou].x - Dc;
+                if ((unsigned)(dd + lo) <= span) {
+                    n++;
+                    Su += ou;
+                    Sv += ov;
+                    Suu += ou * ou;
+                    Suv += ou * ov;
+                    Svv += ov * ov;
+                    b0 += dd;
+                    b1 += ou * dd;
+                    b2 += ov * dd;
+                }
             }
         }
     }
@@ -289,7 +284,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : g.steps);
     const int TWR = kTW + 2 * Rr, THR = kTH + 2 * Rr;
     int2* tile = reinterpret_cast<int2*>(smem);
-    int* Ls = reinterpret_cast<int*>(smem + sizeof(int2) * (size_t)TWR * THR);
+    int* Ls = reinterpret_cast<int*>(smem + sizeof(int2) * (size_t)TWR * THR);  // union-find parents
+    unsigned* Lrow = reinterpret_cast<unsigned*>(Ls + kThreads);                  // left-edge mask per row
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
     const int tid = threadIdx.y * kTW + threadIdx.x;
     if (o.count && (blockIdx.x | blockIdx.y | tid) == 0) *o.count = 0;
@@ -310,7 +306,19 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int2* c = tile + (threadIdx.y + Rr) * TWR + threadIdx.x + Rr;
     const int2 cc = c[0];
     const int Dc = cc.x;  // 0 outside the image
-    Ls[tid] = Dc > 0 ? tid : -1;
+
+    // ---- tile-local components, part 1: each tile row is one warp; the
+    // pixels joined to their left neighbour form runs, labelled by the run's
+    // first lane (found from the ballot of left edges)
+    const int lane = threadIdx.x, row = threadIdx.y;
+    const bool eL = lane > 0 && pair_edge(Dc, c[-1].x, g.K_pair);
+    const bool eU = row > 0 && pair_edge(Dc, c[-TWR].x, g.K_pair);
+    const unsigned Lb = __ballot_sync(0xffffffffu, eL);
+    const unsigned Ub = __ballot_sync(0xffffffffu, eU);
+    const unsigned upto = 0xffffffffu >> (31 - lane);
+    const int run = row * kTW + (31 - __clz(~Lb & upto));
+    Ls[tid] = Dc > 0 ? run : -1;
+    if (lane == 0) Lrow[row] = Lb;
 
     if (inside) {
         float nrm[3] = {0.0f, 0.0f, 0.0f};
@@ -367,17 +375,20 @@ __global__ void __launch_bounds__(kThreads, 2)
         o.mask[(size_t)y * o.mp + x] = m;
     }
 
-    // ---- tile-local components (union-find over the tile's own pixels)
+    // ---- tile-local components, part 2: join the runs of adjacent rows.  A
+    // vertical edge is skipped when the pixel to its left has one too and
+    // both rows are joined there (the left edge already unites the same runs).
     __syncthreads();
-    if (Dc > 0) {
-        if (threadIdx.x + 1 < kTW && pair_edge(Dc, c[1].x, g.K_pair)) union_s(Ls, tid, tid + 1, g.err);
-        if (threadIdx.y + 1 < kTH && pair_edge(Dc, c[TWR].x, g.K_pair)) union_s(Ls, tid, tid + kTW, g.err);
+    if (eU) {
+        const unsigned Lup = Lrow[row - 1];
+        const bool implied = lane > 0 && ((Ub >> (lane - 1)) & 1u) && ((Lb >> lane) & 1u) && ((Lup >> lane) & 1u);
+        if (!implied) union_s(Ls, run, (row - 1) * kTW + (31 - __clz(~Lup & upto)), g.err);
     }
     __syncthreads();
     if (inside) {
         int lab = -1;
         if (Dc > 0) {
-            const int r = find_s(Ls, tid);
+            const int r = find_s(Ls, run);
             lab = (y0 + r / kTW) * g.W + x0 + (r % kTW);
         }
         o.labels[(size_t)y * (o.lp / 4) + x] = lab;
@@ -388,7 +399,7 @@ template <int VAR, int R, int RD>
 cudaError_t launch_var(const Geo& g, const StarTable& t, const void* disp, size_t dp, const FrameOut& o,
                        cudaStream_t s) {
     const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : g.steps);
-    const size_t smem = sizeof(int2) * (size_t)(kTW + 2 * Rr) * (kTH + 2 * Rr) + sizeof(int) * kThreads;
+    const size_t smem = sizeof(int2) * (size_t)(kTW + 2 * Rr) * (kTH + 2 * Rr) + sizeof(int) * (kThreads + kTH);
     const dim3 grid((g.W + kTW - 1) / kTW, (g.H + kTH - 1) / kTH), block(kTW, kTH);
     const char* d = static_cast<const char*>(disp);
     cudaError_t e = cudaSuccess;

@@ -154,12 +154,14 @@ __global__ void __launch_bounds__(256)
                 int nbx, int nby, int tw, int th) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nV = (long long)(nbx - 1) * g.H;
-    int px, py, qx, qy;
+    int px, py, qx, qy, sx, sy;  // (sx, sy): step to the previous pair along the border
     if (t < nV) {
         const int k = (int)(t / g.H) + 1;
         py = qy = (int)(t - (long long)(k - 1) * g.H);
         qx = k * tw;
         px = qx - 1;
+        sx = 0;
+        sy = 1;
     } else {
         const long long t2 = t - nV;
         if (t2 >= (long long)(nby - 1) * g.W) return;
@@ -167,10 +169,27 @@ __global__ void __launch_bounds__(256)
         px = qx = (int)(t2 - (long long)(k - 1) * g.W);
         qy = k * th;
         py = qy - 1;
+        sx = 1;
+        sy = 0;
     }
     const int Dp = load_code<IN>(disp, dp, px, py, g.W, g.H);
     const int Dq = load_code<IN>(disp, dp, qx, qy, g.W, g.H);
     if (!pair_edge(Dp, Dq, g.K_pair)) return;
+    // Skip the union when the previous pair along the border has an edge
+    // and the same labels on both sides: labels are ancestors in the
+    // union-find forest, so that pair (or the first of its run) already
+    // joins the same two sets.
+    if (px - sx >= 0 && py - sy >= 0) {
+        const int Dbp = load_code<IN>(disp, dp, px - sx, py - sy, g.W, g.H);
+        const int Dbq = load_code<IN>(disp, dp, qx - sx, qy - sy, g.W, g.H);
+        if (pair_edge(Dbp, Dbq, g.K_pair)) {
+            const int lp = __ldcg(labels + (size_t)py * lpe + px);
+            const int lq = __ldcg(labels + (size_t)qy * lpe + qx);
+            const int lbp = __ldcg(labels + (size_t)(py - sy) * lpe + (px - sx));
+            const int lbq = __ldcg(labels + (size_t)(qy - sy) * lpe + (qx - sx));
+            if (lp == lbp && lq == lbq) return;
+        }
+    }
     const LabelIndex li{g.W, lpe};
     union_g(labels, li, py * g.W + px, qy * g.W + qx, g.err);
 }
