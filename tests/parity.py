@@ -55,8 +55,12 @@ def to_host(out, normal_fmt=0):
 
 
 def angle_deg(a, b):
-    cos = np.clip((a * b).sum(-1) / (np.linalg.norm(a, axis=-1) * np.linalg.norm(b, axis=-1)), -1.0, 1.0)
-    return np.degrees(np.arccos(cos))
+    """Angle between vectors, atan2(|a x b|, a . b): accurate for tiny angles
+    and insensitive to the FP32 rounding of the vectors' lengths (arccos of a
+    dot product is not: near 1 it turns a 1e-7 length error into 0.02 deg)."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.degrees(np.arctan2(np.linalg.norm(np.cross(a, b), axis=-1), (a * b).sum(-1)))
 
 
 def compare_normals(gpu_n, ref_n, ref_mask):
