@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     return ap.parse_args()
 
 
@@ -271,6 +273,11 @@ def run_ours(args):
     peak = float(peaks["hbm_gbs"])
     traffic = load_traffic(dom)
 
+    # ---- the precision form on the same scenes: uint16 (256 d) in, snorm16 normals out
+    forms = {"precision_u16_snorm16": time_form(
+        scenes, args, dict(in_dtype=sn.SN_IN_U16X256, normal_fmt=sn.SN_NORMALS_SNORM16X4),
+        lambda s: s.disp_u16, 27, dist, world)}
+
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
     if not args.no_e2e:
@@ -279,6 +286,10 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(scenes, args.cpu_seconds)
+
+    serving = None
+    if world == 1 and not args.no_serving:
+        serving = run_serving(args)
 
     if rank == 0:
         fm = sorted(frame_ms)
@@ -306,14 +317,106 @@ def run_ours(args):
                          "algo_bytes_per_px": ALGO_BYTES[dom],
                          "frame_frac": FRAME_ALGO_BYTES * W * H / (elapsed_ms / 1e3 / (args.steps * F)) / 1e9 / peak},
             "gpu_launches": int(launches),
+            "forms": forms,
             "clocks": clocks.summary(),
             "e2e": e2e,
+            "serving": serving,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     pipe.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def time_form(scenes, args, params, pick, bytes_per_px, dist, world):
+    """Device throughput and per-frame times of another form of the chain on
+    the same scenes (same frames per step and step count)."""
+    import torch
+    from paper_2504_15121_gb300 import Pipeline, sn
+    s0 = scenes[0]
+    pipe = Pipeline(s0.camera, s0.W, s0.H, **params)
+    disp = [pipe.upload(pick(s)) for s in scenes]
+    F = args.frames
+    outs = [pipe.buffers() for _ in range(F)]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for f in range(F):
+            pipe.run_frame(disp[f % len(disp)], outs[f], stream=stream, write_den=False)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sn.sn_set_profiling(pipe.ctx, True)
+    sn.sn_stage_times(pipe.ctx)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    _, nf, fm = sn.sn_stage_times(pipe.ctx, cap=args.steps * F)
+    sn.sn_set_profiling(pipe.ctx, False)
+    sn.sn_check_device(pipe.ctx)
+    pipe.close()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    fm = sorted(fm)
+    W, H = s0.W, s0.H
+    return {"value": world * args.steps * F * W * H / (ms / 1e3) / 1e6, "unit": "MPix/s",
+            "frame_ms_p50": fm[len(fm) // 2] if fm else None,
+            "frame_ms_p99": fm[min(len(fm) - 1, int(0.99 * (len(fm) - 1) + 0.5))] if fm else None,
+            "algo_bytes_per_px": bytes_per_px,
+            "params": {k: int(v) for k, v in params.items()}}
+
+
+SERVING_CAMERAS = [("planes_640x480", 120.0)] * 2 + [("mixed_1482x994", 30.0)] * 4 + \
+    [("driving_2048x1024", 30.0)] * 2
+
+
+def run_serving(args):
+    """The serving workload: 8 simulated cameras (2x 640x480 at 120 Hz,
+    4x 1482x994 at 30 Hz, 2x 2048x1024 at 30 Hz), Poisson arrivals, one
+    CUDA graph per request slot, 4 streams; latency from arrival to result
+    ready on the device.  Offered rate x1 for --serve-seconds, then a rate
+    sweep; plain FP32 chain and FP16 in / snorm16 out chain."""
+    import numpy as np
+    import torch
+    from paper_2504_15121_gb300 import serve, sn
+    from scenes import make_scene
+    pools_src = {}
+    for name, _ in SERVING_CAMERAS:
+        if name not in pools_src:
+            pools_src[name] = [make_scene(name, frame=100 + k) for k in range(2)]
+    out = {}
+    for form, params, pick in (
+            ("plain_f32", {}, lambda s: s.disp),
+            ("f16_snorm16", dict(in_dtype=sn.SN_IN_F16, normal_fmt=sn.SN_NORMALS_SNORM16X4),
+             lambda s: s.disp.astype(np.float16))):
+        cams, pools = [], []
+        for name, rate in SERVING_CAMERAS:
+            ss = pools_src[name]
+            cams.append(serve.camera(ss[0].W, ss[0].H, ss[0].camera, rate_hz=rate, **params))
+            pools.append([torch.from_numpy(np.ascontiguousarray(pick(s))).pin_memory() for s in ss])
+        srv = serve.Server(cams, memory_budget=6 << 30, max_slots_per_camera=6, n_streams=4, queue_depth=256)
+        try:
+            res = {"x1": srv.simulate(pools, duration_s=args.serve_seconds, rate_scale=1.0, seed=1)}
+            for k in (8, 24):
+                res[f"x{k}"] = srv.simulate(pools, duration_s=1.0, rate_scale=float(k), seed=k)
+            srv.check()
+        finally:
+            srv.close()
+        out[form] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                     for k, v in res.items()}
+    out["how"] = ("8 cameras: 2x 640x480 @120 Hz, 4x 1482x994 @30 Hz, 2x 2048x1024 @30 Hz; Poisson "
+                  "arrivals; latency = arrival (pinned host frame) -> outputs ready on device; "
+                  "x8/x24 = every camera's rate multiplied")
+    return out
 
 
 def load_traffic(kernel: str):

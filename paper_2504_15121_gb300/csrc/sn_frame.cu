@@ -5,6 +5,8 @@
 // D is the exact integer disparity code used by every sum and decision,
 // 1/D (FP32, correctly rounded; +inf for invalid) carries the covered-depth
 // test, which in reciprocal form reads 1/Dmin - 1/Dmax > K / (2^16 Dc).
+#include <atomic>
+
 #include "sn_device.cuh"
 
 namespace sn {
@@ -395,29 +397,46 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 }
 
+__host__ __device__ constexpr size_t frame_smem(int Rr) {
+    return sizeof(int2) * (size_t)(kTW + 2 * Rr) * (kTH + 2 * Rr) + sizeof(int) * (kThreads + kTH);
+}
+
+// Raises a kernel's dynamic shared-memory limit once per device, to the most
+// any parameter set of its variant can ask for (so no launch, and no launch
+// under stream capture, changes function attributes).
+template <class Kernel>
+cudaError_t smem_limit_once(Kernel k, size_t bytes) {
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done.fetch_or(bit);
+    return e;
+}
+
+template <int IN, int VAR, int R, int RD>
+cudaError_t launch_in(const Geo& g, const StarTable& t, const char* d, size_t dp, const FrameOut& o, cudaStream_t s) {
+    constexpr int Rmax = R > 0 ? R : (VAR == 0 ? 15 : kMaxSteps);
+    const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : g.steps);
+    const dim3 grid((g.W + kTW - 1) / kTW, (g.H + kTH - 1) / kTH), block(kTW, kTH);
+    const cudaError_t e = smem_limit_once(k_frame<IN, VAR, R, RD>, frame_smem(Rmax));
+    if (e != cudaSuccess) return e;
+    k_frame<IN, VAR, R, RD><<<grid, block, frame_smem(Rr), s>>>(g, t, d, dp, o);
+    return cudaGetLastError();
+}
+
 template <int VAR, int R, int RD>
 cudaError_t launch_var(const Geo& g, const StarTable& t, const void* disp, size_t dp, const FrameOut& o,
                        cudaStream_t s) {
-    const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : g.steps);
-    const size_t smem = sizeof(int2) * (size_t)(kTW + 2 * Rr) * (kTH + 2 * Rr) + sizeof(int) * (kThreads + kTH);
-    const dim3 grid((g.W + kTW - 1) / kTW, (g.H + kTH - 1) / kTH), block(kTW, kTH);
     const char* d = static_cast<const char*>(disp);
-    cudaError_t e = cudaSuccess;
     switch (g.in_dtype) {
-        case SN_IN_F32:
-            e = cudaFuncSetAttribute(k_frame<SN_IN_F32, VAR, R, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) k_frame<SN_IN_F32, VAR, R, RD><<<grid, block, smem, s>>>(g, t, d, dp, o);
-            break;
-        case SN_IN_F16:
-            e = cudaFuncSetAttribute(k_frame<SN_IN_F16, VAR, R, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) k_frame<SN_IN_F16, VAR, R, RD><<<grid, block, smem, s>>>(g, t, d, dp, o);
-            break;
-        default:
-            e = cudaFuncSetAttribute(k_frame<SN_IN_U16X256, VAR, R, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) k_frame<SN_IN_U16X256, VAR, R, RD><<<grid, block, smem, s>>>(g, t, d, dp, o);
-            break;
+        case SN_IN_F32: return launch_in<SN_IN_F32, VAR, R, RD>(g, t, d, dp, o, s);
+        case SN_IN_F16: return launch_in<SN_IN_F16, VAR, R, RD>(g, t, d, dp, o, s);
+        default: return launch_in<SN_IN_U16X256, VAR, R, RD>(g, t, d, dp, o, s);
     }
-    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace

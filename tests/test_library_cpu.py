@@ -23,9 +23,13 @@ def sn():
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "sn.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(sn_[a-z0-9_]+)\s*\(", text)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(sn_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(sn):
@@ -34,7 +38,9 @@ def test_every_declared_symbol_is_exported(sn):
     lib = C.CDLL(sn.LIB_PATH)
     for n in names:
         assert hasattr(lib, n), n
-    assert set(names) <= set(sn.EXPORTS)
+    from paper_2504_15121_gb300 import serve
+    assert set(names) <= set(sn.EXPORTS) | set(serve.EXPORTS)
+    assert "sn_server_simulate" in names and "sn_normals_noalloc" in names
 
 
 @pytest.mark.parametrize("M,s", [(8, 10), (16, 30), (4, 1), (12, 7), (16, 6)])
@@ -69,3 +75,17 @@ def test_status_strings(sn):
     for st in range(7):
         assert sn.lib.sn_status_string(st)
     assert sn.lib.sn_star_offsets(17, 3, None, None) == -1
+
+
+def test_server_rejects_bad_config_before_any_cuda_call(sn):
+    from paper_2504_15121_gb300 import serve
+    cfg = serve.sn_server_config(0, None, 1 << 30, 2, 2, 0, 4)
+    h = C.c_void_p()
+    assert serve.lib.sn_server_create(C.byref(cfg), C.byref(h)) == sn.SN_EINVAL
+    cams = (serve.sn_server_camera * 1)(serve.camera(64, 48, Camera(300.0, 300.0, 32.0, 24.0, 0.1)))
+    for bad in (dict(n_streams=0), dict(n_streams=17), dict(max_slots_per_camera=0), dict(queue_depth=0)):
+        kw = dict(n_streams=2, max_slots_per_camera=2, queue_depth=4)
+        kw.update(bad)
+        cfg = serve.sn_server_config(1, cams, 1 << 30, kw["max_slots_per_camera"], kw["n_streams"], 0,
+                                     kw["queue_depth"])
+        assert serve.lib.sn_server_create(C.byref(cfg), C.byref(h)) == sn.SN_EINVAL
