@@ -403,10 +403,10 @@ __host__ __device__ constexpr size_t frame_smem(int Rr) {
 
 // Raises a kernel's dynamic shared-memory limit once per device, to the most
 // any parameter set of its variant can ask for (so no launch, and no launch
-// under stream capture, changes function attributes).
+// under stream capture, changes function attributes).  `done` is the
+// per-variant record of the devices already set.
 template <class Kernel>
-cudaError_t smem_limit_once(Kernel k, size_t bytes) {
-    static std::atomic<unsigned long long> done{0};
+cudaError_t smem_limit_once(Kernel k, size_t bytes, std::atomic<unsigned long long>& done) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -422,7 +422,8 @@ cudaError_t launch_in(const Geo& g, const StarTable& t, const char* d, size_t dp
     constexpr int Rmax = R > 0 ? R : (VAR == 0 ? 15 : kMaxSteps);
     const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : g.steps);
     const dim3 grid((g.W + kTW - 1) / kTW, (g.H + kTH - 1) / kTH), block(kTW, kTH);
-    const cudaError_t e = smem_limit_once(k_frame<IN, VAR, R, RD>, frame_smem(Rmax));
+    static std::atomic<unsigned long long> done{0};
+    const cudaError_t e = smem_limit_once(k_frame<IN, VAR, R, RD>, frame_smem(Rmax), done);
     if (e != cudaSuccess) return e;
     k_frame<IN, VAR, R, RD><<<grid, block, frame_smem(Rr), s>>>(g, t, d, dp, o);
     return cudaGetLastError();
