@@ -1,0 +1,213 @@
+"""FP64 oracle of the learned boundary gate (test infrastructure only).
+
+Only the test suite, the package's smoke check, the benchmark's CPU leg and
+the committed training-label script may import this module; the product
+never does.
+
+Network (frozen definition; the paper has no learned part -- it notes that
+the method is differentiable apart from the adaptive support, Sec. I-C):
+
+  features f(p), 8 channels, from the integer disparity codes D (0 = invalid,
+  pixels outside the image invalid), L = log2 D:
+      f0 = L(p + e_u) - L(p)   if p and p + e_u are valid, else 0
+      f1 = L(p + e_v) - L(p)   if p and p + e_v are valid, else 0
+      f2 = 1 if p is valid, else 0
+      f3..f7 = 0
+  h1 = relu(conv3x3(f) W1 + b1)          16 channels
+  z  = relu(conv3x3(h1) W2 + b2)         16 channels
+  q  = sigmoid(z . W3 + b3)              P(the 5x5 patch at p is one valid surface)
+  conv3x3: out(p) = sum over o in {-1,0,1}^2 of W[(o_v+1)*3 + (o_u+1)] in(p + o).
+  gate(p) = (min over |o|_inf <= 2 of q(p + o) >= tau) and the 9x9 window at
+  p is entirely valid.
+
+Weight layout: W1[16][9][8], W2[16][9][16], W3[16], b1[16], b2[16], b3.
+The GPU runs features, weights and layer-1 activations in BF16 with FP32
+accumulation; `bf16` reproduces that rounding (round to nearest even).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+N_IN, N_HID = 8, 16
+SHAPES = {"W1": (N_HID, 9, N_IN), "b1": (N_HID,), "W2": (N_HID, 9, N_HID), "b2": (N_HID,),
+          "W3": (N_HID,), "b3": (1,)}
+ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
+N_PARAMS = sum(int(np.prod(s)) for s in SHAPES.values())
+
+
+def bf16(x):
+    """Round to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.asarray(x, np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) >> 16) << 16
+    out = r.astype(np.uint32).view(np.float32).astype(np.float64)
+    nan = np.isnan(f)
+    if nan.any():
+        out = np.where(nan, np.nan, out)
+    return out
+
+
+def unflatten(theta):
+    theta = np.asarray(theta, np.float64)
+    out, k = {}, 0
+    for name in ORDER:
+        n = int(np.prod(SHAPES[name]))
+        out[name] = theta[k:k + n].reshape(SHAPES[name])
+        k += n
+    return out
+
+
+def flatten(w):
+    return np.concatenate([np.asarray(w[n], np.float64).ravel() for n in ORDER])
+
+
+def init_params(seed=0):
+    rng = np.random.default_rng(seed)
+    w = {"W1": rng.normal(0, np.sqrt(2.0 / 27), SHAPES["W1"]), "b1": np.zeros(N_HID),
+         "W2": rng.normal(0, np.sqrt(2.0 / 144), SHAPES["W2"]), "b2": np.zeros(N_HID),
+         "W3": rng.normal(0, np.sqrt(1.0 / 16), SHAPES["W3"]), "b3": np.zeros(1)}
+    return flatten(w)
+
+
+# ---------------------------------------------------------------- features
+def features(D):
+    """f for every pixel of an integer-code image (any shape [..., H, W])."""
+    D = np.asarray(D)
+    valid = D > 0
+    L = np.where(valid, np.log2(np.where(valid, D, 1).astype(np.float64)), 0.0)
+    f = np.zeros(D.shape + (N_IN,))
+    vr = np.zeros_like(valid)
+    vr[..., :, :-1] = valid[..., :, :-1] & valid[..., :, 1:]
+    vd = np.zeros_like(valid)
+    vd[..., :-1, :] = valid[..., :-1, :] & valid[..., 1:, :]
+    dr = np.zeros(D.shape)
+    dr[..., :, :-1] = L[..., :, 1:] - L[..., :, :-1]
+    dd = np.zeros(D.shape)
+    dd[..., :-1, :] = L[..., 1:, :] - L[..., :-1, :]
+    f[..., 0] = np.where(vr, dr, 0.0)
+    f[..., 1] = np.where(vd, dd, 0.0)
+    f[..., 2] = valid.astype(np.float64)
+    return f
+
+
+def _conv3x3(x, W, b):
+    """x [..., H, W, Cin], W [Cout, 9, Cin]: valid 3x3 cross-correlation."""
+    H, Wd = x.shape[-3] - 2, x.shape[-2] - 2
+    out = np.zeros(x.shape[:-3] + (H, Wd, W.shape[0]))
+    for oy in range(3):
+        for ox in range(3):
+            patch = x[..., oy:oy + H, ox:ox + Wd, :]
+            out += patch @ W[:, oy * 3 + ox, :].T
+    return out + b
+
+
+def forward_image(D, theta, round_bf16=True):
+    """q for every pixel of an image (outside the image: invalid pixels)."""
+    w = unflatten(theta)
+    if round_bf16:
+        w = {k: (bf16(v) if k.startswith("W") else v) for k, v in w.items()}
+    H, W = D.shape
+    P = 4
+    Dp = np.zeros((H + 2 * P + 1, W + 2 * P + 1), D.dtype)
+    Dp[P:P + H, P:P + W] = D
+    f = features(Dp)[:-1, :-1]                  # (H + 2P) x (W + 2P)
+    if round_bf16:
+        f = bf16(f)
+    h1 = np.maximum(_conv3x3(f, w["W1"], w["b1"]), 0.0)   # margin P - 1
+    if round_bf16:
+        h1 = bf16(h1)
+    z = np.maximum(_conv3x3(h1, w["W2"], w["b2"]), 0.0)   # margin P - 2
+    logit = z @ w["W3"] + w["b3"][0]
+    q = 1.0 / (1.0 + np.exp(-logit))
+    m = P - 2
+    return q[m:m + H, m:m + W] if m > 0 else q
+
+
+def gate_image(D, theta, tau, round_bf16=True):
+    """(gate bits, q, min q over 5x5) of an image."""
+    q = forward_image(D, theta, round_bf16)
+    H, W = D.shape
+    qp = np.pad(q, 2, constant_values=np.inf)
+    qmin = np.full((H, W), np.inf)
+    for oy in range(5):
+        for ox in range(5):
+            qmin = np.minimum(qmin, qp[oy:oy + H, ox:ox + W])
+    valid = np.pad(D > 0, 4, constant_values=False)
+    allv = np.ones((H, W), bool)
+    for oy in range(9):
+        for ox in range(9):
+            allv &= valid[oy:oy + H, ox:ox + W]
+    return (qmin >= tau) & allv, q, qmin
+
+
+# ---------------------------------------------------------------- patches (training)
+def forward_patches(Dp, theta, round_bf16=False, keep=False):
+    """Dp [B, 6, 6] integer codes around each centre (centre at [2, 2]);
+    returns q [B] (and the intermediates when keep=True)."""
+    w = unflatten(theta)
+    if round_bf16:
+        w = {k: (bf16(v) if k.startswith("W") else v) for k, v in w.items()}
+    f = features(Dp)[:, :5, :5, :]
+    if round_bf16:
+        f = bf16(f)
+    a1 = _conv3x3(f, w["W1"], w["b1"])          # [B, 3, 3, 16]
+    h1 = np.maximum(a1, 0.0)
+    if round_bf16:
+        h1 = bf16(h1)
+    a2 = _conv3x3(h1, w["W2"], w["b2"])[:, 0, 0, :]   # [B, 16]
+    z = np.maximum(a2, 0.0)
+    logit = z @ w["W3"] + w["b3"][0]
+    q = 1.0 / (1.0 + np.exp(-logit))
+    if keep:
+        return q, dict(f=f, a1=a1, h1=h1, a2=a2, z=z, logit=logit, w=w)
+    return q
+
+
+def bce(q, y):
+    q = np.clip(q, 1e-12, 1 - 1e-12)
+    return float(np.mean(-(y * np.log(q) + (1 - y) * np.log(1 - q))))
+
+
+def loss_and_grad(Dp, y, theta):
+    """Mean binary cross-entropy of the batch and its gradient (FP64,
+    written out layer by layer)."""
+    q, c = forward_patches(Dp, theta, keep=True)
+    w = c["w"]
+    B = len(y)
+    dlogit = (q - y) / B                                  # d loss / d logit
+    g = {"W3": c["z"].T @ dlogit, "b3": np.array([dlogit.sum()])}
+    dz = np.outer(dlogit, w["W3"]) * (c["a2"] > 0)        # [B, 16]
+    g["b2"] = dz.sum(0)
+    gW2 = np.zeros(SHAPES["W2"])
+    dh1 = np.zeros(c["h1"].shape)                         # [B, 3, 3, 16]
+    for oy in range(3):
+        for ox in range(3):
+            hpos = c["h1"][:, oy, ox, :]                  # [B, 16]
+            gW2[:, oy * 3 + ox, :] = dz.T @ hpos
+            dh1[:, oy, ox, :] = dz @ w["W2"][:, oy * 3 + ox, :]
+    g["W2"] = gW2
+    da1 = dh1 * (c["a1"] > 0)
+    g["b1"] = da1.sum((0, 1, 2))
+    gW1 = np.zeros(SHAPES["W1"])
+    f = c["f"]
+    for oy in range(3):
+        for ox in range(3):
+            fp = f[:, oy:oy + 3, ox:ox + 3, :]            # [B, 3, 3, 8]
+            gW1[:, oy * 3 + ox, :] = np.einsum("bijo,bijc->oc", da1, fp)
+    g["W1"] = gW1
+    return bce(q, y), flatten(g)
+
+
+def patch_labels(prim, valid):
+    """1 where the 5x5 patch centred at a pixel is all valid and of one
+    primitive (generator ground truth), else 0; [H, W] -> [H, W]."""
+    H, W = prim.shape
+    pp = np.pad(prim, 2, constant_values=-2)
+    vp = np.pad(valid, 2, constant_values=False)
+    lab = np.ones((H, W), bool)
+    c = prim
+    for oy in range(5):
+        for ox in range(5):
+            lab &= vp[oy:oy + H, ox:ox + W] & (pp[oy:oy + H, ox:ox + W] == c)
+    return lab

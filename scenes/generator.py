@@ -334,12 +334,17 @@ def _finish(name, cam, zb, rng, sigma, quant, invalid_mode, target, encode16):
 
 
 def make_scene(name: str, seed=0, frame: int = 0, sigma: float | None = None,
-               W: int | None = None, H: int | None = None) -> Scene:
+               W: int | None = None, H: int | None = None, scale: float = 1.0) -> Scene:
     """Render the scene recipe `name` (a key of CONFIGS) for `frame`.
 
-    The random stream is np.random.default_rng([cfg, frame, seed]).
+    The random stream is np.random.default_rng([cfg, frame, seed]).  `scale`
+    shrinks width, height and focal length together (same field of view).
     """
     cfg = dict(CONFIGS[name])
+    if scale != 1.0:
+        cfg["W"] = max(8, int(round(cfg["W"] * scale)))
+        cfg["H"] = max(8, int(round(cfg["H"] * scale)))
+        cfg["f"] = cfg["f"] * scale
     if W is not None:
         cfg["W"] = W
     if H is not None:

@@ -38,8 +38,8 @@ def test_every_declared_symbol_is_exported(sn):
     lib = C.CDLL(sn.LIB_PATH)
     for n in names:
         assert hasattr(lib, n), n
-    from paper_2504_15121_gb300 import serve
-    assert set(names) <= set(sn.EXPORTS) | set(serve.EXPORTS)
+    from paper_2504_15121_gb300 import serve, gate
+    assert set(names) <= set(sn.EXPORTS) | set(serve.EXPORTS) | set(gate.EXPORTS)
     assert "sn_server_simulate" in names and "sn_normals_noalloc" in names
 
 
@@ -89,3 +89,26 @@ def test_server_rejects_bad_config_before_any_cuda_call(sn):
         cfg = serve.sn_server_config(1, cams, 1 << 30, kw["max_slots_per_camera"], kw["n_streams"], 0,
                                      kw["queue_depth"])
         assert serve.lib.sn_server_create(C.byref(cfg), C.byref(h)) == sn.SN_EINVAL
+
+
+def test_gate_weights_format(sn):
+    from paper_2504_15121_gb300 import gate
+    from oracle import gate as ogate
+    assert gate.N_PARAMS == ogate.N_PARAMS == 3505
+    th = gate.init_params(1)
+    assert np.array_equal(gate.parse_blob(gate.weights_blob(th)), th)
+    with pytest.raises(ValueError):
+        gate.parse_blob(b"XXXX" + gate.weights_blob(th)[4:])
+
+
+def test_training_labels_and_codes(sn):
+    from paper_2504_15121_gb300 import gate
+    from oracle import gate as ogate
+    import oracle as orc
+    rng = np.random.default_rng(4)
+    prim = np.repeat(rng.integers(0, 3, (6, 8)), 4, 0).repeat(4, 1)
+    disp = rng.uniform(0.5, 300, prim.shape).astype(np.float32)
+    disp[rng.random(prim.shape) < 0.1] = 0
+    D = gate.codes(disp)
+    assert np.array_equal(D, orc.ingest(disp))
+    assert np.array_equal(gate.one_surface_labels(prim, D), ogate.patch_labels(prim, D > 0))
