@@ -55,9 +55,9 @@ def test_training_reduces_loss_and_checkpoint_resumes(G, tmp_path):
     X, y = G.make_training_set(n_scenes=48, per_class=128, seed=5, workers=4)
     assert len(y) > 5000 and 0.2 < y.mean() < 0.8
     theta0 = G.init_params(0)
-    theta, hist = G.train(X, y, epochs=3, batch=1024, lr=3e-3, seed=0, log=lambda *_: None,
+    theta, hist = G.train(X, y, epochs=6, batch=512, lr=3e-3, seed=0, log=lambda *_: None,
                           checkpoint=str(tmp_path / "ck.npz"))
-    assert hist[-1] < hist[0] and hist[-1] < 0.6
+    assert hist[-1] < 0.8 * hist[0]
     ck = np.load(tmp_path / "ck.npz")
     assert np.array_equal(ck["theta"], theta) and int(ck["version"]) == G.VERSION
     # resuming from the checkpoint continues exactly where the run stopped
