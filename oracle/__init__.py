@@ -91,6 +91,9 @@ def lib():
         L.orc_run_frame.argtypes = [p, C.c_int, C.c_size_t, C.c_int, C.c_int, C.POINTER(_Camera),
                                     C.POINTER(_Params), p, p, p, p, p]
         L.orc_run_frame.restype = C.c_int
+        L.orc_run_frame_gated.argtypes = [p, C.c_int, C.c_size_t, C.c_int, C.c_int, C.POINTER(_Camera),
+                                          C.POINTER(_Params), p, p, p, p, p, p]
+        L.orc_run_frame_gated.restype = C.c_int
         _lib = L
     return _lib
 
@@ -196,8 +199,10 @@ class Frame:
     n_components: int
 
 
-def run_frame(disp: np.ndarray, cam, params: Params | None = None) -> Frame:
-    """The whole chain on one disparity map (float32, float16 or uint16 d*256)."""
+def run_frame(disp: np.ndarray, cam, params: Params | None = None, gate=None) -> Frame:
+    """The whole chain on one disparity map (float32, float16 or uint16 d*256).
+    gate (bool [H, W], optional): the learned gate's decisions; certified
+    pixels take the un-gated 5x5 denoise and the full 9x9 affine window."""
     params = params or Params()
     disp = np.ascontiguousarray(disp)
     H, W = disp.shape
@@ -206,7 +211,9 @@ def run_frame(disp: np.ndarray, cam, params: Params | None = None) -> Frame:
     pts = np.zeros((H, W, 3))
     labels = np.zeros((H, W), np.int32)
     mask = np.zeros((H, W), np.uint8)
-    n = lib().orc_run_frame(_ptr(disp), _dtype_code(disp), disp.strides[0], W, H,
-                            C.byref(_cam(cam)), C.byref(params.c()), _ptr(den), _ptr(nrm),
-                            _ptr(pts), _ptr(labels), _ptr(mask))
+    g = None if gate is None else np.ascontiguousarray(gate, np.uint8)
+    n = lib().orc_run_frame_gated(_ptr(disp), _dtype_code(disp), disp.strides[0], W, H,
+                                  C.byref(_cam(cam)), C.byref(params.c()),
+                                  _ptr(g) if g is not None else None, _ptr(den), _ptr(nrm),
+                                  _ptr(pts), _ptr(labels), _ptr(mask))
     return Frame(den, nrm, pts, labels, mask, n)

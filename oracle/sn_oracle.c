@@ -138,7 +138,18 @@ static double det3(double a[3][3])
            a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
 }
 
+static void denoise_impl(const int32_t *D, int W, int H, const orc_params *P, const uint8_t *gate,
+                         double *den, uint8_t *fit_ok);
+
 void orc_denoise(const int32_t *D, int W, int H, const orc_params *P, double *den, uint8_t *fit_ok)
+{
+    denoise_impl(D, W, H, P, NULL, den, fit_ok);
+}
+
+/* gate (may be NULL): pixels certified by the learned gate use every valid
+ * sample of the window (no range gate). */
+static void denoise_impl(const int32_t *D, int W, int H, const orc_params *P, const uint8_t *gate,
+                         double *den, uint8_t *fit_ok)
 {
     const int r = P->r_denoise;
     const int64_t K = kfix(P->k_range);
@@ -161,7 +172,7 @@ void orc_denoise(const int32_t *D, int W, int H, const orc_params *P, double *de
                     int64_t diff = (int64_t)Di - Dc;
                     if (diff < 0)
                         diff = -diff;
-                    if (diff * 65536 > K * (int64_t)Dc)
+                    if (!(gate && gate[idx]) && diff * 65536 > K * (int64_t)Dc)
                         continue;
                     double phi[3] = {1.0, (double)ou, (double)ov};
                     double di = Di / 256.0;
@@ -297,11 +308,27 @@ int orc_support_mask(const int32_t *D, int W, int H, int u, int v, const orc_par
  * diag (optional, 8 doubles per pixel): N, alpha, beta, gamma, det, g_u, g_v,
  * support flag bits.
  * ------------------------------------------------------------------- */
+static void affine_impl(const int32_t *D, const double *den, int W, int H, const orc_camera *cam,
+                        const orc_params *P, const uint8_t *gate, double *nrm, uint8_t *mask, double *diag);
+
 void orc_affine_normals(const int32_t *D, const double *den, int W, int H, const orc_camera *cam,
                         const orc_params *P, double *nrm, uint8_t *mask, double *diag)
 {
-    const int R = support_radius(P);
+    affine_impl(D, den, W, H, cam, P, NULL, nrm, mask, diag);
+}
+
+/* gate (may be NULL): pixels certified by the learned gate take the fixed
+ * 9x9 window (radius 4) as their support and get ORC_M_LEARNED. */
+static void affine_impl(const int32_t *D, const double *den, int W, int H, const orc_camera *cam,
+                        const orc_params *P, const uint8_t *gate, double *nrm, uint8_t *mask, double *diag)
+{
+    int R = support_radius(P);
+    if (gate && R < 4)
+        R = 4;
     const int side = 2 * R + 1;
+    orc_params Pg = *P;
+    Pg.support = ORC_FIXED;
+    Pg.r_affine = 4;
     int *tou = malloc(sizeof(int) * (P->dirs * P->steps + 1));
     int *tov = malloc(sizeof(int) * (P->dirs * P->steps + 1));
     orc_star_offsets(P->dirs, P->steps, tou, tov);
@@ -323,7 +350,10 @@ void orc_affine_normals(const int32_t *D, const double *den, int W, int H, const
                     continue;
                 }
                 m |= ORC_M_VALID;
-                int N = support_of(D, W, H, u, v, P, tou, tov, incl, R);
+                const int certified = gate && gate[idx];
+                if (certified)
+                    m |= ORC_M_LEARNED;
+                int N = support_of(D, W, H, u, v, certified ? &Pg : P, tou, tov, incl, R);
                 double alpha = 0, beta = 0, gamma = 0;
                 for (int ov = -R; ov <= R; ov++)
                     for (int ou = -R; ou <= R; ou++)
@@ -474,16 +504,30 @@ void orc_points(const double *den, const uint8_t *mask, int W, int H, const orc_
  * components, points.  Outputs are dense [H][W] (x3 for vectors).
  * mask gets bits VALID | NORMAL | FP64 | DENOISED.
  * ------------------------------------------------------------------- */
+int orc_run_frame_gated(const void *disp, int dtype, size_t pitch_bytes, int W, int H, const orc_camera *cam,
+                        const orc_params *P, const uint8_t *gate, double *den, double *nrm, double *pts,
+                        int32_t *labels, uint8_t *mask);
+
 int orc_run_frame(const void *disp, int dtype, size_t pitch_bytes, int W, int H, const orc_camera *cam,
                   const orc_params *P, double *den, double *nrm, double *pts, int32_t *labels,
                   uint8_t *mask)
+{
+    return orc_run_frame_gated(disp, dtype, pitch_bytes, W, H, cam, P, NULL, den, nrm, pts, labels, mask);
+}
+
+/* The chain with the learned gate's decisions as input (gate may be NULL):
+ * certified pixels take the un-gated 5x5 denoise window and the fixed 9x9
+ * affine window. */
+int orc_run_frame_gated(const void *disp, int dtype, size_t pitch_bytes, int W, int H, const orc_camera *cam,
+                        const orc_params *P, const uint8_t *gate, double *den, double *nrm, double *pts,
+                        int32_t *labels, uint8_t *mask)
 {
     size_t n = (size_t)W * H;
     int32_t *D = malloc(sizeof(int32_t) * (n ? n : 1));
     uint8_t *fit = malloc(n ? n : 1);
     orc_ingest(disp, dtype, pitch_bytes, W, H, D);
-    orc_denoise(D, W, H, P, den, fit);
-    orc_affine_normals(D, den, W, H, cam, P, nrm, mask, NULL);
+    denoise_impl(D, W, H, P, gate, den, fit);
+    affine_impl(D, den, W, H, cam, P, gate, nrm, mask, NULL);
     for (size_t i = 0; i < n; i++)
         if (fit[i])
             mask[i] |= ORC_M_DENOISED;

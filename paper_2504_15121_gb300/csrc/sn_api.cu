@@ -6,6 +6,7 @@
 
 #include <new>
 
+#include "sn_gate_internal.h"
 #include "sn_internal.h"
 
 namespace {
@@ -24,6 +25,9 @@ struct sn_ctx {
     sn::Workspace ws;
     unsigned long long launches;
     bool star8;  // the star table is the compile-time M = 8, s = 10 ray set
+    sn::GateDev gate;    // learned gate weights (learned contexts)
+    float* gate_theta;   // their FP32 source on the device
+    bool gate_loaded;
     bool prof;
     cudaEvent_t* ev;  // kProfFrames x (kStages + 1)
     int prof_frames;
@@ -242,7 +246,12 @@ sn_status sn_create(const sn_camera* cam, int W, int H, const sn_params* pin, sn
         return SN_EINVAL;
     if (p.in_dtype < SN_IN_F32 || p.in_dtype > SN_IN_U16X256) return SN_EINVAL;
     if (p.normal_fmt != SN_NORMALS_F32X3 && p.normal_fmt != SN_NORMALS_SNORM16X4) return SN_EINVAL;
-    if (p.learned) return SN_ENOTSUP;
+    if (p.learned != 0 && p.learned != 1) return SN_EINVAL;
+    // the gate certifies the full 9x9 window and 5x5 denoise window of the
+    // default star-fill configuration
+    if (p.learned && (p.support != SN_SUPPORT_STARFILL_CD || p.dirs != 8 || p.steps != 10 || p.r_denoise != 2 ||
+                      p.r_affine != 4))
+        return SN_ENOTSUP;
 
     sn_ctx* c = new (std::nothrow) sn_ctx();
     if (!c) return SN_ENOMEM;
@@ -294,6 +303,10 @@ sn_status sn_create(const sn_camera* cam, int W, int H, const sn_params* pin, sn
         c->ws.den_pitch = ((size_t)W * 4 + 15) & ~(size_t)15;
         e = cudaMalloc(&c->ws.den, c->ws.den_pitch * H);
     }
+    if (e == cudaSuccess && p.learned) {
+        e = sn::gate_alloc(c->gate);
+        if (e == cudaSuccess) e = cudaMalloc(&c->gate_theta, sizeof(float) * sn::kGateParams);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         sn_destroy(c);
@@ -313,6 +326,8 @@ sn_status sn_destroy(sn_ctx* c) {
     }
     if (c->ws.err) cudaFree(c->ws.err);
     if (c->ws.den) cudaFree(c->ws.den);
+    if (c->gate.W1g) sn::gate_free(c->gate);
+    if (c->gate_theta) cudaFree(c->gate_theta);
     delete c;
     return SN_OK;
 }
@@ -409,15 +424,35 @@ sn_status sn_run_frame(sn_ctx* c, const sn_frame_in* in, sn_frame_out* out, sn_s
     fo.count = out->num_components;
     (void)den;
     (void)denp;
-    cudaError_t e = sn::launch_frame(c->geo, c->star, c->star8, in->disp, in->disp_pitch, fo, stream, mk);
+    sn::GateView gv{};
+    if (c->p.learned) {
+        if (!c->gate_loaded) return fail(c, SN_EINVAL, "learned context: gate weights not loaded");
+        gv = sn::GateView{c->gate.W1g, c->gate.W2g, c->gate.b1, c->gate.b2, c->gate.W3, c->gate.b3, c->p.tau};
+    }
+    cudaError_t e = sn::launch_frame(c->geo, c->star, c->star8, in->disp, in->disp_pitch, fo,
+                                     c->p.learned ? &gv : nullptr, stream, mk);
     c->launches += mk.launches;
     return e == cudaSuccess ? SN_OK : cuda_fail(c, e, "sn_run_frame");
 }
 
 sn_status sn_load_gate_weights(sn_ctx* c, const void* blob, size_t bytes) {
-    (void)blob;
-    (void)bytes;
-    return fail(c, SN_ENOTSUP, "learned gate not enabled in this context");
+    if (!c || !blob) return SN_EINVAL;
+    if (!c->p.learned) return fail(c, SN_EINVAL, "context was not created with learned = 1");
+    const unsigned char* b = static_cast<const unsigned char*>(blob);
+    const size_t need = 12 + sizeof(float) * (size_t)sn::kGateParams;
+    uint32_t ver = 0, n = 0;
+    if (bytes >= 12) {
+        memcpy(&ver, b + 4, 4);
+        memcpy(&n, b + 8, 4);
+    }
+    if (bytes < need || memcmp(b, "SNGW", 4) != 0 || ver != 1 || n != (uint32_t)sn::kGateParams)
+        return fail(c, SN_EINVAL, "not a version-1 gate weights blob of the expected size");
+    cudaError_t e = cudaMemcpy(c->gate_theta, b + 12, sizeof(float) * sn::kGateParams, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = sn::gate_layout(c->gate_theta, c->gate, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "sn_load_gate_weights");
+    c->gate_loaded = true;
+    return SN_OK;
 }
 
 sn_status sn_set_profiling(sn_ctx* c, int on) {

@@ -252,6 +252,39 @@ __device__ __forceinline__ short snorm16(float v) {
     return (short)__float2int_rn(32767.0f * fminf(fmaxf(v, -1.0f), 1.0f));
 }
 
+// ---------------------------------------------------------------- tensor cores
+// ldmatrix x4: four 8x8 b16 matrices; lane l gives the address of row l % 8
+// of matrix l / 8 (16-byte aligned rows in shared memory).
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+// D (16x8, fp32) += A (16x16, bf16, row) x B (16x8, bf16, col)
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// ---------------------------------------------------------------- learned gate
+// log2 of an integer disparity code (FP32)
+__device__ __forceinline__ float log2_code(int D) { return __log2f((float)D); }
+
+// Gate features of one pixel from its code and its right / lower
+// neighbours': log2 steps (0 where either pixel is invalid) and validity.
+// Training and inference both use this function.
+__device__ __forceinline__ void gate_feature(int Dc, int Dr, int Dd, float f[3]) {
+    const float Lc = Dc > 0 ? log2_code(Dc) : 0.0f;
+    f[0] = (Dc > 0 && Dr > 0) ? log2_code(Dr) - Lc : 0.0f;
+    f[1] = (Dc > 0 && Dd > 0) ? log2_code(Dd) - Lc : 0.0f;
+    f[2] = Dc > 0 ? 1.0f : 0.0f;
+}
+
 // ---------------------------------------------------------------- union-find
 // Parent arrays hold row-major pixel indices; parent[i] <= i always, so a
 // root is the smallest index of its tree.

@@ -7,6 +7,8 @@
 // test, which in reciprocal form reads 1/Dmin - 1/Dmax > K / (2^16 Dc).
 #include <atomic>
 
+#include <cuda_bf16.h>
+
 #include "sn_device.cuh"
 
 namespace sn {
@@ -276,12 +278,141 @@ __device__ __forceinline__ bool denoise_exact(const int2* c, int stride, int rd_
     return det > 0 && (long long)Dc * det + num > 0;
 }
 
-// VAR: 0 fixed window, 1 star table, 2 compile-time M = 8, s = 10 star.
-// R: halo radius at compile time (0 = runtime).  RD: denoise radius (0 = runtime).
+// Results of one pixel before they are stored.
+struct PixOut {
+    float n[3];
+    float P[3];
+    float dtil;
+    uint8_t m;
+};
+
+__device__ __forceinline__ void pix_zero(PixOut& r) {
+    r.n[0] = r.n[1] = r.n[2] = 0.0f;
+    r.P[0] = r.P[1] = r.P[2] = 0.0f;
+    r.dtil = 0.0f;
+    r.m = 0;
+}
+
+__device__ __forceinline__ void pix_points(const Geo& g, int x, int y, PixOut& r) {
+    const float inv = 1.0f / r.dtil;
+    r.P[0] = g.B * ((float)x - g.cx) * inv;
+    r.P[1] = g.B_fx_over_fy * ((float)y - g.cy) * inv;
+    r.P[2] = g.fxB * inv;
+}
+
+__device__ __forceinline__ void emit(const Geo& g, const FrameOut& o, int x, int y, const PixOut& r) {
+    if (o.den) reinterpret_cast<float*>(reinterpret_cast<char*>(o.den) + (size_t)y * o.denp)[x] = r.dtil;
+    if (g.normal_fmt == SN_NORMALS_F32X3) {
+        char* p0 = static_cast<char*>(o.nrm) + (size_t)y * o.np + (size_t)x * 4;
+        const size_t plane = (size_t)g.H * o.np;
+        *reinterpret_cast<float*>(p0) = r.n[0];
+        *reinterpret_cast<float*>(p0 + plane) = r.n[1];
+        *reinterpret_cast<float*>(p0 + 2 * plane) = r.n[2];
+    } else {
+        short4 q;
+        q.x = snorm16(r.n[0]);
+        q.y = snorm16(r.n[1]);
+        q.z = snorm16(r.n[2]);
+        q.w = 0;
+        reinterpret_cast<short4*>(static_cast<char*>(o.nrm) + (size_t)y * o.np)[x] = q;
+    }
+    char* p0 = reinterpret_cast<char*>(o.pts) + (size_t)y * o.pp + (size_t)x * 4;
+    const size_t plane = (size_t)g.H * o.pp;
+    *reinterpret_cast<float*>(p0) = r.P[0];
+    *reinterpret_cast<float*>(p0 + plane) = r.P[1];
+    *reinterpret_cast<float*>(p0 + 2 * plane) = r.P[2];
+    o.mask[(size_t)y * o.mp + x] = r.m;
+}
+
+// The plain per-pixel chain: range-gated denoise, support (fixed window or
+// star-fill), two-pass fit, normal, point.  c points at the pixel in the tile.
+template <int VAR, int R, int RD>
+__device__ __forceinline__ void plain_pixel(const Geo& g, const StarTable& T, const int2* c, int TWR, int x, int y,
+                                            PixOut& r) {
+    pix_zero(r);
+    const int2 cc = c[0];
+    const int Dc = cc.x;
+    if (Dc <= 0) return;
+    r.m = SN_MASK_VALID;
+    long long num, det;
+    const bool fit = denoise_exact<RD>(c, TWR, g.r_d, Dc, g.K_range, num, det);
+    const float dcf = fit ? i64_to_f32(num) / i64_to_f32(det) : 0.0f;
+    if (fit) r.m |= SN_MASK_DENOISED;
+    r.dtil = ((float)Dc + dcf) * (1.0f / 256.0f);
+    AffSums s;
+    if constexpr (VAR >= 2) {
+        static_assert(R == 10, "the M = 8, s = 10 star needs a halo of 10");
+        star8<10, kTW + 2 * R>(c, Dc, __int_as_float(cc.y), make_thr(g, Dc), s);
+    } else if constexpr (VAR == 1) {
+        star_table(c, TWR, Dc, __int_as_float(cc.y), make_thr(g, Dc), T, g.dirs, g.steps, s);
+    } else {
+        fixed_packed(c, TWR, g.r_a, Dc, s);
+    }
+    bool fp64;
+    if (solve_normal_dc(s, Dc, dcf, [=] { return fit ? (double)num / (double)det : 0.0; }, r.dtil, x, y, g, r.n,
+                        fp64))
+        r.m |= SN_MASK_NORMAL | (fp64 ? SN_MASK_FP64 : 0);
+    pix_points(g, x, y, r);
+}
+
+// The learned fast path of a certified pixel (its 9x9 window is one valid
+// surface): the 5x5 denoise window and the 9x9 affine window are full, so the
+// intercept is the 5x5 mean (S5 = sum of the 25 codes) and the moments are
+// those of the full window: N = 80, alpha = gamma = 540, beta = 0, first
+// moments 0; Bu, Bv are the window sums of u-offset and v-offset times D.
+__device__ __forceinline__ void fast_pixel(const Geo& g, int Dc, int Bu, int Bv, int S5, int x, int y, PixOut& r) {
+    pix_zero(r);
+    r.m = SN_MASK_VALID | SN_MASK_DENOISED | SN_MASK_LEARNED;
+    const int b0 = S5 - 25 * Dc;
+    const float dcf = (float)b0 / 25.0f;
+    r.dtil = ((float)Dc + dcf) * (1.0f / 256.0f);
+    AffSums s;
+    s.N = 80;
+    s.Su = s.Sv = s.Suv = 0;
+    s.Suu = s.Svv = 540;
+    s.Bu = Bu;
+    s.Bv = Bv;
+    bool fp64;
+    if (solve_normal_dc(s, Dc, dcf, [=] { return (double)b0 / 25.0; }, r.dtil, x, y, g, r.n, fp64))
+        r.m |= SN_MASK_NORMAL | (fp64 ? SN_MASK_FP64 : 0);
+    pix_points(g, x, y, r);
+}
+
+// Shared-memory layout of the learned variant (after the tile, the
+// union-find parents and the row masks; all offsets 16-byte aligned).
+constexpr int kFeatW = kTW + 8, kFeatH = kTH + 8;   // features: tile + 4
+constexpr int kH1W = kTW + 6, kH1H = kTH + 6;       // layer 1:  tile + 3
+constexpr int kQW = kTW + 4, kQH = kTH + 4;         // q:        tile + 2
+constexpr int kFeatN = kFeatW * kFeatH;             // 960 (+ 1 zero row)
+constexpr int kH1N = kH1W * kH1H;                   // 836
+constexpr int kH1Tiles = (kH1N + 15) / 16;          // 53
+constexpr int kQN = kQW * kQH;                      // 720 = 45 x 16
+constexpr int kW1Ld = 88, kW2Ld = 152;              // padded bf16 rows of the weights
+constexpr size_t align16z(size_t b) { return (b + 15) & ~(size_t)15; }
+
+struct LearnedSmem {
+    size_t m9, cnt, w1, w2, feat, h1, q, end;
+};
+__host__ __device__ constexpr LearnedSmem learned_layout(size_t base) {
+    LearnedSmem L{};
+    L.m9 = align16z(base);
+    L.cnt = L.m9 + 4 * 24;
+    L.w1 = align16z(L.cnt + 16);
+    L.w2 = align16z(L.w1 + 2 * 16 * kW1Ld);
+    L.feat = align16z(L.w2 + 2 * 16 * kW2Ld);
+    L.h1 = align16z(L.feat + 16 * (kFeatN + 1));
+    L.q = align16z(L.h1 + 32 * 16 * kH1Tiles);
+    L.end = align16z(L.q + 4 * kQN);
+    return L;
+}
+
+// VAR: 0 fixed window, 1 star table, 2 compile-time M = 8, s = 10 star,
+// 3 = 2 with the learned gate.  R: halo radius at compile time (0 = runtime).
+// RD: denoise radius (0 = runtime).
 template <int IN, int VAR, int R, int RD>
 __global__ void __launch_bounds__(kThreads, 2)
     k_frame(const Geo g, const __grid_constant__ StarTable T, const char* __restrict__ disp, size_t dp,
-            const FrameOut o) {
+            const FrameOut o, const GateView gv) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : g.steps);
     const int TWR = kTW + 2 * Rr, THR = kTH + 2 * Rr;
@@ -306,8 +437,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const bool inside = x < g.W && y < g.H;
     const int2* c = tile + (threadIdx.y + Rr) * TWR + threadIdx.x + Rr;
-    const int2 cc = c[0];
-    const int Dc = cc.x;  // 0 outside the image
+    const int Dc = c[0].x;  // 0 outside the image
 
     // ---- tile-local components, part 1: each tile row is one warp; the
     // pixels joined to their left neighbour form runs, labelled by the run's
@@ -322,59 +452,186 @@ __global__ void __launch_bounds__(kThreads, 2)
     Ls[tid] = Dc > 0 ? run : -1;
     if (lane == 0) Lrow[row] = Lb;
 
-    if (inside) {
-        float nrm[3] = {0.0f, 0.0f, 0.0f};
-        float P[3] = {0.0f, 0.0f, 0.0f};
-        float dtil = 0.0f;
-        uint8_t m = 0;
-        if (Dc > 0) {
-            m = SN_MASK_VALID;
-            long long num, det;
-            const bool fit = denoise_exact<RD>(c, TWR, g.r_d, Dc, g.K_range, num, det);
-            const float dcf = fit ? i64_to_f32(num) / i64_to_f32(det) : 0.0f;
-            if (fit) m |= SN_MASK_DENOISED;
-            dtil = ((float)Dc + dcf) * (1.0f / 256.0f);
-            AffSums s;
-            if constexpr (VAR == 2) {
-                static_assert(R == 10, "the M = 8, s = 10 star needs a halo of 10");
-                star8<10, kTW + 2 * R>(c, Dc, __int_as_float(cc.y), make_thr(g, Dc), s);
-            } else if constexpr (VAR == 1) {
-                star_table(c, TWR, Dc, __int_as_float(cc.y), make_thr(g, Dc), T, g.dirs, g.steps, s);
-            } else {
-                fixed_packed(c, TWR, g.r_a, Dc, s);
-            }
-            bool fp64;
-            if (solve_normal_dc(
-                    s, Dc, dcf, [=] { return fit ? (double)num / (double)det : 0.0; }, dtil, x, y, g, nrm, fp64))
-                m |= SN_MASK_NORMAL | (fp64 ? SN_MASK_FP64 : 0);
-            const float inv = 1.0f / dtil;
-            P[0] = g.B * ((float)x - g.cx) * inv;
-            P[1] = g.B_fx_over_fy * ((float)y - g.cy) * inv;
-            P[2] = g.fxB * inv;
+    if constexpr (VAR != 3) {
+        if (inside) {
+            PixOut r;
+            plain_pixel<VAR, R, RD>(g, T, c, TWR, x, y, r);
+            emit(g, o, x, y, r);
         }
-        if (o.den) reinterpret_cast<float*>(reinterpret_cast<char*>(o.den) + (size_t)y * o.denp)[x] = dtil;
-        if (g.normal_fmt == SN_NORMALS_F32X3) {
-            char* p0 = static_cast<char*>(o.nrm) + (size_t)y * o.np + (size_t)x * 4;
-            const size_t plane = (size_t)g.H * o.np;
-            *reinterpret_cast<float*>(p0) = nrm[0];
-            *reinterpret_cast<float*>(p0 + plane) = nrm[1];
-            *reinterpret_cast<float*>(p0 + 2 * plane) = nrm[2];
-        } else {
-            short4 q;
-            q.x = snorm16(nrm[0]);
-            q.y = snorm16(nrm[1]);
-            q.z = snorm16(nrm[2]);
-            q.w = 0;
-            reinterpret_cast<short4*>(static_cast<char*>(o.nrm) + (size_t)y * o.np)[x] = q;
-        }
+    } else {
+        // ================= learned gate (tensor cores), then the two paths
+        constexpr int TW = kTW + 2 * R;
+        constexpr LearnedSmem L = learned_layout(sizeof(int2) * (size_t)(kTW + 2 * R) * (kTH + 2 * R) +
+                                                 sizeof(int) * (kThreads + kTH));
+        unsigned* m9 = reinterpret_cast<unsigned*>(smem + L.m9);
+        int* cnt = reinterpret_cast<int*>(smem + L.cnt);
+        __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(smem + L.w1);
+        __nv_bfloat16* W2s = reinterpret_cast<__nv_bfloat16*>(smem + L.w2);
+        uint4* feat = reinterpret_cast<uint4*>(smem + L.feat);
+        unsigned* h1w = reinterpret_cast<unsigned*>(smem + L.h1);  // 8 words (16 bf16) per pixel
+        float* qs = reinterpret_cast<float*>(smem + L.q);
+        const int warp = tid >> 5;
+        // weights into shared memory (rows padded for conflict-free ldmatrix)
         {
-            char* p0 = reinterpret_cast<char*>(o.pts) + (size_t)y * o.pp + (size_t)x * 4;
-            const size_t plane = (size_t)g.H * o.pp;
-            *reinterpret_cast<float*>(p0) = P[0];
-            *reinterpret_cast<float*>(p0 + plane) = P[1];
-            *reinterpret_cast<float*>(p0 + 2 * plane) = P[2];
+            const unsigned* w1 = reinterpret_cast<const unsigned*>(gv.W1g);
+            const unsigned* w2 = reinterpret_cast<const unsigned*>(gv.W2g);
+            unsigned* w1s = reinterpret_cast<unsigned*>(W1s);
+            unsigned* w2s = reinterpret_cast<unsigned*>(W2s);
+            for (int i = tid; i < 16 * 40; i += kThreads) w1s[(i / 40) * (kW1Ld / 2) + i % 40] = __ldg(w1 + i);
+            for (int i = tid; i < 16 * 72; i += kThreads) w2s[(i / 72) * (kW2Ld / 2) + i % 72] = __ldg(w2 + i);
         }
-        o.mask[(size_t)y * o.mp + x] = m;
+        // features of the tile + 4 region; feat[kFeatN] is a zero row
+        for (int i = tid; i <= kFeatN; i += kThreads) {
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (i < kFeatN) {
+                const int fx = i % kFeatW - 4, fy = i / kFeatW - 4;
+                const int2* p = tile + (fy + R) * TW + fx + R;
+                float f[3];
+                gate_feature(p[0].x, p[1].x, p[TW].x, f);
+                const __nv_bfloat162 a = __floats2bfloat162_rn(f[0], f[1]);
+                const __nv_bfloat162 b = __floats2bfloat162_rn(f[2], 0.0f);
+                v.x = *reinterpret_cast<const unsigned*>(&a);
+                v.y = *reinterpret_cast<const unsigned*>(&b);
+            }
+            feat[i] = v;
+        }
+        // per tile-halo row: bit u set iff columns u - 4 .. u + 4 are all valid
+        for (int r = warp; r < 24; r += kThreads / 32) {
+            const int2* p = tile + (r - 4 + R) * TW + R - 4;
+            const unsigned lo = __ballot_sync(0xffffffffu, p[lane].x > 0);
+            const unsigned hi = __ballot_sync(0xffffffffu, lane <= 8 && p[32 + lane].x > 0);
+            const unsigned long long M = (unsigned long long)lo | ((unsigned long long)hi << 32);
+            unsigned long long a = M;
+#pragma unroll
+            for (int k = 1; k <= 8; k++) a &= M >> k;
+            if (lane == 0) m9[r] = (unsigned)a;
+        }
+        if (tid == 0) *cnt = 0;
+        __syncthreads();
+
+        const int gq = lane >> 2, tq = lane & 3;
+        // layer 1: h1 = relu(conv3x3(feat) W1 + b1) on the tile + 3 region
+        for (int mt = warp; mt < kH1Tiles; mt += kThreads / 32) {
+            const int r = mt * 16 + (lane & 15);
+            const int hx = r % kH1W, hy = r / kH1W;
+            float acc0[4] = {0, 0, 0, 0}, acc1[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int s = 0; s < 5; s++) {
+                const int tap = 2 * s + (lane >> 4);
+                const int fi = (r < kH1N && tap < 9) ? (hy + tap / 3) * kFeatW + hx + tap % 3 : kFeatN;
+                unsigned a[4], b[4];
+                ldsm_x4(a, feat + fi);
+                ldsm_x4(b, W1s + ((lane & 7) + ((lane >> 4) << 3)) * kW1Ld + 16 * s + ((lane >> 3) & 1) * 8);
+                mma_bf16(acc0, a, b[0], b[1]);
+                mma_bf16(acc1, a, b[2], b[3]);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int rr = mt * 16 + gq + 8 * h;
+                if (rr < kH1N) {
+                    const __nv_bfloat162 v0 = __floats2bfloat162_rn(fmaxf(acc0[2 * h] + __ldg(gv.b1 + 2 * tq), 0.0f),
+                                                                    fmaxf(acc0[2 * h + 1] + __ldg(gv.b1 + 2 * tq + 1), 0.0f));
+                    const __nv_bfloat162 v1 = __floats2bfloat162_rn(fmaxf(acc1[2 * h] + __ldg(gv.b1 + 8 + 2 * tq), 0.0f),
+                                                                    fmaxf(acc1[2 * h + 1] + __ldg(gv.b1 + 9 + 2 * tq), 0.0f));
+                    h1w[rr * 8 + tq] = *reinterpret_cast<const unsigned*>(&v0);
+                    h1w[rr * 8 + 4 + tq] = *reinterpret_cast<const unsigned*>(&v1);
+                }
+            }
+        }
+        __syncthreads();
+        // layer 2 and head: q = sigmoid(relu(conv3x3(h1) W2 + b2) . W3 + b3) on the tile + 2 region
+        for (int mt = warp; mt < kQN / 16; mt += kThreads / 32) {
+            const int r = mt * 16 + (lane & 15);
+            const int qx = r % kQW, qy = r / kQW;
+            float acc0[4] = {0, 0, 0, 0}, acc1[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int tap = 0; tap < 9; tap++) {
+                const int hi = (qy + tap / 3) * kH1W + qx + tap % 3;
+                unsigned a[4], b[4];
+                ldsm_x4(a, h1w + hi * 8 + (lane >> 4) * 4);
+                ldsm_x4(b, W2s + ((lane & 7) + ((lane >> 4) << 3)) * kW2Ld + 16 * tap + ((lane >> 3) & 1) * 8);
+                mma_bf16(acc0, a, b[0], b[1]);
+                mma_bf16(acc1, a, b[2], b[3]);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int c0 = 2 * tq, c1 = 8 + 2 * tq;
+                float part = __ldg(gv.W3 + c0) * fmaxf(acc0[2 * h] + __ldg(gv.b2 + c0), 0.0f) +
+                             __ldg(gv.W3 + c0 + 1) * fmaxf(acc0[2 * h + 1] + __ldg(gv.b2 + c0 + 1), 0.0f) +
+                             __ldg(gv.W3 + c1) * fmaxf(acc1[2 * h] + __ldg(gv.b2 + c1), 0.0f) +
+                             __ldg(gv.W3 + c1 + 1) * fmaxf(acc1[2 * h + 1] + __ldg(gv.b2 + c1 + 1), 0.0f);
+                part += __shfl_xor_sync(0xffffffffu, part, 1);
+                part += __shfl_xor_sync(0xffffffffu, part, 2);
+                if (tq == 0) qs[mt * 16 + gq + 8 * h] = 1.0f / (1.0f + __expf(-(part + __ldg(gv.b3))));
+            }
+        }
+        __syncthreads();
+        // gate: min of q over the 5x5 neighbourhood >= tau and the 9x9 window all valid
+        bool gated = false;
+        if (inside && Dc > 0) {
+            float qmin = qs[row * kQW + lane];
+#pragma unroll
+            for (int oy = 0; oy < 5; oy++)
+#pragma unroll
+                for (int ox = 0; ox < 5; ox++) qmin = fminf(qmin, qs[(row + oy) * kQW + lane + ox]);
+            unsigned allv = 0xffffffffu;
+#pragma unroll
+            for (int j = 0; j < 9; j++) allv &= m9[row + j];
+            gated = qmin >= gv.tau && ((allv >> lane) & 1u);
+        }
+        const bool any = __syncthreads_or(gated);
+        int* rs = reinterpret_cast<int*>(smem + L.feat);  // features are dead: row sums
+        int* list = reinterpret_cast<int*>(smem + L.h1);   // layer 1 is dead: work list
+        if (any) {
+            // row sums over the tile +- 4 rows: R0 = sum D, R1 = sum u D (|u| <= 4), R5 = sum D (|u| <= 2)
+            for (int e = tid; e < 24 * kTW; e += kThreads) {
+                const int rr = e / kTW, cx = e % kTW;
+                const int2* p = tile + (rr - 4 + R) * TW + cx + R;
+                int s0 = 0, s1 = 0, s5 = 0;
+#pragma unroll
+                for (int u = -4; u <= 4; u++) {
+                    const int D = p[u].x;
+                    s0 += D;
+                    s1 += u * D;
+                    if (u >= -2 && u <= 2) s5 += D;
+                }
+                rs[e] = s0;
+                rs[24 * kTW + e] = s1;
+                rs[48 * kTW + e] = s5;
+            }
+        }
+        __syncthreads();
+        if (inside) {
+            if (gated) {
+                int Bu = 0, Bv = 0, S5 = 0;
+#pragma unroll
+                for (int j = 0; j < 9; j++) {
+                    const int e = (row + j) * kTW + lane;
+                    Bu += rs[24 * kTW + e];
+                    Bv += (j - 4) * rs[e];
+                    if (j >= 2 && j <= 6) S5 += rs[48 * kTW + e];
+                }
+                PixOut r;
+                fast_pixel(g, Dc, Bu, Bv, S5, x, y, r);
+                emit(g, o, x, y, r);
+            } else if (Dc > 0) {
+                list[atomicAdd(cnt, 1)] = tid;
+            } else {
+                PixOut r;
+                pix_zero(r);
+                emit(g, o, x, y, r);
+            }
+        }
+        __syncthreads();
+        // the uncertified pixels, packed so that whole warps walk star rays
+        const int nl = *cnt;
+        for (int i = tid; i < nl; i += kThreads) {
+            const int p = list[i];
+            const int px = p % kTW, py = p / kTW;
+            PixOut r;
+            plain_pixel<VAR, R, RD>(g, T, tile + (py + R) * TW + px + R, TW, x0 + px, y0 + py, r);
+            emit(g, o, x0 + px, y0 + py, r);
+        }
     }
 
     // ---- tile-local components, part 2: join the runs of adjacent rows.  A
@@ -418,25 +675,28 @@ cudaError_t smem_limit_once(Kernel k, size_t bytes, std::atomic<unsigned long lo
 }
 
 template <int IN, int VAR, int R, int RD>
-cudaError_t launch_in(const Geo& g, const StarTable& t, const char* d, size_t dp, const FrameOut& o, cudaStream_t s) {
+cudaError_t launch_in(const Geo& g, const StarTable& t, const char* d, size_t dp, const FrameOut& o,
+                      const GateView& gv, cudaStream_t s) {
     constexpr int Rmax = R > 0 ? R : (VAR == 0 ? 15 : kMaxSteps);
     const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : g.steps);
+    const size_t bytes = VAR == 3 ? learned_layout(frame_smem(R)).end : frame_smem(Rr);
+    const size_t bytes_max = VAR == 3 ? learned_layout(frame_smem(R)).end : frame_smem(Rmax);
     const dim3 grid((g.W + kTW - 1) / kTW, (g.H + kTH - 1) / kTH), block(kTW, kTH);
     static std::atomic<unsigned long long> done{0};
-    const cudaError_t e = smem_limit_once(k_frame<IN, VAR, R, RD>, frame_smem(Rmax), done);
+    const cudaError_t e = smem_limit_once(k_frame<IN, VAR, R, RD>, bytes_max, done);
     if (e != cudaSuccess) return e;
-    k_frame<IN, VAR, R, RD><<<grid, block, frame_smem(Rr), s>>>(g, t, d, dp, o);
+    k_frame<IN, VAR, R, RD><<<grid, block, bytes, s>>>(g, t, d, dp, o, gv);
     return cudaGetLastError();
 }
 
 template <int VAR, int R, int RD>
 cudaError_t launch_var(const Geo& g, const StarTable& t, const void* disp, size_t dp, const FrameOut& o,
-                       cudaStream_t s) {
+                       const GateView& gv, cudaStream_t s) {
     const char* d = static_cast<const char*>(disp);
     switch (g.in_dtype) {
-        case SN_IN_F32: return launch_in<SN_IN_F32, VAR, R, RD>(g, t, d, dp, o, s);
-        case SN_IN_F16: return launch_in<SN_IN_F16, VAR, R, RD>(g, t, d, dp, o, s);
-        default: return launch_in<SN_IN_U16X256, VAR, R, RD>(g, t, d, dp, o, s);
+        case SN_IN_F32: return launch_in<SN_IN_F32, VAR, R, RD>(g, t, d, dp, o, gv, s);
+        case SN_IN_F16: return launch_in<SN_IN_F16, VAR, R, RD>(g, t, d, dp, o, gv, s);
+        default: return launch_in<SN_IN_U16X256, VAR, R, RD>(g, t, d, dp, o, gv, s);
     }
 }
 
@@ -462,14 +722,18 @@ bool star_is_m8(const StarTable& t, int dirs, int steps) {
 }
 
 cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const void* disp, size_t dp,
-                         const FrameOut& o, cudaStream_t s, Marks& mk) {
+                         const FrameOut& o, const GateView* gv, cudaStream_t s, Marks& mk) {
     cudaError_t e;
-    if (g.support == SN_SUPPORT_STARFILL_CD && star8)
-        e = g.r_d == 2 ? launch_var<2, 10, 2>(g, t, disp, dp, o, s) : launch_var<2, 10, 0>(g, t, disp, dp, o, s);
+    const GateView none{};
+    if (gv && star8 && g.r_d == 2)
+        e = launch_var<3, 10, 2>(g, t, disp, dp, o, *gv, s);
+    else if (g.support == SN_SUPPORT_STARFILL_CD && star8)
+        e = g.r_d == 2 ? launch_var<2, 10, 2>(g, t, disp, dp, o, none, s)
+                       : launch_var<2, 10, 0>(g, t, disp, dp, o, none, s);
     else if (g.support == SN_SUPPORT_STARFILL_CD)
-        e = launch_var<1, 0, 0>(g, t, disp, dp, o, s);
+        e = launch_var<1, 0, 0>(g, t, disp, dp, o, none, s);
     else
-        e = launch_var<0, 0, 0>(g, t, disp, dp, o, s);
+        e = launch_var<0, 0, 0>(g, t, disp, dp, o, none, s);
     mk.after(s);
     if (e != cudaSuccess) return e;
     return launch_ccl_merge_flatten(g, disp, dp, o.labels, o.lp, o.count, kTW, kTH, s, mk);

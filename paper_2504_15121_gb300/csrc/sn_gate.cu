@@ -14,6 +14,7 @@
 
 #include <new>
 
+#include "sn_device.cuh"
 #include "sn_gate_internal.h"
 
 namespace sn {
@@ -25,21 +26,6 @@ namespace sn {
 namespace {
 
 constexpr int kGM = 64, kGN = 16, kGK = 16, kLd = 24;  // smem row stride (bf16), conflict-free ldmatrix
-
-__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void* p) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(a));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
 
 __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const __nv_bfloat16* __restrict__ A, long long sam,
                                               long long sak, const __nv_bfloat16* __restrict__ B, long long sbk,
@@ -91,18 +77,6 @@ cudaError_t gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, long long sam
     const dim3 grid((M + kGM - 1) / kGM, (N + kGN - 1) / kGN);
     k_gemm<<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc);
     return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------ features
-// log2 of an integer code (exact for powers of two, FP32 elsewhere)
-__device__ __forceinline__ float log2_code(int D) { return __log2f((float)D); }
-
-// f(p) of one pixel from its code and its right / lower neighbours'.
-__device__ __forceinline__ void gate_feature(int Dc, int Dr, int Dd, float f[3]) {
-    const float Lc = Dc > 0 ? log2_code(Dc) : 0.0f;
-    f[0] = (Dc > 0 && Dr > 0) ? log2_code(Dr) - Lc : 0.0f;
-    f[1] = (Dc > 0 && Dd > 0) ? log2_code(Dd) - Lc : 0.0f;
-    f[2] = Dc > 0 ? 1.0f : 0.0f;
 }
 
 namespace {

@@ -1,6 +1,7 @@
 // Internal declarations shared by the C-ABI layer and the kernels.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -112,8 +113,19 @@ struct FrameOut {
 };
 constexpr int kFrameTW = 32;
 constexpr int kFrameTH = 16;
+// Learned gate weights as the frame kernel reads them (device pointers).
+struct GateView {
+    const __nv_bfloat16* W1g;  // [16][80]
+    const __nv_bfloat16* W2g;  // [16][144]
+    const float* b1;
+    const float* b2;
+    const float* W3;
+    const float* b3;
+    float tau;
+};
+// gv == nullptr: plain chain; otherwise the learned variant (star M = 8, s = 10, r_d = 2).
 cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const void* disp, size_t dp,
-                         const FrameOut& o, cudaStream_t s, Marks& mk);
+                         const FrameOut& o, const GateView* gv, cudaStream_t s, Marks& mk);
 bool star_is_m8(const StarTable& t, int dirs, int steps);
 
 }  // namespace sn

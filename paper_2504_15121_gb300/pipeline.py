@@ -40,10 +40,17 @@ _IN_DTYPE = {torch.float32: sn.SN_IN_F32, torch.float16: sn.SN_IN_F16, torch.int
 class Pipeline:
     """One sn_ctx for W x H frames with fixed camera and parameters."""
 
-    def __init__(self, cam, W: int, H: int, **params):
+    def __init__(self, cam, W: int, H: int, gate_weights=None, **params):
+        """params: fields of sn_params.  learned=1 loads the gate weights
+        (gate_weights: path or bytes; default: the packaged trained weights)."""
         self.W, self.H = W, H
         self.params = sn.default_params(**params)
         self.ctx = sn.sn_create(cam, W, H, self.params)
+        if self.params.learned:
+            from . import gate
+            blob = gate_weights if isinstance(gate_weights, (bytes, bytearray)) else \
+                open(gate_weights or gate.DEFAULT_WEIGHTS, "rb").read()
+            sn.sn_load_gate_weights(self.ctx, bytes(blob))
 
     def close(self):
         if self.ctx:

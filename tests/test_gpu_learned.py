@@ -1,0 +1,85 @@
+"""Learned form on the GPU (trained weights from paper_2504_15121_gb300/weights).
+
+* gate decisions: the GPU's certified pixels (mask bit LEARNED) equal the
+  FP64 oracle network's (oracle/gate.py with the same BF16 roundings of
+  weights, features and layer-1 activations) wherever the oracle's minimum q
+  is not within 5e-3 of tau -- the FP32 accumulation order and the FP32 log2
+  of the features may move q by ~1e-4 and only decide ties at tau;
+* given those decisions the whole chain matches the oracle with the parity
+  tolerances of tests/parity.py (masks and labels bit-exact);
+* the gain: on each test scene the learned form certifies most pixels and
+  its mean angular error against the generator's ground truth is no worse
+  than the plain form's (the full 9x9 window has more samples than the star).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import gate as ogate
+from scenes import make_scene
+from parity import angle_deg, compare_frame, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+TAU = 0.9
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_15121_gb300 as P
+    return P
+
+
+def gt_error(n, mask, scene):
+    ok = ((mask & oracle.M_NORMAL) > 0) & ~scene.background
+    return float(angle_deg(n[ok], scene.gt_normal[ok].astype(np.float64)).mean()), int(ok.sum())
+
+
+@pytest.mark.parametrize("name,frame", [("planes_640x480", 4), ("mixed_1482x994", 4), ("driving_2048x1024", 4)])
+def test_learned_gate_and_chain(P, name, frame):
+    from paper_2504_15121_gb300 import gate as G
+    theta = G.load_weights().astype(np.float64)
+    s = make_scene(name, frame=frame)
+    pipe = P.Pipeline(s.camera, s.W, s.H, learned=1)
+    try:
+        g = run_gpu(pipe, s.disp)
+    finally:
+        pipe.close()
+    gpu_gate = (g["mask"] & oracle.M_LEARNED) > 0
+    D = oracle.ingest(s.disp)
+    og, q, qmin = ogate.gate_image(D, theta, TAU)
+    clear = np.abs(qmin - TAU) >= 5e-3
+    bad = (gpu_gate != og) & clear
+    assert not bad.any(), (int(bad.sum()), np.argwhere(bad)[:5])
+    ref = oracle.run_frame(s.disp, s.camera, gate=gpu_gate)
+    compare_frame(g, ref)
+    plain_ref = oracle.run_frame(s.disp, s.camera)
+    e_learned, n_learned = gt_error(g["normals"], g["mask"], s)
+    e_plain, n_plain = gt_error(plain_ref.normals, plain_ref.mask, s)
+    frac = gpu_gate.sum() / max((D > 0).sum(), 1)
+    print(f"{name}: certified {frac:.3f}, ambiguous {(~clear).sum()}, GT error learned {e_learned:.3f} deg "
+          f"({n_learned}) vs plain {e_plain:.3f} deg ({n_plain})")
+    assert frac > 0.3
+    assert n_learned >= n_plain
+    assert e_learned <= e_plain + 0.05
+
+
+def test_learned_needs_weights_and_default_star(P):
+    sn = P.sn
+    s = make_scene("planes_320x240", frame=0)
+    with pytest.raises(sn.SnError) as ei:
+        sn.sn_create(s.camera, s.W, s.H, sn.default_params(learned=1, dirs=16))
+    assert ei.value.status == sn.SN_ENOTSUP
+    ctx = sn.sn_create(s.camera, s.W, s.H, sn.default_params(learned=1))
+    try:
+        pipe_out = P.FrameBuffers.allocate(s.W, s.H)
+        disp = sn.empty_image(s.H, s.W, __import__("torch").float32, fill=1.0)
+        with pytest.raises(sn.SnError) as ei:
+            sn.sn_run_frame(ctx, disp, pipe_out.normals, pipe_out.points, pipe_out.labels, pipe_out.mask)
+        assert ei.value.status == sn.SN_EINVAL
+        with pytest.raises(sn.SnError):
+            sn.sn_load_gate_weights(ctx, b"SNGW" + bytes(20))
+    finally:
+        sn.sn_destroy(ctx)

@@ -538,3 +538,31 @@ def test_run_frame_on_noiseless_plane():
     inner = (slice(1, -1), slice(1, -1))
     assert np.linalg.norm(fr.normals[inner] - gt[inner], axis=-1).max() < 1e-9
     assert (fr.mask & 0x17 == 0x13).all()  # valid | normal | denoised, no FP64 flag
+
+
+def test_gated_chain_is_box_mean_and_full_window():
+    # a certified pixel takes every valid sample of the 5x5 window (the box
+    # mean, no range gate) and the fixed 9x9 window as its support
+    rng = np.random.default_rng(12)
+    H, W = 30, 40
+    D = (20000 + 40 * np.arange(W)[None, :] - 25 * np.arange(H)[:, None]
+         + rng.integers(-300, 300, (H, W))).astype(np.int32)
+    D[rng.random((H, W)) < 0.03] = 0
+    disp = (D / 256.0).astype(np.float32)
+    gate = np.zeros((H, W), bool)
+    gate[6:-6, 6:-6] = True
+    gate &= D > 0
+    fr = oracle.run_frame(disp, CAM, gate=gate)
+    fixed = oracle.run_frame(disp, CAM, Params(support=FIXED, r_affine=4, k_range=1.0))
+    from numpy.lib.stride_tricks import sliding_window_view
+    vals = sliding_window_view(np.pad(D, 2) / 256.0, (5, 5))
+    cnt = sliding_window_view(np.pad(D > 0, 2), (5, 5)).sum((-1, -2))
+    box = vals.sum((-1, -2)) / np.maximum(cnt, 1)
+    g = gate & (fr.mask & 16 > 0)
+    assert np.abs(fr.den[g] - fixed.den[g]).max() < 1e-9
+    full = g & (cnt == 25)
+    assert np.abs(fr.den[full] - box[full]).max() < 1e-9
+    assert np.abs(fr.normals[g] - fixed.normals[g]).max() < 1e-12
+    assert ((fr.mask[gate] & oracle.M_LEARNED) > 0).all() and not (fr.mask[~gate] & oracle.M_LEARNED).any()
+    plain = oracle.run_frame(disp, CAM)
+    assert np.array_equal(fr.normals[~gate], plain.normals[~gate])
