@@ -17,8 +17,9 @@ the method is differentiable apart from the adaptive support, Sec. I-C):
   z  = relu(conv3x3(h1) W2 + b2)         16 channels
   q  = sigmoid(z . W3 + b3)              P(the 5x5 patch at p is one valid surface)
   conv3x3: out(p) = sum over o in {-1,0,1}^2 of W[(o_v+1)*3 + (o_u+1)] in(p + o).
-  gate(p) = (min over |o|_inf <= 2 of q(p + o) >= tau) and the 9x9 window at
-  p is entirely valid.
+  gate(p) = (min over |o|_inf <= 2 of q(p + o) >= tau) and p is valid.
+  Label of a patch: at least 13 of its 25 pixels are valid (pixels outside
+  the image are invalid) and all its valid pixels show one primitive.
 
 Weight layout: W1[16][9][8], W2[16][9][16], W3[16], b1[16], b2[16], b3.
 The GPU runs features, weights and layer-1 activations in BF16 with FP32
@@ -133,12 +134,7 @@ def gate_image(D, theta, tau, round_bf16=True):
     for oy in range(5):
         for ox in range(5):
             qmin = np.minimum(qmin, qp[oy:oy + H, ox:ox + W])
-    valid = np.pad(D > 0, 4, constant_values=False)
-    allv = np.ones((H, W), bool)
-    for oy in range(9):
-        for ox in range(9):
-            allv &= valid[oy:oy + H, ox:ox + W]
-    return (qmin >= tau) & allv, q, qmin
+    return (qmin >= tau) & (D > 0), q, qmin
 
 
 # ---------------------------------------------------------------- patches (training)
@@ -200,14 +196,20 @@ def loss_and_grad(Dp, y, theta):
 
 
 def patch_labels(prim, valid):
-    """1 where the 5x5 patch centred at a pixel is all valid and of one
-    primitive (generator ground truth), else 0; [H, W] -> [H, W]."""
+    """1 where the 5x5 patch centred at a pixel has at least 13 valid pixels
+    (outside the image: invalid) and all of them show one primitive
+    (generator ground truth), else 0; [H, W] -> [H, W]."""
     H, W = prim.shape
     pp = np.pad(prim, 2, constant_values=-2)
     vp = np.pad(valid, 2, constant_values=False)
-    lab = np.ones((H, W), bool)
-    c = prim
+    cnt = np.zeros((H, W), int)
+    lo = np.full((H, W), np.iinfo(np.int64).max)
+    hi = np.full((H, W), np.iinfo(np.int64).min)
     for oy in range(5):
         for ox in range(5):
-            lab &= vp[oy:oy + H, ox:ox + W] & (pp[oy:oy + H, ox:ox + W] == c)
-    return lab
+            v = vp[oy:oy + H, ox:ox + W]
+            p = pp[oy:oy + H, ox:ox + W].astype(np.int64)
+            cnt += v
+            lo = np.where(v, np.minimum(lo, p), lo)
+            hi = np.where(v, np.maximum(hi, p), hi)
+    return (cnt >= 13) & (lo == hi)

@@ -355,25 +355,42 @@ __device__ __forceinline__ void plain_pixel(const Geo& g, const StarTable& T, co
     pix_points(g, x, y, r);
 }
 
-// The learned fast path of a certified pixel (its 9x9 window is one valid
-// surface): the 5x5 denoise window and the 9x9 affine window are full, so the
-// intercept is the 5x5 mean (S5 = sum of the 25 codes) and the moments are
-// those of the full window: N = 80, alpha = gamma = 540, beta = 0, first
-// moments 0; Bu, Bv are the window sums of u-offset and v-offset times D.
-__device__ __forceinline__ void fast_pixel(const Geo& g, int Dc, int Bu, int Bv, int S5, int x, int y, PixOut& r) {
+// Sums over the valid samples of a square window around a pixel (offsets
+// u, v): moments and the data sums of D, u D, v D.
+struct WinSums {
+    int n, Su, Sv, Suu, Suv, Svv, SD, SuD, SvD;
+};
+
+// The learned fast path of a certified pixel (its 9x9 window shows one
+// surface): the denoise fit takes every valid sample of the 5x5 window (no
+// range gate) and the affine fit every valid sample of the 9x9 window
+// except the centre (no star-fill).
+__device__ __forceinline__ void fast_pixel(const Geo& g, int Dc, const WinSums& w2, const WinSums& w4, int x, int y,
+                                           PixOut& r) {
     pix_zero(r);
-    r.m = SN_MASK_VALID | SN_MASK_DENOISED | SN_MASK_LEARNED;
-    const int b0 = S5 - 25 * Dc;
-    const float dcf = (float)b0 / 25.0f;
+    r.m = SN_MASK_VALID | SN_MASK_LEARNED;
+    const int b0 = w2.SD - w2.n * Dc, b1 = w2.SuD - w2.Su * Dc, b2 = w2.SvD - w2.Sv * Dc;
+    const long long M00 = (long long)w2.Suu * w2.Svv - (long long)w2.Suv * w2.Suv;
+    const long long M10 = (long long)w2.Su * w2.Svv - (long long)w2.Sv * w2.Suv;
+    const long long M20 = (long long)w2.Su * w2.Suv - (long long)w2.Sv * w2.Suu;
+    const long long det = w2.n * M00 - w2.Su * M10 + w2.Sv * M20;
+    const long long num = b0 * M00 - b1 * M10 + b2 * M20;
+    const bool fit = det > 0 && (long long)Dc * det + num > 0;
+    const float dcf = fit ? i64_to_f32(num) / i64_to_f32(det) : 0.0f;
+    if (fit) r.m |= SN_MASK_DENOISED;
     r.dtil = ((float)Dc + dcf) * (1.0f / 256.0f);
     AffSums s;
-    s.N = 80;
-    s.Su = s.Sv = s.Suv = 0;
-    s.Suu = s.Svv = 540;
-    s.Bu = Bu;
-    s.Bv = Bv;
+    s.N = w4.n - 1;
+    s.Su = w4.Su;
+    s.Sv = w4.Sv;
+    s.Suu = w4.Suu;
+    s.Suv = w4.Suv;
+    s.Svv = w4.Svv;
+    s.Bu = w4.SuD - Dc * w4.Su;
+    s.Bv = w4.SvD - Dc * w4.Sv;
     bool fp64;
-    if (solve_normal_dc(s, Dc, dcf, [=] { return (double)b0 / 25.0; }, r.dtil, x, y, g, r.n, fp64))
+    if (solve_normal_dc(s, Dc, dcf, [=] { return fit ? (double)num / (double)det : 0.0; }, r.dtil, x, y, g, r.n,
+                        fp64))
         r.m |= SN_MASK_NORMAL | (fp64 ? SN_MASK_FP64 : 0);
     pix_points(g, x, y, r);
 }
@@ -463,7 +480,6 @@ __global__ void __launch_bounds__(kThreads, 2)
         constexpr int TW = kTW + 2 * R;
         constexpr LearnedSmem L = learned_layout(sizeof(int2) * (size_t)(kTW + 2 * R) * (kTH + 2 * R) +
                                                  sizeof(int) * (kThreads + kTH));
-        unsigned* m9 = reinterpret_cast<unsigned*>(smem + L.m9);
         int* cnt = reinterpret_cast<int*>(smem + L.cnt);
         __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(smem + L.w1);
         __nv_bfloat16* W2s = reinterpret_cast<__nv_bfloat16*>(smem + L.w2);
@@ -494,17 +510,6 @@ __global__ void __launch_bounds__(kThreads, 2)
                 v.y = *reinterpret_cast<const unsigned*>(&b);
             }
             feat[i] = v;
-        }
-        // per tile-halo row: bit u set iff columns u - 4 .. u + 4 are all valid
-        for (int r = warp; r < 24; r += kThreads / 32) {
-            const int2* p = tile + (r - 4 + R) * TW + R - 4;
-            const unsigned lo = __ballot_sync(0xffffffffu, p[lane].x > 0);
-            const unsigned hi = __ballot_sync(0xffffffffu, lane <= 8 && p[32 + lane].x > 0);
-            const unsigned long long M = (unsigned long long)lo | ((unsigned long long)hi << 32);
-            unsigned long long a = M;
-#pragma unroll
-            for (int k = 1; k <= 8; k++) a &= M >> k;
-            if (lane == 0) m9[r] = (unsigned)a;
         }
         if (tid == 0) *cnt = 0;
         __syncthreads();
@@ -566,7 +571,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
         }
         __syncthreads();
-        // gate: min of q over the 5x5 neighbourhood >= tau and the 9x9 window all valid
+        // gate: min of q over the 5x5 neighbourhood >= tau
         bool gated = false;
         if (inside && Dc > 0) {
             float qmin = qs[row * kQW + lane];
@@ -574,45 +579,83 @@ __global__ void __launch_bounds__(kThreads, 2)
             for (int oy = 0; oy < 5; oy++)
 #pragma unroll
                 for (int ox = 0; ox < 5; ox++) qmin = fminf(qmin, qs[(row + oy) * kQW + lane + ox]);
-            unsigned allv = 0xffffffffu;
-#pragma unroll
-            for (int j = 0; j < 9; j++) allv &= m9[row + j];
-            gated = qmin >= gv.tau && ((allv >> lane) & 1u);
+            gated = qmin >= gv.tau;
         }
         const bool any = __syncthreads_or(gated);
-        int* rs = reinterpret_cast<int*>(smem + L.feat);  // features are dead: row sums
-        int* list = reinterpret_cast<int*>(smem + L.h1);   // layer 1 is dead: work list
+        int* rs = reinterpret_cast<int*>(smem + L.feat);  // features and layer 1 are dead: row sums
+        int* list = reinterpret_cast<int*>(smem + L.q);    // q is dead once the gates are known: work list
+        constexpr int kRS = 24 * kTW;                      // row-sum entries (tile rows -4..19)
         if (any) {
-            // row sums over the tile +- 4 rows: R0 = sum D, R1 = sum u D (|u| <= 4), R5 = sum D (|u| <= 2)
-            for (int e = tid; e < 24 * kTW; e += kThreads) {
+            // per row entry, over the valid samples of |u| <= 4 and |u| <= 2:
+            // count, sum u, sum u^2, sum D, sum u D
+            for (int e = tid; e < kRS; e += kThreads) {
                 const int rr = e / kTW, cx = e % kTW;
                 const int2* p = tile + (rr - 4 + R) * TW + cx + R;
-                int s0 = 0, s1 = 0, s5 = 0;
+                int a0 = 0, a1 = 0, a2 = 0, d0 = 0, d1 = 0, e0 = 0, e1 = 0, e2 = 0, f0 = 0, f1 = 0;
 #pragma unroll
                 for (int u = -4; u <= 4; u++) {
                     const int D = p[u].x;
-                    s0 += D;
-                    s1 += u * D;
-                    if (u >= -2 && u <= 2) s5 += D;
+                    const int v = D > 0 ? 1 : 0;
+                    a0 += v;
+                    a1 += u * v;
+                    a2 += u * u * v;
+                    d0 += D;
+                    d1 += u * D;
+                    if (u >= -2 && u <= 2) {
+                        e0 += v;
+                        e1 += u * v;
+                        e2 += u * u * v;
+                        f0 += D;
+                        f1 += u * D;
+                    }
                 }
-                rs[e] = s0;
-                rs[24 * kTW + e] = s1;
-                rs[48 * kTW + e] = s5;
+                rs[0 * kRS + e] = a0;
+                rs[1 * kRS + e] = a1;
+                rs[2 * kRS + e] = a2;
+                rs[3 * kRS + e] = d0;
+                rs[4 * kRS + e] = d1;
+                rs[5 * kRS + e] = e0;
+                rs[6 * kRS + e] = e1;
+                rs[7 * kRS + e] = e2;
+                rs[8 * kRS + e] = f0;
+                rs[9 * kRS + e] = f1;
             }
         }
         __syncthreads();
         if (inside) {
             if (gated) {
-                int Bu = 0, Bv = 0, S5 = 0;
+                WinSums w2{}, w4{};
 #pragma unroll
                 for (int j = 0; j < 9; j++) {
+                    const int v = j - 4;
                     const int e = (row + j) * kTW + lane;
-                    Bu += rs[24 * kTW + e];
-                    Bv += (j - 4) * rs[e];
-                    if (j >= 2 && j <= 6) S5 += rs[48 * kTW + e];
+                    const int a0 = rs[e], a1 = rs[kRS + e], a2 = rs[2 * kRS + e], d0 = rs[3 * kRS + e],
+                              d1 = rs[4 * kRS + e];
+                    w4.n += a0;
+                    w4.Su += a1;
+                    w4.Sv += v * a0;
+                    w4.Suu += a2;
+                    w4.Suv += v * a1;
+                    w4.Svv += v * v * a0;
+                    w4.SD += d0;
+                    w4.SuD += d1;
+                    w4.SvD += v * d0;
+                    if (v >= -2 && v <= 2) {
+                        const int e0 = rs[5 * kRS + e], e1 = rs[6 * kRS + e], e2 = rs[7 * kRS + e],
+                                  f0 = rs[8 * kRS + e], f1 = rs[9 * kRS + e];
+                        w2.n += e0;
+                        w2.Su += e1;
+                        w2.Sv += v * e0;
+                        w2.Suu += e2;
+                        w2.Suv += v * e1;
+                        w2.Svv += v * v * e0;
+                        w2.SD += f0;
+                        w2.SuD += f1;
+                        w2.SvD += v * f0;
+                    }
                 }
                 PixOut r;
-                fast_pixel(g, Dc, Bu, Bv, S5, x, y, r);
+                fast_pixel(g, Dc, w2, w4, x, y, r);
                 emit(g, o, x, y, r);
             } else if (Dc > 0) {
                 list[atomicAdd(cnt, 1)] = tid;

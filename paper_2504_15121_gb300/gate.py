@@ -165,18 +165,24 @@ def codes(disp: np.ndarray) -> np.ndarray:
 
 
 def one_surface_labels(prim: np.ndarray, D: np.ndarray) -> np.ndarray:
-    """True where the 5x5 patch centred at a pixel lies in the image, is all
-    valid and shows a single primitive of the generator."""
+    """True where the 5x5 patch centred at a pixel has at least 13 valid
+    pixels (outside the image: invalid) and all of them show a single
+    primitive of the generator."""
     H, W = D.shape
-    ok = np.zeros((H, W), bool)
-    v = D > 0
-    core = np.ones((H - 4, W - 4), bool)
-    c = prim[2:H - 2, 2:W - 2]
+    v = np.pad(D > 0, 2)
+    p = np.pad(prim.astype(np.int64), 2)
+    cnt = np.zeros((H, W), np.int64)
+    first = np.full((H, W), -10 ** 9, np.int64)
+    same = np.ones((H, W), bool)
     for dy in range(5):
         for dx in range(5):
-            core &= v[dy:dy + H - 4, dx:dx + W - 4] & (prim[dy:dy + H - 4, dx:dx + W - 4] == c)
-    ok[2:H - 2, 2:W - 2] = core
-    return ok
+            vv = v[dy:dy + H, dx:dx + W]
+            pv = p[dy:dy + H, dx:dx + W]
+            cnt += vv
+            unset = vv & (first == -10 ** 9)
+            first = np.where(unset, pv, first)
+            same &= ~vv | (pv == first)
+    return (cnt >= 13) & same
 
 
 def _scene_samples(args):
@@ -189,7 +195,7 @@ def _scene_samples(args):
     H, W = D.shape
     Dp = np.pad(D, 3)
     pos = np.flatnonzero(lab.ravel())
-    neg = np.flatnonzero((~lab & (D > 0)).ravel())
+    neg = np.flatnonzero((~lab).ravel())
     take = []
     for idx, n in ((pos, per_class), (neg, per_class)):
         if idx.size:

@@ -85,15 +85,20 @@ def test_features_by_hand():
 
 
 def test_patch_labels_by_hand():
-    prim = np.zeros((7, 7), int)
+    prim = np.zeros((8, 8), int)
     prim[:, 5:] = 1
-    valid = np.ones((7, 7), bool)
-    valid[0, 0] = False
+    valid = np.ones((8, 8), bool)
+    valid[:, 4] = False             # an invalid column just left of the boundary
+    valid[7, :] = False
     lab = gate.patch_labels(prim, valid)
-    # a 5x5 patch is positive only when it lies inside the image, avoids the
-    # invalid corner and the primitive boundary at column 5
-    want = np.zeros((7, 7), bool)
-    want[2:5, 2] = True
-    want[3:5, 2] = True
-    want[2, 2] = False          # its patch contains (0, 0)
+    want = np.zeros((8, 8), bool)
+    # one primitive and >= 13 valid pixels: centres in columns 0..2 need rows
+    # covering enough valid pixels; column 2 sees columns 0..4 (4 valid)
+    for v in range(8):
+        for u in range(8):
+            rows = [r for r in range(v - 2, v + 3) if 0 <= r < 8]
+            cols = [c for c in range(u - 2, u + 3) if 0 <= c < 8]
+            vals = [prim[r, c] for r in rows for c in cols if valid[r, c]]
+            want[v, u] = len(vals) >= 13 and len(set(vals)) == 1
     assert np.array_equal(lab, want)
+    assert lab[2, 1] and lab[3, 2] and not lab[3, 3] and not lab[3, 5]

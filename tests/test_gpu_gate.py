@@ -68,8 +68,10 @@ def test_training_reduces_loss_and_checkpoint_resumes(G, tmp_path):
     b.resume(ck["theta"], ck["m"], ck["v"], int(ck["step"]))
     la = float(a.step(Xd, yd, 1e-3))
     lb = float(b.step(Xd, yd, 1e-3))
-    assert la == lb
-    assert np.array_equal(a.state()[0], b.state()[0])
+    # the loss and gradients are summed with atomics (order varies): equal
+    # to FP32 rounding
+    assert abs(la - lb) <= 1e-5 * abs(la)
+    assert np.allclose(a.state()[0], b.state()[0], rtol=0, atol=1e-6)
     a.close()
     b.close()
     path = tmp_path / "w.bin"
