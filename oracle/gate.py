@@ -195,21 +195,24 @@ def loss_and_grad(Dp, y, theta):
     return bce(q, y), flatten(g)
 
 
-def patch_labels(prim, valid):
-    """1 where the 5x5 patch centred at a pixel has at least 13 valid pixels
-    (outside the image: invalid) and all of them show one primitive
-    (generator ground truth), else 0; [H, W] -> [H, W]."""
-    H, W = prim.shape
-    pp = np.pad(prim, 2, constant_values=-2)
-    vp = np.pad(valid, 2, constant_values=False)
-    cnt = np.zeros((H, W), int)
-    lo = np.full((H, W), np.iinfo(np.int64).max)
-    hi = np.full((H, W), np.iinfo(np.int64).min)
-    for oy in range(5):
-        for ox in range(5):
-            v = vp[oy:oy + H, ox:ox + W]
-            p = pp[oy:oy + H, ox:ox + W].astype(np.int64)
-            cnt += v
-            lo = np.where(v, np.minimum(lo, p), lo)
-            hi = np.where(v, np.maximum(hi, p), hi)
-    return (cnt >= 13) & (lo == hi)
+def patch_labels(d_true, valid):
+    """Training label of every pixel: 1 where the 5x5 patch centred at it has
+    at least 13 valid pixels (outside the image: invalid) and no depth
+    discontinuity -- every two 4-adjacent valid pixels of the patch differ in
+    noise-free disparity d_true by at most max(0.03 min(d1, d2), 0.25 px)."""
+    H, W = d_true.shape
+    lab = np.zeros((H, W), bool)
+
+    def ok(a, b):
+        return abs(a - b) <= max(0.03 * min(a, b), 0.25)
+    for v in range(H):
+        for u in range(W):
+            cells = [(r, c) for r in range(v - 2, v + 3) for c in range(u - 2, u + 3)
+                     if 0 <= r < H and 0 <= c < W and valid[r, c]]
+            if len(cells) < 13:
+                continue
+            s = set(cells)
+            lab[v, u] = all(ok(d_true[r, c], d_true[r2, c2])
+                            for (r, c) in cells for (r2, c2) in ((r, c + 1), (r + 1, c))
+                            if (r2, c2) in s)
+    return lab

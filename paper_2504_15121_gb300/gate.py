@@ -164,25 +164,33 @@ def codes(disp: np.ndarray) -> np.ndarray:
     return np.where((disp > 0) & (r >= 1) & (r <= 131071), r, 0).astype(np.int32)
 
 
-def one_surface_labels(prim: np.ndarray, D: np.ndarray) -> np.ndarray:
+def one_surface_labels(d_true: np.ndarray, D: np.ndarray) -> np.ndarray:
     """True where the 5x5 patch centred at a pixel has at least 13 valid
-    pixels (outside the image: invalid) and all of them show a single
-    primitive of the generator."""
+    pixels (outside the image: invalid) and no depth discontinuity: every two
+    4-adjacent valid pixels of the patch differ in noise-free disparity by at
+    most max(0.03 min(d1, d2), 0.25 px)."""
     H, W = D.shape
-    v = np.pad(D > 0, 2)
-    p = np.pad(prim.astype(np.int64), 2)
+    v = np.pad(D > 0, 3)
+    t = np.pad(d_true.astype(np.float64), 3)
+    # smooth[i] of a pair of neighbours: both valid and within the bound, or not both valid
+    okr = np.ones_like(v)
+    a, b = t[:, :-1], t[:, 1:]
+    both = v[:, :-1] & v[:, 1:]
+    okr[:, :-1] = ~both | (np.abs(a - b) <= np.maximum(0.03 * np.minimum(a, b), 0.25))
+    okd = np.ones_like(v)
+    a, b = t[:-1, :], t[1:, :]
+    both = v[:-1, :] & v[1:, :]
+    okd[:-1, :] = ~both | (np.abs(a - b) <= np.maximum(0.03 * np.minimum(a, b), 0.25))
     cnt = np.zeros((H, W), np.int64)
-    first = np.full((H, W), -10 ** 9, np.int64)
-    same = np.ones((H, W), bool)
+    smooth = np.ones((H, W), bool)
     for dy in range(5):
         for dx in range(5):
-            vv = v[dy:dy + H, dx:dx + W]
-            pv = p[dy:dy + H, dx:dx + W]
-            cnt += vv
-            unset = vv & (first == -10 ** 9)
-            first = np.where(unset, pv, first)
-            same &= ~vv | (pv == first)
-    return (cnt >= 13) & same
+            cnt += v[1 + dy:1 + dy + H, 1 + dx:1 + dx + W]
+            if dx < 4:
+                smooth &= okr[1 + dy:1 + dy + H, 1 + dx:1 + dx + W]
+            if dy < 4:
+                smooth &= okd[1 + dy:1 + dy + H, 1 + dx:1 + dx + W]
+    return (cnt >= 13) & smooth
 
 
 def _scene_samples(args):
@@ -190,7 +198,7 @@ def _scene_samples(args):
     from scenes import make_scene
     s = make_scene(name, frame=frame, scale=scale, seed=seed)
     D = codes(s.disp)
-    lab = one_surface_labels(s.prim, D)
+    lab = one_surface_labels(s.disp_true, D)
     rng = np.random.default_rng([seed, frame, 7])
     H, W = D.shape
     Dp = np.pad(D, 3)

@@ -44,6 +44,7 @@ class Scene:
     background: np.ndarray      # bool [H, W]; no primitive hit
     disp_u16: np.ndarray | None = None   # uint16 rint(d * 256), 0 = invalid
     disp_f16: np.ndarray | None = None   # float16 d, 0 = invalid
+    disp_true: np.ndarray | None = None  # float32 noise-free disparity, 0 on background
     meta: dict = field(default_factory=dict)
 
     @property
@@ -328,7 +329,7 @@ def _finish(name, cam, zb, rng, sigma, quant, invalid_mode, target, encode16):
     gt = np.where(hit[..., None], zb.n, 0.0).astype(np.float32)
     return Scene(name=name, camera=cam, disp=d, gt_normal=gt,
                  prim=zb.prim.astype(np.int32), background=~hit,
-                 disp_u16=u16, disp_f16=f16,
+                 disp_u16=u16, disp_f16=f16, disp_true=d_true.astype(np.float32),
                  meta=dict(invalid_fraction=float((inv & hit).sum()) / max(int(hit.sum()), 1),
                            n_primitives=zb.count))
 

@@ -85,20 +85,18 @@ def test_features_by_hand():
 
 
 def test_patch_labels_by_hand():
-    prim = np.zeros((8, 8), int)
-    prim[:, 5:] = 1
-    valid = np.ones((8, 8), bool)
-    valid[:, 4] = False             # an invalid column just left of the boundary
-    valid[7, :] = False
-    lab = gate.patch_labels(prim, valid)
-    want = np.zeros((8, 8), bool)
-    # one primitive and >= 13 valid pixels: centres in columns 0..2 need rows
-    # covering enough valid pixels; column 2 sees columns 0..4 (4 valid)
-    for v in range(8):
-        for u in range(8):
-            rows = [r for r in range(v - 2, v + 3) if 0 <= r < 8]
-            cols = [c for c in range(u - 2, u + 3) if 0 <= c < 8]
-            vals = [prim[r, c] for r in rows for c in cols if valid[r, c]]
-            want[v, u] = len(vals) >= 13 and len(set(vals)) == 1
-    assert np.array_equal(lab, want)
-    assert lab[2, 1] and lab[3, 2] and not lab[3, 3] and not lab[3, 5]
+    # a ramp (smooth) with a depth jump between columns 5 and 6, a hole
+    d = np.tile(10.0 + 0.2 * np.arange(10), (9, 1))
+    d[:, 6:] += 5.0                         # jump of 5 px >> max(3 %, 0.25)
+    valid = np.ones((9, 10), bool)
+    valid[4, 1:4] = False
+    lab = gate.patch_labels(d, valid)
+    assert lab[4, 3] and lab[2, 2]          # smooth, enough valid pixels
+    assert not lab[4, 4] and not lab[4, 7]  # the patch straddles the jump
+    assert lab[4, 8] and not lab[0, 0]      # right of the jump; corner patch has 9 pixels
+    # only 4-adjacent valid pairs count: with column 6 invalid the jump
+    # between columns 5 and 7 is not a pair of neighbours
+    valid2 = valid.copy()
+    valid2[:, 6] = False
+    lab2 = gate.patch_labels(d, valid2)
+    assert lab2[4, 4] and lab2[4, 5]

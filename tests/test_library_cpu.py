@@ -106,9 +106,11 @@ def test_training_labels_and_codes(sn):
     from oracle import gate as ogate
     import oracle as orc
     rng = np.random.default_rng(4)
-    prim = np.repeat(rng.integers(0, 3, (6, 8)), 4, 0).repeat(4, 1)
-    disp = rng.uniform(0.5, 300, prim.shape).astype(np.float32)
-    disp[rng.random(prim.shape) < 0.1] = 0
+    d_true = np.repeat(rng.uniform(20, 40, (3, 4)), 8, 0).repeat(8, 1) + 0.05 * rng.normal(size=(24, 32))
+    disp = (d_true + rng.normal(0, 0.3, d_true.shape)).astype(np.float32)
+    disp[rng.random(d_true.shape) < 0.1] = 0
     D = gate.codes(disp)
     assert np.array_equal(D, orc.ingest(disp))
-    assert np.array_equal(gate.one_surface_labels(prim, D), ogate.patch_labels(prim, D > 0))
+    lab = gate.one_surface_labels(d_true, D)
+    assert np.array_equal(lab, ogate.patch_labels(d_true, D > 0))
+    assert 0.05 < lab.mean() < 0.95
