@@ -103,8 +103,9 @@ def _conv3x3(x, W, b):
     return out + b
 
 
-def forward_image(D, theta, round_bf16=True):
-    """q for every pixel of an image (outside the image: invalid pixels)."""
+def forward_image(D, theta, round_bf16=True, margin=0):
+    """q for every pixel of an image and `margin` (<= 2) pixels around it
+    (outside the image: invalid pixels)."""
     w = unflatten(theta)
     if round_bf16:
         w = {k: (bf16(v) if k.startswith("W") else v) for k, v in w.items()}
@@ -121,20 +122,20 @@ def forward_image(D, theta, round_bf16=True):
     z = np.maximum(_conv3x3(h1, w["W2"], w["b2"]), 0.0)   # margin P - 2
     logit = z @ w["W3"] + w["b3"][0]
     q = 1.0 / (1.0 + np.exp(-logit))
-    m = P - 2
-    return q[m:m + H, m:m + W] if m > 0 else q
+    m = P - 2 - margin                 # q covers the image + (P - 2) on each side
+    return q[m:m + H + 2 * margin, m:m + W + 2 * margin] if m > 0 else q
 
 
 def gate_image(D, theta, tau, round_bf16=True):
-    """(gate bits, q, min q over 5x5) of an image."""
-    q = forward_image(D, theta, round_bf16)
+    """(gate bits, q, min q over 5x5) of an image; the minimum includes the q
+    of pixels outside the image (which are invalid pixels)."""
     H, W = D.shape
-    qp = np.pad(q, 2, constant_values=np.inf)
+    qe = forward_image(D, theta, round_bf16, margin=2)
     qmin = np.full((H, W), np.inf)
     for oy in range(5):
         for ox in range(5):
-            qmin = np.minimum(qmin, qp[oy:oy + H, ox:ox + W])
-    return (qmin >= tau) & (D > 0), q, qmin
+            qmin = np.minimum(qmin, qe[oy:oy + H, ox:ox + W])
+    return (qmin >= tau) & (D > 0), qe[2:2 + H, 2:2 + W], qmin
 
 
 # ---------------------------------------------------------------- patches (training)
