@@ -22,13 +22,15 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "driving_2048x1024"
 METRIC = "MPix/s (2048x1024 stereo normals chain)"
 # algorithmic bytes per pixel of each launch of sn_run_frame (compulsory
-# reads and writes of that kernel; see DESIGN.md)
+# reads and writes of that kernel)
 ALGO_BYTES = {
     "frame": 4 + 12 + 12 + 1 + 4,         # disp in; normals, points, mask, tile-local labels out
     "ccl_merge": 0,                       # tile borders only
@@ -273,10 +275,20 @@ def run_ours(args):
     peak = float(peaks["hbm_gbs"])
     traffic = load_traffic(dom)
 
-    # ---- the precision form on the same scenes: uint16 (256 d) in, snorm16 normals out
-    forms = {"precision_u16_snorm16": time_form(
-        scenes, args, dict(in_dtype=sn.SN_IN_U16X256, normal_fmt=sn.SN_NORMALS_SNORM16X4),
-        lambda s: s.disp_u16, 27, dist, world)}
+    gt_plain = gt_error_deg(outs, scenes)
+
+    # ---- other forms on the same scenes: uint16 (256 d) in and snorm16
+    # normals out (precision form); the learned gate with FP32 and with the
+    # precision form's I/O
+    u16 = dict(in_dtype=sn.SN_IN_U16X256, normal_fmt=sn.SN_NORMALS_SNORM16X4)
+    forms = {
+        "precision_u16_snorm16": time_form(scenes, args, u16, lambda s: s.disp_u16, 27, dist, world),
+        "learned_f32": time_form(scenes, args, dict(learned=1), lambda s: s.disp, FRAME_ALGO_BYTES, dist, world),
+        "learned_u16_snorm16": time_form(scenes, args, dict(u16, learned=1), lambda s: s.disp_u16, 27, dist,
+                                         world),
+    }
+    for f in forms.values():
+        f["vs_plain"] = f["value"] / value
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
@@ -311,6 +323,7 @@ def run_ours(args):
             "frame_ms": {"p50": pct(0.5), "p99": pct(0.99), "max": fm[-1] if fm else None,
                          "source": "CUDA events around each sn_run_frame in the timed region"},
             "stage_ms_per_frame": {k: round(v, 5) for k, v in avg.items()},
+            "gt_error_deg": gt_plain,
             "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
@@ -361,6 +374,7 @@ def time_form(scenes, args, params, pick, bytes_per_px, dist, world):
     _, nf, fm = sn.sn_stage_times(pipe.ctx, cap=args.steps * F)
     sn.sn_set_profiling(pipe.ctx, False)
     sn.sn_check_device(pipe.ctx)
+    gt = gt_error_deg(outs, scenes)
     pipe.close()
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
@@ -372,7 +386,31 @@ def time_form(scenes, args, params, pick, bytes_per_px, dist, world):
             "frame_ms_p50": fm[len(fm) // 2] if fm else None,
             "frame_ms_p99": fm[min(len(fm) - 1, int(0.99 * (len(fm) - 1) + 0.5))] if fm else None,
             "algo_bytes_per_px": bytes_per_px,
+            "gt_error_deg": gt,
             "params": {k: int(v) for k, v in params.items()}}
+
+
+def gt_error_deg(outs, scenes):
+    """Mean angular error (degrees) of the normals against the generator's
+    ground truth, over the foreground pixels with a valid normal of the first
+    frame of each distinct scene (read back after the timed region), and the
+    fraction of valid pixels the learned gate certified."""
+    import torch
+    errs, cert = [], []
+    for s, out in zip(scenes, outs):
+        m = out.mask.cpu().numpy()
+        if out.normals.dtype == torch.int16:
+            n = out.normals.cpu().numpy()[..., :3].astype(np.float64) / 32767.0
+        else:
+            n = np.moveaxis(out.normals.cpu().numpy().astype(np.float64), 0, -1)
+        ok = ((m & 2) > 0) & ~s.background
+        a, b = n[ok], s.gt_normal[ok].astype(np.float64)
+        ang = np.degrees(np.arctan2(np.linalg.norm(np.cross(a, b), axis=-1), (a * b).sum(-1)))
+        errs.append(ang)
+        cert.append(((m & 8) > 0).sum() / max(((m & 1) > 0).sum(), 1))
+    e = np.concatenate(errs)
+    return {"mean": float(e.mean()), "median": float(np.median(e)), "pixels": int(e.size),
+            "certified": float(np.mean(cert)), "scenes": len(errs)}
 
 
 SERVING_CAMERAS = [("planes_640x480", 120.0)] * 2 + [("mixed_1482x994", 30.0)] * 4 + \

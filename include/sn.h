@@ -91,9 +91,20 @@ enum {
  *             rint(256 d), 0 = invalid)
  *  normal_fmt SN_NORMALS_F32X3 (3 float planes) or SN_NORMALS_SNORM16X4
  *             (int16 x4 per pixel: rint(32767 n), 4th lane 0)
- *  learned    1 = use the learned gate (weights via sn_load_gate_weights)
+ *  learned    1 = use the learned gate (weights via sn_load_gate_weights);
+ *             needs the default star (support, dirs 8, steps 10, r_denoise 2,
+ *             r_affine 4), else SN_ENOTSUP.  A small network gives each pixel
+ *             the probability q that the 5x5 patch centred there shows one
+ *             surface; a valid pixel whose q values over the
+ *             (2 SN_LEARNED_RADIUS - 3)^2 neighbourhood (pixels outside the
+ *             image included) are all >= tau is certified (SN_MASK_LEARNED):
+ *             its denoise fit takes every valid sample of the 5x5 window (no
+ *             range gate) and its affine fit every valid sample of the
+ *             (2 SN_LEARNED_RADIUS + 1)^2 window but the centre (no
+ *             star-fill).  Other pixels take the plain chain.
  * Every k is used as the integer K = rint(65536 k).
  */
+#define SN_LEARNED_RADIUS 6
 typedef struct {
     int r_denoise;
     int r_affine;

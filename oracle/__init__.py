@@ -78,6 +78,8 @@ def lib():
         p = C.c_void_p
         L.orc_ingest.argtypes = [p, C.c_int, C.c_size_t, C.c_int, C.c_int, p]
         L.orc_ingest.restype = C.c_int
+        L.orc_learned_radius.argtypes = []
+        L.orc_learned_radius.restype = C.c_int
         L.orc_denoise.argtypes = [p, C.c_int, C.c_int, C.POINTER(_Params), p, p]
         L.orc_star_offsets.argtypes = [C.c_int, C.c_int, p, p]
         L.orc_star_offsets.restype = C.c_int
@@ -199,10 +201,16 @@ class Frame:
     n_components: int
 
 
+def learned_radius() -> int:
+    """Radius of the full window fitted at pixels the learned gate certifies."""
+    return int(lib().orc_learned_radius())
+
+
 def run_frame(disp: np.ndarray, cam, params: Params | None = None, gate=None) -> Frame:
     """The whole chain on one disparity map (float32, float16 or uint16 d*256).
     gate (bool [H, W], optional): the learned gate's decisions; certified
-    pixels take the un-gated 5x5 denoise and the full 9x9 affine window."""
+    pixels take the un-gated 5x5 denoise and the full (2 learned_radius() + 1)^2
+    affine window."""
     params = params or Params()
     disp = np.ascontiguousarray(disp)
     H, W = disp.shape

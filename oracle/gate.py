@@ -17,7 +17,9 @@ the method is differentiable apart from the adaptive support, Sec. I-C):
   z  = relu(conv3x3(h1) W2 + b2)         16 channels
   q  = sigmoid(z . W3 + b3)              P(the 5x5 patch at p is one valid surface)
   conv3x3: out(p) = sum over o in {-1,0,1}^2 of W[(o_v+1)*3 + (o_u+1)] in(p + o).
-  gate(p) = (min over |o|_inf <= 2 of q(p + o) >= tau) and p is valid.
+  gate(p) = (min over |o|_inf <= r - 2 of q(p + o) >= tau) and p is valid,
+  r the radius of the full window a certified pixel fits (the union of the
+  5x5 patches centred within r - 2 of p is that window).
   Label of a patch: at least 13 of its 25 pixels are valid (pixels outside
   the image are invalid) and all its valid pixels show one primitive.
 
@@ -104,13 +106,13 @@ def _conv3x3(x, W, b):
 
 
 def forward_image(D, theta, round_bf16=True, margin=0):
-    """q for every pixel of an image and `margin` (<= 2) pixels around it
-    (outside the image: invalid pixels)."""
+    """q for every pixel of an image and `margin` pixels around it (outside
+    the image: invalid pixels)."""
     w = unflatten(theta)
     if round_bf16:
         w = {k: (bf16(v) if k.startswith("W") else v) for k, v in w.items()}
     H, W = D.shape
-    P = 4
+    P = max(4, margin + 2)
     Dp = np.zeros((H + 2 * P + 1, W + 2 * P + 1), D.dtype)
     Dp[P:P + H, P:P + W] = D
     f = features(Dp)[:-1, :-1]                  # (H + 2P) x (W + 2P)
@@ -126,16 +128,18 @@ def forward_image(D, theta, round_bf16=True, margin=0):
     return q[m:m + H + 2 * margin, m:m + W + 2 * margin] if m > 0 else q
 
 
-def gate_image(D, theta, tau, round_bf16=True):
-    """(gate bits, q, min q over 5x5) of an image; the minimum includes the q
+def gate_image(D, theta, tau, radius, round_bf16=True):
+    """(gate bits, q, min q over the (2 radius - 3)^2 neighbourhood) of an
+    image for a full window of the given radius; the minimum includes the q
     of pixels outside the image (which are invalid pixels)."""
     H, W = D.shape
-    qe = forward_image(D, theta, round_bf16, margin=2)
+    m = radius - 2
+    qe = forward_image(D, theta, round_bf16, margin=m)
     qmin = np.full((H, W), np.inf)
-    for oy in range(5):
-        for ox in range(5):
+    for oy in range(2 * m + 1):
+        for ox in range(2 * m + 1):
             qmin = np.minimum(qmin, qe[oy:oy + H, ox:ox + W])
-    return (qmin >= tau) & (D > 0), qe[2:2 + H, 2:2 + W], qmin
+    return (qmin >= tau) & (D > 0), qe[m:m + H, m:m + W], qmin
 
 
 # ---------------------------------------------------------------- patches (training)

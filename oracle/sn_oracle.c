@@ -55,6 +55,12 @@ enum {
     ORC_M_DENOISED = 16  /* 3-parameter denoise fit was determined */
 };
 
+/* Radius of the full window that a pixel certified by the learned gate fits
+ * (the gate certifies the union of 5x5 patches centred within radius - 2). */
+#define ORC_LEARNED_RADIUS 6
+
+int orc_learned_radius(void) { return ORC_LEARNED_RADIUS; }
+
 typedef struct {
     double fx, fy, cx, cy, baseline;
 } orc_camera;
@@ -318,17 +324,18 @@ void orc_affine_normals(const int32_t *D, const double *den, int W, int H, const
 }
 
 /* gate (may be NULL): pixels certified by the learned gate take the fixed
- * 9x9 window (radius 4) as their support and get ORC_M_LEARNED. */
+ * (2 ORC_LEARNED_RADIUS + 1)^2 window as their support and get
+ * ORC_M_LEARNED. */
 static void affine_impl(const int32_t *D, const double *den, int W, int H, const orc_camera *cam,
                         const orc_params *P, const uint8_t *gate, double *nrm, uint8_t *mask, double *diag)
 {
     int R = support_radius(P);
-    if (gate && R < 4)
-        R = 4;
+    if (gate && R < ORC_LEARNED_RADIUS)
+        R = ORC_LEARNED_RADIUS;
     const int side = 2 * R + 1;
     orc_params Pg = *P;
     Pg.support = ORC_FIXED;
-    Pg.r_affine = 4;
+    Pg.r_affine = ORC_LEARNED_RADIUS;
     int *tou = malloc(sizeof(int) * (P->dirs * P->steps + 1));
     int *tov = malloc(sizeof(int) * (P->dirs * P->steps + 1));
     orc_star_offsets(P->dirs, P->steps, tou, tov);
@@ -516,8 +523,8 @@ int orc_run_frame(const void *disp, int dtype, size_t pitch_bytes, int W, int H,
 }
 
 /* The chain with the learned gate's decisions as input (gate may be NULL):
- * certified pixels take the un-gated 5x5 denoise window and the fixed 9x9
- * affine window. */
+ * certified pixels take the un-gated 5x5 denoise window and the fixed
+ * (2 ORC_LEARNED_RADIUS + 1)^2 affine window. */
 int orc_run_frame_gated(const void *disp, int dtype, size_t pitch_bytes, int W, int H, const orc_camera *cam,
                         const orc_params *P, const uint8_t *gate, double *den, double *nrm, double *pts,
                         int32_t *labels, uint8_t *mask)

@@ -361,11 +361,11 @@ struct WinSums {
     int n, Su, Sv, Suu, Suv, Svv, SD, SuD, SvD;
 };
 
-// The learned fast path of a certified pixel (its 9x9 window shows one
-// surface): the denoise fit takes every valid sample of the 5x5 window (no
-// range gate) and the affine fit every valid sample of the 9x9 window
-// except the centre (no star-fill).
-__device__ __forceinline__ void fast_pixel(const Geo& g, int Dc, const WinSums& w2, const WinSums& w4, int x, int y,
+// The learned fast path of a certified pixel (its (2 kFastR + 1)^2 window
+// shows one surface): the denoise fit takes every valid sample of the 5x5
+// window (no range gate) and the affine fit every valid sample of the full
+// window except the centre (no star-fill).
+__device__ __forceinline__ void fast_pixel(const Geo& g, int Dc, const WinSums& w2, const WinSums& wa, int x, int y,
                                            PixOut& r) {
     pix_zero(r);
     r.m = SN_MASK_VALID | SN_MASK_LEARNED;
@@ -380,14 +380,14 @@ __device__ __forceinline__ void fast_pixel(const Geo& g, int Dc, const WinSums& 
     if (fit) r.m |= SN_MASK_DENOISED;
     r.dtil = ((float)Dc + dcf) * (1.0f / 256.0f);
     AffSums s;
-    s.N = w4.n - 1;
-    s.Su = w4.Su;
-    s.Sv = w4.Sv;
-    s.Suu = w4.Suu;
-    s.Suv = w4.Suv;
-    s.Svv = w4.Svv;
-    s.Bu = w4.SuD - Dc * w4.Su;
-    s.Bv = w4.SvD - Dc * w4.Sv;
+    s.N = wa.n - 1;
+    s.Su = wa.Su;
+    s.Sv = wa.Sv;
+    s.Suu = wa.Suu;
+    s.Suv = wa.Suv;
+    s.Svv = wa.Svv;
+    s.Bu = wa.SuD - Dc * wa.Su;
+    s.Bv = wa.SvD - Dc * wa.Sv;
     bool fp64;
     if (solve_normal_dc(s, Dc, dcf, [=] { return fit ? (double)num / (double)det : 0.0; }, r.dtil, x, y, g, r.n,
                         fp64))
@@ -395,33 +395,46 @@ __device__ __forceinline__ void fast_pixel(const Geo& g, int Dc, const WinSums& 
     pix_points(g, x, y, r);
 }
 
+// The learned fast path fits the full (2 kFastR + 1)^2 window; the gate
+// certifies it when the 5x5 patches centred within kQM of the pixel all show
+// one surface (their union is the window).
+constexpr int kFastR = SN_LEARNED_RADIUS, kQM = kFastR - 2;
+static_assert(kFastR >= 3 && kFastR + 1 <= 10, "the features of the q region must lie inside the halo of 10");
 // Shared-memory layout of the learned variant (after the tile, the
 // union-find parents and the row masks; all offsets 16-byte aligned).
-constexpr int kFeatW = kTW + 8, kFeatH = kTH + 8;   // features: tile + 4
-constexpr int kH1W = kTW + 6, kH1H = kTH + 6;       // layer 1:  tile + 3
-constexpr int kQW = kTW + 4, kQH = kTH + 4;         // q:        tile + 2
-constexpr int kFeatN = kFeatW * kFeatH;             // 960 (+ 1 zero row)
-constexpr int kH1N = kH1W * kH1H;                   // 836
-constexpr int kH1Tiles = (kH1N + 15) / 16;          // 53
-constexpr int kQN = kQW * kQH;                      // 720 = 45 x 16
-constexpr int kW1Ld = 88, kW2Ld = 152;              // padded bf16 rows of the weights
+constexpr int kFeatW = kTW + 2 * (kQM + 2), kFeatH = kTH + 2 * (kQM + 2);  // features: tile + kQM + 2
+constexpr int kH1W = kTW + 2 * (kQM + 1), kH1H = kTH + 2 * (kQM + 1);      // layer 1:  tile + kQM + 1
+constexpr int kQW = kTW + 2 * kQM, kQH = kTH + 2 * kQM;                    // q:        tile + kQM
+constexpr int kFeatN = kFeatW * kFeatH;     // (+ 1 zero row)
+constexpr int kH1N = kH1W * kH1H;
+constexpr int kH1Tiles = (kH1N + 15) / 16;  // m-tiles of 16 pixels
+constexpr int kQN = kQW * kQH;
+constexpr int kQTiles = (kQN + 15) / 16;
+constexpr int kRSRows = kTH + 2 * kFastR;   // row-sum rows: tile rows -kFastR .. kTH - 1 + kFastR
+constexpr int kRS = kRSRows * kTW;          // row-sum entries per quantity
+constexpr int kW1Ld = 88, kW2Ld = 152;      // padded bf16 rows of the weights
 constexpr size_t align16z(size_t b) { return (b + 15) & ~(size_t)15; }
 
 struct LearnedSmem {
-    size_t m9, cnt, w1, w2, feat, h1, q, end;
+    size_t cnt, w1, w2, feat, h1, q, end;
 };
 __host__ __device__ constexpr LearnedSmem learned_layout(size_t base) {
     LearnedSmem L{};
-    L.m9 = align16z(base);
-    L.cnt = L.m9 + 4 * 24;
+    L.cnt = align16z(base);
     L.w1 = align16z(L.cnt + 16);
     L.w2 = align16z(L.w1 + 2 * 16 * kW1Ld);
     L.feat = align16z(L.w2 + 2 * 16 * kW2Ld);
     L.h1 = align16z(L.feat + 16 * (kFeatN + 1));
     L.q = align16z(L.h1 + 32 * 16 * kH1Tiles);
-    L.end = align16z(L.q + 4 * kQN);
+    L.end = align16z(L.q + 4 * 16 * kQTiles);
     return L;
 }
+// The q region later holds the work list (one int per tile pixel); features
+// and layer 1 later hold the row sums (10 ints per entry) and layer 1 the
+// row minima of q.
+static_assert(16 * kQTiles >= kThreads, "work list");
+static_assert(learned_layout(0).q - learned_layout(0).feat >= sizeof(int) * 10 * kRS, "row sums");
+static_assert(32 * 16 * kH1Tiles >= sizeof(float) * kQH * kTW, "row minima of q");
 
 // VAR: 0 fixed window, 1 star table, 2 compile-time M = 8, s = 10 star,
 // 3 = 2 with the learned gate.  R: halo radius at compile time (0 = runtime).
@@ -496,11 +509,11 @@ __global__ void __launch_bounds__(kThreads, 2)
             for (int i = tid; i < 16 * 40; i += kThreads) w1s[(i / 40) * (kW1Ld / 2) + i % 40] = __ldg(w1 + i);
             for (int i = tid; i < 16 * 72; i += kThreads) w2s[(i / 72) * (kW2Ld / 2) + i % 72] = __ldg(w2 + i);
         }
-        // features of the tile + 4 region; feat[kFeatN] is a zero row
+        // features of the tile + (kQM + 2) region; feat[kFeatN] is a zero row
         for (int i = tid; i <= kFeatN; i += kThreads) {
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
             if (i < kFeatN) {
-                const int fx = i % kFeatW - 4, fy = i / kFeatW - 4;
+                const int fx = i % kFeatW - (kQM + 2), fy = i / kFeatW - (kQM + 2);
                 const int2* p = tile + (fy + R) * TW + fx + R;
                 float f[3];
                 gate_feature(p[0].x, p[1].x, p[TW].x, f);
@@ -515,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         __syncthreads();
 
         const int gq = lane >> 2, tq = lane & 3;
-        // layer 1: h1 = relu(conv3x3(feat) W1 + b1) on the tile + 3 region
+        // layer 1: h1 = relu(conv3x3(feat) W1 + b1) on the tile + (kQM + 1) region
         for (int mt = warp; mt < kH1Tiles; mt += kThreads / 32) {
             const int r = mt * 16 + (lane & 15);
             const int hx = r % kH1W, hy = r / kH1W;
@@ -544,9 +557,10 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
         }
         __syncthreads();
-        // layer 2 and head: q = sigmoid(relu(conv3x3(h1) W2 + b2) . W3 + b3) on the tile + 2 region
-        for (int mt = warp; mt < kQN / 16; mt += kThreads / 32) {
-            const int r = mt * 16 + (lane & 15);
+        // layer 2 and head: q = sigmoid(relu(conv3x3(h1) W2 + b2) . W3 + b3) on
+        // the tile + kQM region (rows of the last m-tile past it repeat its last pixel)
+        for (int mt = warp; mt < kQTiles; mt += kThreads / 32) {
+            const int r = min(mt * 16 + (lane & 15), kQN - 1);
             const int qx = r % kQW, qy = r / kQW;
             float acc0[4] = {0, 0, 0, 0}, acc1[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -571,29 +585,37 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
         }
         __syncthreads();
-        // gate: min of q over the 5x5 neighbourhood >= tau
+        // gate: min of q over the (2 kQM + 1)^2 neighbourhood >= tau, as a
+        // row pass (into the dead layer-1 region) and a column pass
+        float* qrow = reinterpret_cast<float*>(smem + L.h1);
+        for (int e = tid; e < kQH * kTW; e += kThreads) {
+            const float* q0 = qs + (e / kTW) * kQW + e % kTW;
+            float m = q0[0];
+#pragma unroll
+            for (int ox = 1; ox <= 2 * kQM; ox++) m = fminf(m, q0[ox]);
+            qrow[e] = m;
+        }
+        __syncthreads();
         bool gated = false;
         if (inside && Dc > 0) {
-            float qmin = qs[row * kQW + lane];
+            float qmin = qrow[row * kTW + lane];
 #pragma unroll
-            for (int oy = 0; oy < 5; oy++)
-#pragma unroll
-                for (int ox = 0; ox < 5; ox++) qmin = fminf(qmin, qs[(row + oy) * kQW + lane + ox]);
+            for (int oy = 1; oy <= 2 * kQM; oy++) qmin = fminf(qmin, qrow[(row + oy) * kTW + lane]);
             gated = qmin >= gv.tau;
         }
         const bool any = __syncthreads_or(gated);
         int* rs = reinterpret_cast<int*>(smem + L.feat);  // features and layer 1 are dead: row sums
         int* list = reinterpret_cast<int*>(smem + L.q);    // q is dead once the gates are known: work list
-        constexpr int kRS = 24 * kTW;                      // row-sum entries (tile rows -4..19)
         if (any) {
-            // per row entry, over the valid samples of |u| <= 4 and |u| <= 2:
-            // count, sum u, sum u^2, sum D, sum u D
+            // per row entry (tile rows -kFastR .. kTH - 1 + kFastR), over the
+            // valid samples of |u| <= kFastR and |u| <= 2: count, sum u,
+            // sum u^2, sum D, sum u D
             for (int e = tid; e < kRS; e += kThreads) {
                 const int rr = e / kTW, cx = e % kTW;
-                const int2* p = tile + (rr - 4 + R) * TW + cx + R;
+                const int2* p = tile + (rr - kFastR + R) * TW + cx + R;
                 int a0 = 0, a1 = 0, a2 = 0, d0 = 0, d1 = 0, e0 = 0, e1 = 0, e2 = 0, f0 = 0, f1 = 0;
 #pragma unroll
-                for (int u = -4; u <= 4; u++) {
+                for (int u = -kFastR; u <= kFastR; u++) {
                     const int D = p[u].x;
                     const int v = D > 0 ? 1 : 0;
                     a0 += v;
@@ -624,22 +646,22 @@ __global__ void __launch_bounds__(kThreads, 2)
         __syncthreads();
         if (inside) {
             if (gated) {
-                WinSums w2{}, w4{};
+                WinSums w2{}, wa{};
 #pragma unroll
-                for (int j = 0; j < 9; j++) {
-                    const int v = j - 4;
+                for (int j = 0; j <= 2 * kFastR; j++) {
+                    const int v = j - kFastR;
                     const int e = (row + j) * kTW + lane;
                     const int a0 = rs[e], a1 = rs[kRS + e], a2 = rs[2 * kRS + e], d0 = rs[3 * kRS + e],
                               d1 = rs[4 * kRS + e];
-                    w4.n += a0;
-                    w4.Su += a1;
-                    w4.Sv += v * a0;
-                    w4.Suu += a2;
-                    w4.Suv += v * a1;
-                    w4.Svv += v * v * a0;
-                    w4.SD += d0;
-                    w4.SuD += d1;
-                    w4.SvD += v * d0;
+                    wa.n += a0;
+                    wa.Su += a1;
+                    wa.Sv += v * a0;
+                    wa.Suu += a2;
+                    wa.Suv += v * a1;
+                    wa.Svv += v * v * a0;
+                    wa.SD += d0;
+                    wa.SuD += d1;
+                    wa.SvD += v * d0;
                     if (v >= -2 && v <= 2) {
                         const int e0 = rs[5 * kRS + e], e1 = rs[6 * kRS + e], e2 = rs[7 * kRS + e],
                                   f0 = rs[8 * kRS + e], f1 = rs[9 * kRS + e];
@@ -655,7 +677,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     }
                 }
                 PixOut r;
-                fast_pixel(g, Dc, w2, w4, x, y, r);
+                fast_pixel(g, Dc, w2, wa, x, y, r);
                 emit(g, o, x, y, r);
             } else if (Dc > 0) {
                 list[atomicAdd(cnt, 1)] = tid;

@@ -100,3 +100,30 @@ def test_patch_labels_by_hand():
     valid2[:, 6] = False
     lab2 = gate.patch_labels(d, valid2)
     assert lab2[4, 4] and lab2[4, 5]
+
+
+@pytest.mark.parametrize("radius", [3, 6])
+def test_gate_image_is_min_of_patch_q(radius):
+    # the image form's gate equals, pixel by pixel, the minimum of the patch
+    # form's q over the (2 radius - 3)^2 neighbourhood of the zero-padded image
+    rng = np.random.default_rng(4)
+    H, W = 11, 13
+    D = rng.integers(4000, 4300, (H, W))
+    D[:, 7:] *= 2
+    D[rng.random((H, W)) < 0.1] = 0
+    theta = gate.init_params(5) + 0.1 * rng.normal(size=gate.N_PARAMS)
+    _, _, qmin0 = gate.gate_image(D, theta, 0.5, radius, round_bf16=False)
+    qs = np.unique(qmin0[D > 0])
+    k = len(qs) // 2
+    tau = float(0.5 * (qs[k - 1] + qs[k]))     # splits the image, far from every qmin
+    g, q, qmin = gate.gate_image(D, theta, tau, radius, round_bf16=False)
+    m, P = radius - 2, radius + 2
+    Dp = np.pad(D, P)
+    for v in range(H):
+        for u in range(W):
+            patches = np.stack([Dp[v + oy + P - 2:v + oy + P + 4, u + ox + P - 2:u + ox + P + 4]
+                                for oy in range(-m, m + 1) for ox in range(-m, m + 1)])
+            qm = gate.forward_patches(patches, theta).min()
+            assert abs(qm - qmin[v, u]) < 1e-12
+            assert g[v, u] == ((qm >= tau) and D[v, u] > 0)
+    assert 0 < g.sum() < (D > 0).sum()

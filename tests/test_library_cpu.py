@@ -43,6 +43,13 @@ def test_every_declared_symbol_is_exported(sn):
     assert "sn_server_simulate" in names and "sn_normals_noalloc" in names
 
 
+def test_learned_radius_matches_oracle():
+    # the header's constant (compiled into the kernel) and the oracle's own
+    text = open(os.path.join(ROOT, "include", "sn.h")).read()
+    r = int(re.search(r"#define SN_LEARNED_RADIUS (\d+)", text).group(1))
+    assert r == oracle.learned_radius()
+
+
 @pytest.mark.parametrize("M,s", [(8, 10), (16, 30), (4, 1), (12, 7), (16, 6)])
 def test_star_table_matches_oracle(sn, M, s):
     ou, ov = sn.star_offsets(M, s)

@@ -542,7 +542,7 @@ def test_run_frame_on_noiseless_plane():
 
 def test_gated_chain_is_box_mean_and_full_window():
     # a certified pixel takes every valid sample of the 5x5 window (the box
-    # mean, no range gate) and the fixed 9x9 window as its support
+    # mean, no range gate) and the fixed (2 r + 1)^2 window as its support
     rng = np.random.default_rng(12)
     H, W = 30, 40
     D = (20000 + 40 * np.arange(W)[None, :] - 25 * np.arange(H)[:, None]
@@ -550,10 +550,12 @@ def test_gated_chain_is_box_mean_and_full_window():
     D[rng.random((H, W)) < 0.03] = 0
     disp = (D / 256.0).astype(np.float32)
     gate = np.zeros((H, W), bool)
-    gate[6:-6, 6:-6] = True
+    r = oracle.learned_radius()
+    assert 3 <= r <= 9
+    gate[r + 2:-r - 2, r + 2:-r - 2] = True
     gate &= D > 0
     fr = oracle.run_frame(disp, CAM, gate=gate)
-    fixed = oracle.run_frame(disp, CAM, Params(support=FIXED, r_affine=4, k_range=1.0))
+    fixed = oracle.run_frame(disp, CAM, Params(support=FIXED, r_affine=r, k_range=1.0))
     from numpy.lib.stride_tricks import sliding_window_view
     vals = sliding_window_view(np.pad(D, 2) / 256.0, (5, 5))
     cnt = sliding_window_view(np.pad(D > 0, 2), (5, 5)).sum((-1, -2))
