@@ -336,10 +336,27 @@ __device__ __forceinline__ int find_g(const int* L, const LabelIndex& li, int x,
     return x;
 }
 
+// Root of x with path halving: every node passed is re-pointed at its
+// grandparent (an ancestor, so concurrent unions stay correct).
+__device__ __forceinline__ int find_halve(int* L, const LabelIndex& li, int x, int* err) {
+    for (int it = 0; it < kFindLimit; it++) {
+        const int p = __ldcg(L + li.addr(x));
+        if (p == x) return x;
+        const int gp = __ldcg(L + li.addr(p));
+        if (gp == p) return p;
+        __stcg(L + li.addr(x), gp);
+        x = gp;
+    }
+    atomicOr(err, kErrFindLimit);
+    return x;
+}
+
+// Lock-free union: the larger root is linked to the smaller by atomicMin;
+// a lost race retries from the value found.
 __device__ __forceinline__ void union_g(int* L, const LabelIndex& li, int a, int b, int* err) {
     for (int it = 0; it < kUnionLimit; it++) {
-        a = find_g(L, li, a, err);
-        b = find_g(L, li, b, err);
+        a = find_halve(L, li, a, err);
+        b = find_halve(L, li, b, err);
         if (a == b) return;
         if (a < b) {
             const int t = a;

@@ -147,66 +147,80 @@ __global__ void __launch_bounds__(kCclTile * 8)
 
 // Pass 2: join components across tile borders (global atomicMin union).
 // Tiles are tw x th pixels; thread t handles one 4-neighbour pair that
-// straddles a vertical (x = k tw) or horizontal (y = k th) tile border.
+// straddles a vertical (x = k tw) or horizontal (y = k th) tile border.  The
+// 32 pairs of a warp lie along one border: of the pairs with an edge that
+// join the same two labels only the first unites them.
 template <int IN>
 __global__ void __launch_bounds__(256)
     k_ccl_merge(const Geo g, const char* __restrict__ disp, size_t dp, int* labels, size_t lpe,
                 int nbx, int nby, int tw, int th) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nV = (long long)(nbx - 1) * g.H;
-    int px, py, qx, qy, sx, sy;  // (sx, sy): step to the previous pair along the border
+    const int lane = threadIdx.x & 31;
+    bool act = false;
+    int px = 0, py = 0, qx = 0, qy = 0;
     if (t < nV) {
         const int k = (int)(t / g.H) + 1;
         py = qy = (int)(t - (long long)(k - 1) * g.H);
         qx = k * tw;
         px = qx - 1;
-        sx = 0;
-        sy = 1;
-    } else {
+        act = true;
+    } else if (t - nV < (long long)(nby - 1) * g.W) {
         const long long t2 = t - nV;
-        if (t2 >= (long long)(nby - 1) * g.W) return;
         const int k = (int)(t2 / g.W) + 1;
         px = qx = (int)(t2 - (long long)(k - 1) * g.W);
         qy = k * th;
         py = qy - 1;
-        sx = 1;
-        sy = 0;
+        act = true;
     }
-    const int Dp = load_code<IN>(disp, dp, px, py, g.W, g.H);
-    const int Dq = load_code<IN>(disp, dp, qx, qy, g.W, g.H);
-    if (!pair_edge(Dp, Dq, g.K_pair)) return;
-    // Skip the union when the previous pair along the border has an edge
-    // and the same labels on both sides: labels are ancestors in the
-    // union-find forest, so that pair (or the first of its run) already
-    // joins the same two sets.
-    if (px - sx >= 0 && py - sy >= 0) {
-        const int Dbp = load_code<IN>(disp, dp, px - sx, py - sy, g.W, g.H);
-        const int Dbq = load_code<IN>(disp, dp, qx - sx, qy - sy, g.W, g.H);
-        if (pair_edge(Dbp, Dbq, g.K_pair)) {
-            const int lp = __ldcg(labels + (size_t)py * lpe + px);
-            const int lq = __ldcg(labels + (size_t)qy * lpe + qx);
-            const int lbp = __ldcg(labels + (size_t)(py - sy) * lpe + (px - sx));
-            const int lbq = __ldcg(labels + (size_t)(qy - sy) * lpe + (qx - sx));
-            if (lp == lbp && lq == lbq) return;
+    int lp = 0, lq = 0;
+    unsigned long long key = ~0ull - (unsigned)lane;  // unique for lanes without an edge
+    if (act) {
+        const int Dp = load_code<IN>(disp, dp, px, py, g.W, g.H);
+        const int Dq = load_code<IN>(disp, dp, qx, qy, g.W, g.H);
+        act = pair_edge(Dp, Dq, g.K_pair);
+        if (act) {
+            lp = __ldcg(labels + (size_t)py * lpe + px);
+            lq = __ldcg(labels + (size_t)qy * lpe + qx);
+            key = ((unsigned long long)(unsigned)lp << 32) | (unsigned)lq;
         }
     }
-    const LabelIndex li{g.W, lpe};
-    union_g(labels, li, py * g.W + px, qy * g.W + qx, g.err);
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (act && lp != lq && (int)(__ffs(peers) - 1) == lane) {
+        const LabelIndex li{g.W, lpe};
+        union_g(labels, li, lp, lq, g.err);
+    }
 }
 
 // Pass 3: every pixel points at its global root, which is the smallest
-// index of its component; roots are counted.
-__global__ void __launch_bounds__(kTW* kTH)
+// index of its component; roots are counted.  A thread takes kFlatPix
+// pixels of one column of a kTW x kTH tile (their label loads overlap, and
+// a label equal to the previous pixel's reuses its root).
+constexpr int kFlatPix = 4;
+__global__ void __launch_bounds__(kTW * kTH / kFlatPix)
     k_ccl_flatten(const Geo g, int* labels, size_t lpe, int* count) {
-    const int x = blockIdx.x * kTW + threadIdx.x, y = blockIdx.y * kTH + threadIdx.y;
-    if (x >= g.W || y >= g.H) return;
-    int* a = labels + (size_t)y * lpe + x;
-    const int l = __ldcg(a);
-    if (l < 0) return;
+    const int x = blockIdx.x * kTW + threadIdx.x;
+    const int y0 = blockIdx.y * kTH + threadIdx.y;
+    constexpr int kStep = kTH / kFlatPix;
+    int l[kFlatPix];
+#pragma unroll
+    for (int i = 0; i < kFlatPix; i++) {
+        const int y = y0 + i * kStep;
+        l[i] = (x < g.W && y < g.H) ? __ldcg(labels + (size_t)y * lpe + x) : -1;
+    }
     const LabelIndex li{g.W, lpe};
-    const int r = find_g(labels, li, l, g.err);
-    if (r != l) __stcg(a, r);
-    if (count && r == y * g.W + x) atomicAdd(count, 1);
+    int roots = 0, prev_l = -1, prev_r = -1;
+#pragma unroll
+    for (int i = 0; i < kFlatPix; i++) {
+        if (l[i] < 0) continue;
+        const int y = y0 + i * kStep;
+        const int r = l[i] == prev_l ? prev_r : find_g(labels, li, l[i], g.err);
+        prev_l = l[i];
+        prev_r = r;
+        if (r != l[i]) __stcg(labels + (size_t)y * lpe + x, r);
+        roots += r == y * g.W + x;
+    }
+    if (count && roots) atomicAdd(count, roots);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -274,7 +288,7 @@ cudaError_t launch_ccl_merge_flatten(const Geo& g, const void* disp, size_t dp, 
         }
     }
     mk.after(s, pairs > 0);
-    k_ccl_flatten<<<grid2(g), dim3(kTW, kTH), 0, s>>>(g, labels, lpe, count);
+    k_ccl_flatten<<<grid2(g), dim3(kTW, kTH / kFlatPix), 0, s>>>(g, labels, lpe, count);
     mk.after(s);
     return cudaGetLastError();
 }
