@@ -399,7 +399,7 @@ __device__ __forceinline__ void fast_pixel(const Geo& g, int Dc, const WinSums& 
 // certifies it when the 5x5 patches centred within kQM of the pixel all show
 // one surface (their union is the window).
 constexpr int kFastR = SN_LEARNED_RADIUS, kQM = kFastR - 2;
-static_assert(kFastR >= 3 && kFastR + 1 <= 10, "the features of the q region must lie inside the halo of 10");
+static_assert(kFastR >= 3 && kFastR + 2 <= 10, "the features of the q region must lie inside the halo of 10");
 // Shared-memory layout of the learned variant (after the tile, the
 // union-find parents and the row masks; all offsets 16-byte aligned).
 constexpr int kFeatW = kTW + 2 * (kQM + 2), kFeatH = kTH + 2 * (kQM + 2);  // features: tile + kQM + 2
@@ -412,7 +412,13 @@ constexpr int kQN = kQW * kQH;
 constexpr int kQTiles = (kQN + 15) / 16;
 constexpr int kRSRows = kTH + 2 * kFastR;   // row-sum rows: tile rows -kFastR .. kTH - 1 + kFastR
 constexpr int kRS = kRSRows * kTW;          // row-sum entries per quantity
-constexpr int kW1Ld = 88, kW2Ld = 152;      // padded bf16 rows of the weights
+// Layer 1 runs with K = 48: k-step s is feature row dy = s, its two 8-wide
+// halves the feature rows of positions dx = 0 and dx = 2, each of which holds
+// its own features and its right neighbour's (so dx = 1 rides along with
+// dx = 0, and the weights of the 4th pixel dx = 3 are zero).
+constexpr int kW1K = 48;
+constexpr int kW1Ld = 56, kW2Ld = 152;      // padded bf16 rows of the weights (conflict-free ldmatrix)
+constexpr int kH1Ld = 12;                   // words per layer-1 row: 16 bf16 + 16 B pad (conflict-free ldmatrix)
 constexpr size_t align16z(size_t b) { return (b + 15) & ~(size_t)15; }
 
 struct LearnedSmem {
@@ -425,7 +431,7 @@ __host__ __device__ constexpr LearnedSmem learned_layout(size_t base) {
     L.w2 = align16z(L.w1 + 2 * 16 * kW1Ld);
     L.feat = align16z(L.w2 + 2 * 16 * kW2Ld);
     L.h1 = align16z(L.feat + 16 * (kFeatN + 1));
-    L.q = align16z(L.h1 + 32 * 16 * kH1Tiles);
+    L.q = align16z(L.h1 + 4 * kH1Ld * 16 * kH1Tiles);
     L.end = align16z(L.q + 4 * 16 * kQTiles);
     return L;
 }
@@ -434,7 +440,7 @@ __host__ __device__ constexpr LearnedSmem learned_layout(size_t base) {
 // row minima of q.
 static_assert(16 * kQTiles >= kThreads, "work list");
 static_assert(learned_layout(0).q - learned_layout(0).feat >= sizeof(int) * 10 * kRS, "row sums");
-static_assert(32 * 16 * kH1Tiles >= sizeof(float) * kQH * kTW, "row minima of q");
+static_assert(4 * kH1Ld * 16 * kH1Tiles >= sizeof(float) * kQH * kTW, "row minima of q");
 
 // VAR: 0 fixed window, 1 star table, 2 compile-time M = 8, s = 10 star,
 // 3 = 2 with the learned gate.  R: halo radius at compile time (0 = runtime).
@@ -497,30 +503,40 @@ __global__ void __launch_bounds__(kThreads, 2)
         __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(smem + L.w1);
         __nv_bfloat16* W2s = reinterpret_cast<__nv_bfloat16*>(smem + L.w2);
         uint4* feat = reinterpret_cast<uint4*>(smem + L.feat);
-        unsigned* h1w = reinterpret_cast<unsigned*>(smem + L.h1);  // 8 words (16 bf16) per pixel
+        unsigned* h1w = reinterpret_cast<unsigned*>(smem + L.h1);  // kH1Ld words (16 bf16 + pad) per pixel
         float* qs = reinterpret_cast<float*>(smem + L.q);
         const int warp = tid >> 5;
         // weights into shared memory (rows padded for conflict-free ldmatrix)
         {
-            const unsigned* w1 = reinterpret_cast<const unsigned*>(gv.W1g);
+            // W1g is [16][80] with k = tap * 8 + channel (tap = 3 dy + dx)
+            for (int i = tid; i < 16 * kW1K; i += kThreads) {
+                const int nn = i / kW1K, k = i % kW1K;
+                const int dy = k / 16, dx = 2 * ((k % 16) / 8) + ((k % 8) >= 4), ch = k % 4;
+                W1s[nn * kW1Ld + k] = (dx <= 2 && ch < 3) ? gv.W1g[nn * 80 + (3 * dy + dx) * 8 + ch]
+                                                           : __float2bfloat16(0.0f);
+            }
             const unsigned* w2 = reinterpret_cast<const unsigned*>(gv.W2g);
-            unsigned* w1s = reinterpret_cast<unsigned*>(W1s);
             unsigned* w2s = reinterpret_cast<unsigned*>(W2s);
-            for (int i = tid; i < 16 * 40; i += kThreads) w1s[(i / 40) * (kW1Ld / 2) + i % 40] = __ldg(w1 + i);
             for (int i = tid; i < 16 * 72; i += kThreads) w2s[(i / 72) * (kW2Ld / 2) + i % 72] = __ldg(w2 + i);
         }
-        // features of the tile + (kQM + 2) region; feat[kFeatN] is a zero row
+        // features of the tile + (kQM + 2) region: position i holds its own
+        // features (channels 0-3) and its right neighbour's (4-7)
         for (int i = tid; i <= kFeatN; i += kThreads) {
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
             if (i < kFeatN) {
                 const int fx = i % kFeatW - (kQM + 2), fy = i / kFeatW - (kQM + 2);
                 const int2* p = tile + (fy + R) * TW + fx + R;
-                float f[3];
+                float f[3], f1[3];
                 gate_feature(p[0].x, p[1].x, p[TW].x, f);
+                gate_feature(p[1].x, p[2].x, p[TW + 1].x, f1);
                 const __nv_bfloat162 a = __floats2bfloat162_rn(f[0], f[1]);
                 const __nv_bfloat162 b = __floats2bfloat162_rn(f[2], 0.0f);
+                const __nv_bfloat162 a1 = __floats2bfloat162_rn(f1[0], f1[1]);
+                const __nv_bfloat162 b1 = __floats2bfloat162_rn(f1[2], 0.0f);
                 v.x = *reinterpret_cast<const unsigned*>(&a);
                 v.y = *reinterpret_cast<const unsigned*>(&b);
+                v.z = *reinterpret_cast<const unsigned*>(&a1);
+                v.w = *reinterpret_cast<const unsigned*>(&b1);
             }
             feat[i] = v;
         }
@@ -528,18 +544,23 @@ __global__ void __launch_bounds__(kThreads, 2)
         __syncthreads();
 
         const int gq = lane >> 2, tq = lane & 3;
-        // layer 1: h1 = relu(conv3x3(feat) W1 + b1) on the tile + (kQM + 1) region
+        // each lane's output channels: 2 tq, 2 tq + 1 (first n-half), 8 + 2 tq, 9 + 2 tq (second)
+        const float b1a = __ldg(gv.b1 + 2 * tq), b1b = __ldg(gv.b1 + 2 * tq + 1);
+        const float b1c = __ldg(gv.b1 + 8 + 2 * tq), b1d = __ldg(gv.b1 + 9 + 2 * tq);
+        const __nv_bfloat16* w1row = W1s + ((lane & 7) + ((lane >> 4) << 3)) * kW1Ld + ((lane >> 3) & 1) * 8;
+        const __nv_bfloat16* w2row = W2s + ((lane & 7) + ((lane >> 4) << 3)) * kW2Ld + ((lane >> 3) & 1) * 8;
+        // layer 1: h1 = relu(conv3x3(feat) W1 + b1) on the tile + (kQM + 1) region; rows of
+        // the last m-tile past the region repeat its last pixel (their results are dropped)
         for (int mt = warp; mt < kH1Tiles; mt += kThreads / 32) {
-            const int r = mt * 16 + (lane & 15);
+            const int r = min(mt * 16 + (lane & 15), kH1N - 1);
             const int hx = r % kH1W, hy = r / kH1W;
-            float acc0[4] = {0, 0, 0, 0}, acc1[4] = {0, 0, 0, 0};
+            const uint4* fa = feat + hy * kFeatW + hx + 2 * (lane >> 4);
+            float acc0[4] = {b1a, b1b, b1a, b1b}, acc1[4] = {b1c, b1d, b1c, b1d};
 #pragma unroll
-            for (int s = 0; s < 5; s++) {
-                const int tap = 2 * s + (lane >> 4);
-                const int fi = (r < kH1N && tap < 9) ? (hy + tap / 3) * kFeatW + hx + tap % 3 : kFeatN;
+            for (int st = 0; st < 3; st++) {
                 unsigned a[4], b[4];
-                ldsm_x4(a, feat + fi);
-                ldsm_x4(b, W1s + ((lane & 7) + ((lane >> 4) << 3)) * kW1Ld + 16 * s + ((lane >> 3) & 1) * 8);
+                ldsm_x4(a, fa + st * kFeatW);
+                ldsm_x4(b, w1row + 16 * st);
                 mma_bf16(acc0, a, b[0], b[1]);
                 mma_bf16(acc1, a, b[2], b[3]);
             }
@@ -547,41 +568,43 @@ __global__ void __launch_bounds__(kThreads, 2)
             for (int h = 0; h < 2; h++) {
                 const int rr = mt * 16 + gq + 8 * h;
                 if (rr < kH1N) {
-                    const __nv_bfloat162 v0 = __floats2bfloat162_rn(fmaxf(acc0[2 * h] + __ldg(gv.b1 + 2 * tq), 0.0f),
-                                                                    fmaxf(acc0[2 * h + 1] + __ldg(gv.b1 + 2 * tq + 1), 0.0f));
-                    const __nv_bfloat162 v1 = __floats2bfloat162_rn(fmaxf(acc1[2 * h] + __ldg(gv.b1 + 8 + 2 * tq), 0.0f),
-                                                                    fmaxf(acc1[2 * h + 1] + __ldg(gv.b1 + 9 + 2 * tq), 0.0f));
-                    h1w[rr * 8 + tq] = *reinterpret_cast<const unsigned*>(&v0);
-                    h1w[rr * 8 + 4 + tq] = *reinterpret_cast<const unsigned*>(&v1);
+                    const __nv_bfloat162 v0 = __floats2bfloat162_rn(fmaxf(acc0[2 * h], 0.0f), fmaxf(acc0[2 * h + 1], 0.0f));
+                    const __nv_bfloat162 v1 = __floats2bfloat162_rn(fmaxf(acc1[2 * h], 0.0f), fmaxf(acc1[2 * h + 1], 0.0f));
+                    h1w[rr * kH1Ld + tq] = *reinterpret_cast<const unsigned*>(&v0);
+                    h1w[rr * kH1Ld + 4 + tq] = *reinterpret_cast<const unsigned*>(&v1);
                 }
             }
         }
         __syncthreads();
         // layer 2 and head: q = sigmoid(relu(conv3x3(h1) W2 + b2) . W3 + b3) on
         // the tile + kQM region (rows of the last m-tile past it repeat its last pixel)
-        for (int mt = warp; mt < kQTiles; mt += kThreads / 32) {
-            const int r = min(mt * 16 + (lane & 15), kQN - 1);
-            const int qx = r % kQW, qy = r / kQW;
-            float acc0[4] = {0, 0, 0, 0}, acc1[4] = {0, 0, 0, 0};
+        {
+            const float b2a = __ldg(gv.b2 + 2 * tq), b2b = __ldg(gv.b2 + 2 * tq + 1);
+            const float b2c = __ldg(gv.b2 + 8 + 2 * tq), b2d = __ldg(gv.b2 + 9 + 2 * tq);
+            const float w3a = __ldg(gv.W3 + 2 * tq), w3b = __ldg(gv.W3 + 2 * tq + 1);
+            const float w3c = __ldg(gv.W3 + 8 + 2 * tq), w3d = __ldg(gv.W3 + 9 + 2 * tq);
+            const float b3 = __ldg(gv.b3);
+            for (int mt = warp; mt < kQTiles; mt += kThreads / 32) {
+                const int r = min(mt * 16 + (lane & 15), kQN - 1);
+                const int qx = r % kQW, qy = r / kQW;
+                const unsigned* ha = h1w + (qy * kH1W + qx) * kH1Ld + (lane >> 4) * 4;
+                float acc0[4] = {b2a, b2b, b2a, b2b}, acc1[4] = {b2c, b2d, b2c, b2d};
 #pragma unroll
-            for (int tap = 0; tap < 9; tap++) {
-                const int hi = (qy + tap / 3) * kH1W + qx + tap % 3;
-                unsigned a[4], b[4];
-                ldsm_x4(a, h1w + hi * 8 + (lane >> 4) * 4);
-                ldsm_x4(b, W2s + ((lane & 7) + ((lane >> 4) << 3)) * kW2Ld + 16 * tap + ((lane >> 3) & 1) * 8);
-                mma_bf16(acc0, a, b[0], b[1]);
-                mma_bf16(acc1, a, b[2], b[3]);
-            }
+                for (int tap = 0; tap < 9; tap++) {
+                    unsigned a[4], b[4];
+                    ldsm_x4(a, ha + ((tap / 3) * kH1W + tap % 3) * kH1Ld);
+                    ldsm_x4(b, w2row + 16 * tap);
+                    mma_bf16(acc0, a, b[0], b[1]);
+                    mma_bf16(acc1, a, b[2], b[3]);
+                }
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int c0 = 2 * tq, c1 = 8 + 2 * tq;
-                float part = __ldg(gv.W3 + c0) * fmaxf(acc0[2 * h] + __ldg(gv.b2 + c0), 0.0f) +
-                             __ldg(gv.W3 + c0 + 1) * fmaxf(acc0[2 * h + 1] + __ldg(gv.b2 + c0 + 1), 0.0f) +
-                             __ldg(gv.W3 + c1) * fmaxf(acc1[2 * h] + __ldg(gv.b2 + c1), 0.0f) +
-                             __ldg(gv.W3 + c1 + 1) * fmaxf(acc1[2 * h + 1] + __ldg(gv.b2 + c1 + 1), 0.0f);
-                part += __shfl_xor_sync(0xffffffffu, part, 1);
-                part += __shfl_xor_sync(0xffffffffu, part, 2);
-                if (tq == 0) qs[mt * 16 + gq + 8 * h] = 1.0f / (1.0f + __expf(-(part + __ldg(gv.b3))));
+                for (int h = 0; h < 2; h++) {
+                    float part = w3a * fmaxf(acc0[2 * h], 0.0f) + w3b * fmaxf(acc0[2 * h + 1], 0.0f) +
+                                 w3c * fmaxf(acc1[2 * h], 0.0f) + w3d * fmaxf(acc1[2 * h + 1], 0.0f);
+                    part += __shfl_xor_sync(0xffffffffu, part, 1);
+                    part += __shfl_xor_sync(0xffffffffu, part, 2);
+                    if (tq == 0) qs[mt * 16 + gq + 8 * h] = 1.0f / (1.0f + __expf(-(part + b3)));
+                }
             }
         }
         __syncthreads();
