@@ -303,6 +303,9 @@ def run_ours(args):
         "learned_f32": time_form(scenes, args, dict(learned=1), lambda s: s.disp, FRAME_ALGO_BYTES, dist, world),
         "learned_u16_snorm16": time_form(scenes, args, dict(u16, learned=1), lambda s: s.disp_u16, 27, dist,
                                          world),
+        # the paper's larger adaptive setting (Table perf-disc2): star-fill CD with 16 directions, 30 steps
+        "cd_s30_d16_f32": time_form(scenes, args, dict(dirs=16, steps=30), lambda s: s.disp, FRAME_ALGO_BYTES,
+                                    dist, world),
     }
     for f in forms.values():
         f["vs_plain"] = f["value"] / value

@@ -59,6 +59,15 @@ def test_scene_full_size(P, name):
     print(f"{name}: normals mean {mean:.2e} max {mx:.2e} deg, {ref.n_components} components")
 
 
+def test_starfill_s30_d16_full_size(P):
+    # the paper's larger adaptive setting (Table perf-disc2, CD s30 d16) on a
+    # whole 1482x994 frame: table-driven star with shared diagonal pixels
+    s = make_scene("mixed_1482x994", frame=2)
+    g, ref = chain(P, s.disp, s.camera, support=1, dirs=16, steps=30)
+    mean, mx = compare_frame(g, ref)
+    print(f"s30 d16: normals mean {mean:.2e} max {mx:.2e} deg")
+
+
 def test_driving_u16_and_f16_inputs(P):
     s = make_scene("driving_2048x1024", frame=1)
     for arr, dt in ((s.disp_u16, P.sn.SN_IN_U16X256), (s.disp_f16, P.sn.SN_IN_F16)):
