@@ -309,6 +309,9 @@ def run_ours(args):
     }
     for f in forms.values():
         f["vs_plain"] = f["value"] / value
+    # the comparison estimators of Sec. IV on the same scenes (normals only)
+    comparators = {"cross": time_comparator(scenes, args, "cross", 0, world),
+                   "pca_9x9": time_comparator(scenes, args, "pca", 4, world)}
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
@@ -358,6 +361,7 @@ def run_ours(args):
                                  / hbm_peak}},
             "gpu_launches": int(launches),
             "forms": forms,
+            "comparators": comparators,
             "clocks": clk,
             "e2e": e2e,
             "serving": serving,
@@ -447,6 +451,65 @@ def time_form(scenes, args, params, pick, bytes_per_px, dist, world):
             "algo_bytes_per_px": bytes_per_px,
             "gt_error_deg": gt,
             "params": {k: int(v) for k, v in params.items()}}
+
+
+def time_comparator(scenes, args, which, r, world):
+    """Device throughput and ground-truth error of a comparison estimator of
+    Sec. IV (sn_cross_normals, sn_pca_normals) on the same scenes: normals and
+    mask only, so compare it with the chain's normal stage, not the chain."""
+    import torch
+    from paper_2504_15121_gb300 import sn
+    s0 = scenes[0]
+    ctx = sn.sn_create(s0.camera, s0.W, s0.H, sn.default_params())
+    try:
+        disp = []
+        for s in scenes:
+            t = sn.empty_image(s0.H, s0.W, torch.float32)
+            t.copy_(torch.from_numpy(s.disp))
+            disp.append(t)
+        F = args.frames
+        outs = [(sn.empty_planes(3, s0.H, s0.W), sn.empty_image(s0.H, s0.W, torch.uint8)) for _ in range(F)]
+        main = torch.cuda.current_stream()
+        streams = [torch.cuda.Stream() for _ in range(args.streams)]
+
+        def step():
+            ev = main.record_event()
+            for st in streams:
+                st.wait_event(ev)
+            for f in range(F):
+                n, m = outs[f]
+                st = streams[f % len(streams)]
+                if which == "cross":
+                    sn.sn_cross_normals(ctx, disp[f % len(disp)], n, m, stream=st)
+                else:
+                    sn.sn_pca_normals(ctx, disp[f % len(disp)], r, n, m, stream=st)
+            for st in streams:
+                main.wait_stream(st)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = max(3, args.steps // 4)
+        t0.record(main)
+        for _ in range(steps):
+            step()
+        t1.record(main)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        sn.sn_check_device(ctx)
+
+        class _O:
+            pass
+        wrapped = []
+        for n, m in outs[:len(scenes)]:
+            o = _O()
+            o.normals, o.mask = n, m
+            wrapped.append(o)
+        gt = gt_error_deg(wrapped, scenes)
+    finally:
+        sn.sn_destroy(ctx)
+    return {"value": world * steps * F * s0.W * s0.H / (ms / 1e3) / 1e6, "unit": "MPix/s",
+            "what": "normals + mask only", "gt_error_deg": gt}
 
 
 def gt_error_deg(outs, scenes):

@@ -167,6 +167,27 @@ sn_status sn_affine_normals(sn_ctx *ctx, const void *disp, size_t disp_pitch, co
                             size_t den_pitch, void *normals, size_t normals_pitch, uint8_t *mask,
                             size_t mask_pitch, sn_stream stream);
 
+/* Comparison estimators of the paper's experiments (Sec. IV, "Implemented
+ * algorithms"), on the same ingest; not part of sn_run_frame.  Points are
+ * X = B (u - cx, fx/fy (v - cy), fx) / (D / 256) of the valid pixels.
+ * sn_cross_normals ("Cross"): n = t_u x t_v with t_u = X(u+1, v) - X(u, v),
+ *   or X(u, v) - X(u-1, v) when the right neighbour is invalid, and t_v the
+ *   same downwards / upwards; a normal iff the centre and both tangents
+ *   exist.
+ * sn_pca_normals ("PCA n x n", n = 2r + 1, 1 <= r <= 7 else SN_EINVAL): the
+ *   eigenvector of the smallest eigenvalue of the covariance of the valid
+ *   points of the window (centre included), closed form in FP32; a normal
+ *   iff the centre is valid and the window holds >= 3 valid pixels that
+ *   are not all on one image line (exact integer test).
+ * Both turn the normal towards the camera (n . X < 0).
+ *   disp     [H][disp_pitch] input in the context's in_dtype
+ *   normals  the context's normal_fmt
+ *   mask     uint8 output: SN_MASK_VALID | SN_MASK_NORMAL */
+sn_status sn_cross_normals(sn_ctx *ctx, const void *disp, size_t disp_pitch, void *normals,
+                           size_t normals_pitch, uint8_t *mask, size_t mask_pitch, sn_stream stream);
+sn_status sn_pca_normals(sn_ctx *ctx, const void *disp, size_t disp_pitch, int r, void *normals,
+                         size_t normals_pitch, uint8_t *mask, size_t mask_pitch, sn_stream stream);
+
 /* Connected surface components (abstract: "detecting connected surface
  * components"; adaptive relative threshold as in the covered-depth rule of
  * Sec. III-D).  Two 4-neighbours p, q are joined iff both are valid and

@@ -359,6 +359,33 @@ sn_status sn_affine_normals(sn_ctx* c, const void* disp, size_t dpitch, const fl
     return e == cudaSuccess ? SN_OK : cuda_fail(c, e, "sn_affine_normals");
 }
 
+sn_status sn_cross_normals(sn_ctx* c, const void* disp, size_t dpitch, void* nrm, size_t np, uint8_t* mask,
+                           size_t mp, sn_stream stream) {
+    if (!c) return SN_EINVAL;
+    sn_status st;
+    if ((st = check_buf(c, disp, dpitch, in_elem(c->p.in_dtype), "disp")) != SN_OK) return st;
+    if ((st = check_buf(c, nrm, np, nrm_elem(c->p.normal_fmt), "normals")) != SN_OK) return st;
+    if ((st = check_buf(c, mask, mp, 1, "mask")) != SN_OK) return st;
+    sn::Marks mk;
+    cudaError_t e = sn::launch_cross(c->geo, disp, dpitch, nrm, np, mask, mp, stream, mk);
+    c->launches += mk.launches;
+    return e == cudaSuccess ? SN_OK : cuda_fail(c, e, "sn_cross_normals");
+}
+
+sn_status sn_pca_normals(sn_ctx* c, const void* disp, size_t dpitch, int r, void* nrm, size_t np, uint8_t* mask,
+                         size_t mp, sn_stream stream) {
+    if (!c) return SN_EINVAL;
+    if (r < 1 || r > 7) return fail(c, SN_EINVAL, "pca radius outside 1..7");
+    sn_status st;
+    if ((st = check_buf(c, disp, dpitch, in_elem(c->p.in_dtype), "disp")) != SN_OK) return st;
+    if ((st = check_buf(c, nrm, np, nrm_elem(c->p.normal_fmt), "normals")) != SN_OK) return st;
+    if ((st = check_buf(c, mask, mp, 1, "mask")) != SN_OK) return st;
+    sn::Marks mk;
+    cudaError_t e = sn::launch_pca(c->geo, disp, dpitch, r, nrm, np, mask, mp, stream, mk);
+    c->launches += mk.launches;
+    return e == cudaSuccess ? SN_OK : cuda_fail(c, e, "sn_pca_normals");
+}
+
 sn_status sn_components(sn_ctx* c, const void* disp, size_t dpitch, int32_t* labels, size_t lp, int32_t* ncomp,
                         sn_stream stream) {
     if (!c) return SN_EINVAL;

@@ -89,6 +89,11 @@ cudaError_t launch_points(const Geo& g, const float* den, size_t denp, const uin
 // three stage slots: tile-local union-find, border merge, flatten
 cudaError_t launch_components(const Geo& g, const void* disp, size_t dp, int32_t* labels,
                               size_t lp, int32_t* count, cudaStream_t s, Marks& mk);
+// comparison estimators (one stage slot each)
+cudaError_t launch_cross(const Geo& g, const void* disp, size_t dp, void* nrm, size_t np, uint8_t* mask,
+                         size_t mp, cudaStream_t s, Marks& mk);
+cudaError_t launch_pca(const Geo& g, const void* disp, size_t dp, int r, void* nrm, size_t np, uint8_t* mask,
+                       size_t mp, cudaStream_t s, Marks& mk);
 // two stage slots: border merge between tw x th tiles, flatten
 cudaError_t launch_ccl_merge_flatten(const Geo& g, const void* disp, size_t dp, int32_t* labels,
                                      size_t lp, int32_t* count, int tw, int th, cudaStream_t s,

@@ -75,6 +75,8 @@ def _load():
         "sn_denoise": ([vp, vp, sz, vp, sz, vp, sz, vp], i),
         "sn_affine_normals": ([vp, vp, sz, vp, sz, vp, sz, vp, sz, vp], i),
         "sn_components": ([vp, vp, sz, vp, sz, vp, vp], i),
+        "sn_cross_normals": ([vp, vp, sz, vp, sz, vp, sz, vp], i),
+        "sn_pca_normals": ([vp, vp, sz, i, vp, sz, vp, sz, vp], i),
         "sn_pointcloud": ([vp, vp, sz, vp, sz, vp, sz, vp], i),
         "sn_run_frame": ([vp, C.POINTER(sn_frame_in), C.POINTER(sn_frame_out), vp], i),
         "sn_load_gate_weights": ([vp, vp, sz], i),
@@ -104,7 +106,8 @@ EXPORTS = ("sn_version", "sn_default_params", "sn_create", "sn_destroy", "sn_den
            "sn_affine_normals", "sn_components", "sn_pointcloud", "sn_run_frame",
            "sn_load_gate_weights", "sn_star_offsets", "sn_check_device", "sn_status_string",
            "sn_last_error", "sn_set_profiling", "sn_stage_count", "sn_stage_name",
-           "sn_stage_times", "sn_launch_count", "sn_normals_noalloc")
+           "sn_stage_times", "sn_launch_count", "sn_normals_noalloc", "sn_cross_normals",
+           "sn_pca_normals")
 
 
 # ---------------------------------------------------------------- helpers
@@ -207,6 +210,20 @@ def sn_affine_normals(ctx, disp, den, normals, mask, stream=None):
     n, np_ = _img(normals)
     m, mp = _img(mask)
     _check(ctx, lib.sn_affine_normals(ctx, d, dp, e, ep, n, np_, m, mp, _stream(stream)))
+
+
+def sn_cross_normals(ctx, disp, normals, mask, stream=None):
+    d, dp = _img(disp)
+    n, np_ = _img(normals)
+    m, mp = _img(mask)
+    _check(ctx, lib.sn_cross_normals(ctx, d, dp, n, np_, m, mp, _stream(stream)))
+
+
+def sn_pca_normals(ctx, disp, r, normals, mask, stream=None):
+    d, dp = _img(disp)
+    n, np_ = _img(normals)
+    m, mp = _img(mask)
+    _check(ctx, lib.sn_pca_normals(ctx, d, dp, int(r), n, np_, m, mp, _stream(stream)))
 
 
 def sn_components(ctx, disp, labels, num_components=None, stream=None):
