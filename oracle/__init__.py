@@ -24,7 +24,7 @@ _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "libsn_oracle.so")
 
 F32, F16, U16X256 = 0, 1, 2
-FIXED, STAR_CD = 0, 1
+FIXED, STAR_CD, STAR_ST = 0, 1, 2
 M_VALID, M_NORMAL, M_FP64, M_LEARNED, M_DENOISED = 1, 2, 4, 8, 16
 
 
@@ -36,7 +36,7 @@ class _Camera(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("r_denoise", C.c_int), ("r_affine", C.c_int), ("support", C.c_int),
                 ("dirs", C.c_int), ("steps", C.c_int), ("k_cd", C.c_double),
-                ("k_pair", C.c_double), ("k_range", C.c_double)]
+                ("k_pair", C.c_double), ("k_range", C.c_double), ("st_t", C.c_double)]
 
 
 @dataclass
@@ -51,10 +51,11 @@ class Params:
     k_cd: float = 0.1
     k_pair: float = 0.05
     k_range: float = 0.05
+    st_t: float = 0.1      # ST threshold on the depth Laplacian (metres)
 
     def c(self) -> _Params:
         return _Params(self.r_denoise, self.r_affine, self.support, self.dirs, self.steps,
-                       self.k_cd, self.k_pair, self.k_range)
+                       self.k_cd, self.k_pair, self.k_range, self.st_t)
 
 
 def build(force: bool = False) -> str:
@@ -62,7 +63,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_LIB_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fopenmp", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -83,7 +84,9 @@ def lib():
         L.orc_denoise.argtypes = [p, C.c_int, C.c_int, C.POINTER(_Params), p, p]
         L.orc_star_offsets.argtypes = [C.c_int, C.c_int, p, p]
         L.orc_star_offsets.restype = C.c_int
-        L.orc_support_mask.argtypes = [p, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(_Params), p]
+        L.orc_support_mask.argtypes = [p, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(_Params), p, p]
+        L.orc_st_edges.argtypes = [p, C.c_int, C.c_int, C.POINTER(_Camera), C.c_double, p]
+        L.orc_st_edges.restype = None
         L.orc_support_mask.restype = C.c_int
         L.orc_affine_normals.argtypes = [p, p, C.c_int, C.c_int, C.POINTER(_Camera),
                                          C.POINTER(_Params), p, p, p]
@@ -145,14 +148,27 @@ def star_offsets(dirs: int, steps: int):
     return ou.reshape(dirs, steps), ov.reshape(dirs, steps)
 
 
-def support_mask(D: np.ndarray, u: int, v: int, params: Params | None = None):
-    """Boolean (2R+1)^2 grid of the offsets in the support of pixel (u, v)."""
+def st_edges(D: np.ndarray, cam, t: float) -> np.ndarray:
+    """ST edge map: |5-point depth Laplacian| > t (metres), or an invalid
+    4-neighbour (Sec. III-D, simple thresholding)."""
+    D = np.ascontiguousarray(D, dtype=np.int32)
+    H, W = D.shape
+    E = np.zeros((H, W), np.uint8)
+    lib().orc_st_edges(_ptr(D), W, H, C.byref(_cam(cam)), float(t), _ptr(E))
+    return E.astype(bool)
+
+
+def support_mask(D: np.ndarray, u: int, v: int, params: Params | None = None, cam=None):
+    """Boolean (2R+1)^2 grid of the offsets in the support of pixel (u, v)
+    (the ST support needs the camera for its edge map)."""
     params = params or Params()
     D = np.ascontiguousarray(D, dtype=np.int32)
     H, W = D.shape
     R = params.r_affine if params.support == FIXED else params.steps
     incl = np.zeros((2 * R + 1, 2 * R + 1), np.uint8)
-    lib().orc_support_mask(_ptr(D), W, H, u, v, C.byref(params.c()), _ptr(incl))
+    E = np.ascontiguousarray(st_edges(D, cam, params.st_t), np.uint8) if params.support == STAR_ST else None
+    lib().orc_support_mask(_ptr(D), W, H, u, v, C.byref(params.c()), _ptr(E) if E is not None else None,
+                           _ptr(incl))
     return incl.astype(bool)
 
 

@@ -30,6 +30,12 @@
  *       support is the set union of visited offsets; the stopping pixel and
  *       invalid pixels are excluded; the centre contributes nothing.
  *   R8  covered-depth test in exact integer form.
+ *   R9  simple-thresholding stop (ST, Sec. III-D): an edge pixel is one whose
+ *       5-point depth Laplacian ((z_l + z_r) + (z_u + z_d)) - 4 z_c, with
+ *       z = (256 fx B) / D in metres, exceeds t in magnitude, or one with an
+ *       invalid 4-neighbour; evaluated in FP64 in exactly that order with no
+ *       fused multiply-add; a ray stops before the first invalid or edge
+ *       pixel (excluded, as R7's stopping pixel).
  *   R10 components: 4-connected, edge iff both valid and
  *       2^16 |Dp - Dq| <= K_pair min(Dp, Dq); label = minimum row-major index.
  *   R11 normal valid iff centre valid, >= 3 support pixels, det > 0;
@@ -46,7 +52,7 @@
 #define ORC_DMAX 131071 /* largest integer disparity code: d < 512 px */
 
 enum { ORC_F32 = 0, ORC_F16 = 1, ORC_U16X256 = 2 };
-enum { ORC_FIXED = 0, ORC_STAR_CD = 1 };
+enum { ORC_FIXED = 0, ORC_STAR_CD = 1, ORC_STAR_ST = 2 };
 enum {
     ORC_M_VALID = 1,     /* input disparity valid */
     ORC_M_NORMAL = 2,    /* normal valid */
@@ -74,6 +80,7 @@ typedef struct {
     double k_cd;
     double k_pair;
     double k_range;
+    double st_t; /* ST threshold on the depth Laplacian, metres */
 } orc_params;
 
 /* K = rint(k 2^16): fixed-point form of a relative threshold. */
@@ -232,10 +239,34 @@ static int cd_stop(int64_t Dmin, int64_t Dmax, int64_t Dc, int64_t K)
     return (Dmax - Dmin) * Dc * 65536 > K * Dmin * Dmax;
 }
 
+/* ST edge map (R9): E[v W + u] = 1 for an edge pixel. */
+void orc_st_edges(const int32_t *D, int W, int H, const orc_camera *cam, double t, uint8_t *E)
+{
+    const double F = (256.0 * cam->fx) * cam->baseline;
+#pragma omp parallel for schedule(static)
+    for (int v = 0; v < H; v++)
+        for (int u = 0; u < W; u++) {
+            const int32_t Dc = at(D, W, H, u, v), Dl = at(D, W, H, u - 1, v), Dr = at(D, W, H, u + 1, v);
+            const int32_t Du = at(D, W, H, u, v - 1), Dd = at(D, W, H, u, v + 1);
+            uint8_t e = 1;
+            if (Dc > 0 && Dl > 0 && Dr > 0 && Du > 0 && Dd > 0) {
+                const double zc = F / (double)Dc, zl = F / (double)Dl, zr = F / (double)Dr;
+                const double zu = F / (double)Du, zd = F / (double)Dd;
+                const double a = zl + zr;
+                const double b = zu + zd;
+                const double c = a + b;
+                const double L = c - 4.0 * zc;
+                e = fabs(L) > t;
+            }
+            E[(size_t)v * W + u] = e;
+        }
+}
+
 /* Support of pixel (u, v): incl is a (2R+1)^2 grid of offsets, R the
- * support radius.  Returns the number of included (non-centre) offsets. */
+ * support radius.  Returns the number of included (non-centre) offsets.
+ * stedge: the ST edge map (ST support only). */
 static int support_of(const int32_t *D, int W, int H, int u, int v, const orc_params *P,
-                      const int *tou, const int *tov, uint8_t *incl, int R)
+                      const int *tou, const int *tov, uint8_t *incl, int R, const uint8_t *stedge)
 {
     int side = 2 * R + 1, n = 0;
     memset(incl, 0, (size_t)side * side);
@@ -249,6 +280,21 @@ static int support_of(const int32_t *D, int W, int H, int u, int v, const orc_pa
                     continue;
                 if (at(D, W, H, u + ou, v + ov) > 0) {
                     incl[(ov + R) * side + ou + R] = 1;
+                    n++;
+                }
+            }
+        return n;
+    }
+    if (P->support == ORC_STAR_ST) {
+        for (int j = 0; j < P->dirs; j++)
+            for (int k = 1; k <= P->steps; k++) {
+                int ou = tou[j * P->steps + k - 1], ov = tov[j * P->steps + k - 1];
+                int uu = u + ou, vv = v + ov;
+                if (at(D, W, H, uu, vv) <= 0 || stedge[(size_t)vv * W + uu])
+                    break; /* an invalid or edge pixel stops the ray and is excluded */
+                uint8_t *cell = &incl[(ov + R) * side + ou + R];
+                if (!*cell) {
+                    *cell = 1;
                     n++;
                 }
             }
@@ -283,14 +329,16 @@ static int support_radius(const orc_params *P)
     return P->support == ORC_FIXED ? P->r_affine : P->steps;
 }
 
-/* Exposed for tests: the support set of one pixel. */
-int orc_support_mask(const int32_t *D, int W, int H, int u, int v, const orc_params *P, uint8_t *incl)
+/* Exposed for tests: the support set of one pixel (stedge: the ST edge
+ * map, for the ST support only). */
+int orc_support_mask(const int32_t *D, int W, int H, int u, int v, const orc_params *P, const uint8_t *stedge,
+                     uint8_t *incl)
 {
     int R = support_radius(P);
     int *tou = malloc(sizeof(int) * (P->dirs * P->steps + 1));
     int *tov = malloc(sizeof(int) * (P->dirs * P->steps + 1));
     orc_star_offsets(P->dirs, P->steps, tou, tov);
-    int n = support_of(D, W, H, u, v, P, tou, tov, incl, R);
+    int n = support_of(D, W, H, u, v, P, tou, tov, incl, R, stedge);
     free(tou);
     free(tov);
     return n;
@@ -339,6 +387,11 @@ static void affine_impl(const int32_t *D, const double *den, int W, int H, const
     int *tou = malloc(sizeof(int) * (P->dirs * P->steps + 1));
     int *tov = malloc(sizeof(int) * (P->dirs * P->steps + 1));
     orc_star_offsets(P->dirs, P->steps, tou, tov);
+    uint8_t *stedge = NULL;
+    if (P->support == ORC_STAR_ST) {
+        stedge = malloc((size_t)W * H);
+        orc_st_edges(D, W, H, cam, P->st_t, stedge);
+    }
 #pragma omp parallel
     {
         uint8_t *incl = malloc((size_t)side * side);
@@ -360,7 +413,7 @@ static void affine_impl(const int32_t *D, const double *den, int W, int H, const
                 const int certified = gate && gate[idx];
                 if (certified)
                     m |= ORC_M_LEARNED;
-                int N = support_of(D, W, H, u, v, certified ? &Pg : P, tou, tov, incl, R);
+                int N = support_of(D, W, H, u, v, certified ? &Pg : P, tou, tov, incl, R, stedge);
                 double alpha = 0, beta = 0, gamma = 0;
                 for (int ov = -R; ov <= R; ov++)
                     for (int ou = -R; ou <= R; ou++)
@@ -425,6 +478,7 @@ static void affine_impl(const int32_t *D, const double *den, int W, int H, const
     }
     free(tou);
     free(tov);
+    free(stedge);
 }
 
 /* ---------------------------------------------------------------------

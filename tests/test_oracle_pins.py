@@ -568,3 +568,73 @@ def test_gated_chain_is_box_mean_and_full_window():
     assert ((fr.mask[gate] & oracle.M_LEARNED) > 0).all() and not (fr.mask[~gate] & oracle.M_LEARNED).any()
     plain = oracle.run_frame(disp, CAM)
     assert np.array_equal(fr.normals[~gate], plain.normals[~gate])
+
+
+# ---------------------------------------------------------------- ST stop (Sec. III-D)
+def test_st_edges_constant_and_step():
+    # constant depth: Laplacian 0 inside; the border and invalid pixels'
+    # neighbours are edges (a 4-neighbour is missing)
+    D = np.full((12, 16), 6000, np.int32)
+    D[5, 7] = 0
+    E = oracle.st_edges(D, CAM, 0.01)
+    inner = np.zeros_like(E)
+    inner[1:-1, 1:-1] = True
+    want = ~inner
+    for (v, u) in [(5, 7), (4, 7), (6, 7), (5, 6), (5, 8)]:
+        want[v, u] = True
+    assert np.array_equal(E, want)
+    # a depth step between columns 7 and 8: the two columns beside it see
+    # |Laplacian| = |z1 - z2|, an edge iff that exceeds t
+    D = np.full((12, 16), 6000, np.int32)
+    D[:, 8:] = 6200
+    F = 256.0 * CAM.fx * CAM.baseline
+    dz = F / 6000 - F / 6200
+    for t, edge in [(0.5 * dz, True), (1.5 * dz, False)]:
+        E = oracle.st_edges(D, CAM, t)
+        assert (E[1:-1, 7] == edge).all() and (E[1:-1, 8] == edge).all()
+        assert not E[1:-1, 1:7].any() and not E[1:-1, 9:-1].any()
+
+
+def test_st_laplacian_scale_on_a_paraboloid():
+    # z = z0 + a (u^2 + v^2) has 5-point Laplacian 4a everywhere; the codes
+    # round z, so thresholds 10 % either side of 4a switch every interior pixel
+    H, W, a, z0 = 20, 24, 0.02, 1.5
+    F = 256.0 * CAM.fx * CAM.baseline
+    u = np.arange(W)[None, :] - W / 2
+    v = np.arange(H)[:, None] - H / 2
+    D = np.rint(F / (z0 + a * (u * u + v * v))).astype(np.int32)
+    assert (D > 0).all() and (D <= 131071).all()
+    assert oracle.st_edges(D, CAM, 0.9 * 4 * a)[1:-1, 1:-1].all()
+    assert not oracle.st_edges(D, CAM, 1.1 * 4 * a)[1:-1, 1:-1].any()
+
+
+def test_st_support_brute_force():
+    # rays stop before the first invalid or edge pixel, which is excluded
+    rng = np.random.default_rng(9)
+    H, W = 30, 34
+    D = rng.integers(5000, 5100, (H, W)).astype(np.int32)
+    D[:, 17:] += 900
+    D[rng.random((H, W)) < 0.05] = 0
+    t = 0.05
+    E = oracle.st_edges(D, CAM, t)
+    M, s = 8, 10
+    p = Params(support=oracle.STAR_ST, dirs=M, steps=s, st_t=t)
+    checked = 0
+    for v in range(H):
+        for u in range(W):
+            if D[v, u] <= 0:
+                continue
+            want = set()
+            for j in range(M):
+                th = 2 * math.pi * j / M
+                for k in range(1, s + 1):
+                    o = (_round_half_away(k * math.cos(th)), _round_half_away(k * math.sin(th)))
+                    uu, vv = u + o[0], v + o[1]
+                    if not (0 <= uu < W and 0 <= vv < H) or D[vv, uu] <= 0 or E[vv, uu]:
+                        break
+                    want.add(o)
+            got = oracle.support_mask(D, u, v, p, cam=CAM)
+            assert {(ou - s, ov - s) for ov, ou in zip(*np.nonzero(got))} == want, (u, v)
+            checked += 1
+    assert checked > 900
+    assert 0.05 < E.mean() < 0.6      # the test exercises both outcomes
