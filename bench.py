@@ -306,6 +306,9 @@ def run_ours(args):
         # the paper's larger adaptive setting (Table perf-disc2): star-fill CD with 16 directions, 30 steps
         "cd_s30_d16_f32": time_form(scenes, args, dict(dirs=16, steps=30), lambda s: s.disp, FRAME_ALGO_BYTES,
                                     dist, world),
+        # star-fill with the depth-edge stop (ST s10 d8 t0.1, Table perf-disc)
+        "st_s10_d8_f32": time_form(scenes, args, dict(support=2, st_t=0.1), lambda s: s.disp, FRAME_ALGO_BYTES,
+                                   dist, world),
     }
     for f in forms.values():
         f["vs_plain"] = f["value"] / value

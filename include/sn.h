@@ -63,7 +63,7 @@ typedef struct {
     double fx, fy, cx, cy, baseline;
 } sn_camera;
 
-enum { SN_SUPPORT_FIXED = 0, SN_SUPPORT_STARFILL_CD = 1 };
+enum { SN_SUPPORT_FIXED = 0, SN_SUPPORT_STARFILL_CD = 1, SN_SUPPORT_STARFILL_ST = 2 };
 enum { SN_IN_F32 = 0, SN_IN_F16 = 1, SN_IN_U16X256 = 2 };
 enum { SN_NORMALS_F32X3 = 0, SN_NORMALS_SNORM16X4 = 1 };
 
@@ -80,7 +80,8 @@ enum {
  *  r_denoise  radius of the denoise window (1..4), default 2 (5x5)
  *  r_affine   radius of the fixed affine window (1..15), default 4 (9x9;
  *             the paper's main setting, Tables perf-disc/perf-disc2)
- *  support    SN_SUPPORT_FIXED or SN_SUPPORT_STARFILL_CD (default; Sec. III-D)
+ *  support    SN_SUPPORT_FIXED, SN_SUPPORT_STARFILL_CD (default) or
+ *             SN_SUPPORT_STARFILL_ST (Sec. III-D: rays stop at depth edges)
  *  dirs,steps star-fill directions M (4..16) and steps s (1..30), default 8, 10
  *  k_cd       covered-depth threshold k (Sec. III-D), default 0.1
  *  k_pair     relative disparity step that still joins two 4-neighbours into
@@ -102,6 +103,12 @@ enum {
  *             range gate) and its affine fit every valid sample of the
  *             (2 SN_LEARNED_RADIUS + 1)^2 window but the centre (no
  *             star-fill).  Other pixels take the plain chain.
+ *  st_t       ST threshold t (metres), default 0.1: a pixel is a depth edge
+ *             iff one of its 4-neighbours is invalid or its 5-point depth
+ *             Laplacian ((z_l + z_r) + (z_u + z_d)) - 4 z_c, z = 256 fx B / D,
+ *             exceeds t in magnitude (decided as in FP64 evaluated in that
+ *             order without fused multiply-adds); an ST ray stops before the
+ *             first invalid or edge pixel
  * Every k is used as the integer K = rint(65536 k).
  */
 #define SN_LEARNED_RADIUS 6
@@ -118,6 +125,7 @@ typedef struct {
     int in_dtype;
     int normal_fmt;
     int learned;
+    float st_t;
 } sn_params;
 
 /* Fills *p with the defaults listed above. */

@@ -134,6 +134,15 @@ void cd_band(int K, float* hi, float* lo) {
     *lo = (float)(1.0 - e);
 }
 
+// ST constants: F = 256 fx B as the FP64 product (256 fx) B (the order the
+// exact Laplacian test uses), its FP32 copy for the banded fast test, and t.
+static void set_st(sn::Geo& g, const sn_camera* cam, float t) {
+    g.st_F = (256.0 * cam->fx) * cam->baseline;
+    g.st_Ff = (float)g.st_F;
+    g.st_t = (double)t;
+    g.st_tf = t;
+}
+
 // Validates camera, size and parameters like sn_create and fills the kernel
 // constants, without touching the device (used by the allocation-free entry
 // point; err is left null for the caller to set).
@@ -143,7 +152,8 @@ sn_status prepare_constants(const sn_camera* cam, int W, int H, const sn_params*
         !isfinite(cam->fx) || !isfinite(cam->fy) || !isfinite(cam->baseline))
         return SN_EINVAL;
     if (p->r_denoise < 1 || p->r_denoise > 4 || p->r_affine < 1 || p->r_affine > 15) return SN_EINVAL;
-    if (p->support != SN_SUPPORT_FIXED && p->support != SN_SUPPORT_STARFILL_CD) return SN_EINVAL;
+    if (p->support < SN_SUPPORT_FIXED || p->support > SN_SUPPORT_STARFILL_ST) return SN_EINVAL;
+    if (!(p->st_t >= 0.0f) || !isfinite(p->st_t)) return SN_EINVAL;
     if (p->dirs < 4 || p->dirs > kMaxDirs || p->steps < 1 || p->steps > kMaxSteps) return SN_EINVAL;
     if (!(p->k_cd >= 0 && p->k_cd <= 1) || !(p->k_pair >= 0 && p->k_pair <= 1) ||
         !(p->k_range >= 0 && p->k_range <= 1) || !(p->tau >= 0 && p->tau <= 1))
@@ -180,6 +190,7 @@ sn_status prepare_constants(const sn_camera* cam, int W, int H, const sn_params*
     g->dcx = cam->cx;
     g->dcy = cam->cy;
     g->dB = cam->baseline;
+    set_st(*g, cam, p->st_t);
     return SN_OK;
 }
 
@@ -203,6 +214,7 @@ void sn_default_params(sn_params* p) {
     p->in_dtype = SN_IN_F32;
     p->normal_fmt = SN_NORMALS_F32X3;
     p->learned = 0;
+    p->st_t = 0.1f;
 }
 
 const char* sn_status_string(sn_status s) {
@@ -239,7 +251,8 @@ sn_status sn_create(const sn_camera* cam, int W, int H, const sn_params* pin, sn
     else
         sn_default_params(&p);
     if (p.r_denoise < 1 || p.r_denoise > 4 || p.r_affine < 1 || p.r_affine > 15) return SN_EINVAL;
-    if (p.support != SN_SUPPORT_FIXED && p.support != SN_SUPPORT_STARFILL_CD) return SN_EINVAL;
+    if (p.support < SN_SUPPORT_FIXED || p.support > SN_SUPPORT_STARFILL_ST) return SN_EINVAL;
+    if (!(p.st_t >= 0.0f) || !isfinite(p.st_t)) return SN_EINVAL;
     if (p.dirs < 4 || p.dirs > sn::kMaxDirs || p.steps < 1 || p.steps > sn::kMaxSteps) return SN_EINVAL;
     if (!(p.k_cd >= 0 && p.k_cd <= 1) || !(p.k_pair >= 0 && p.k_pair <= 1) || !(p.k_range >= 0 && p.k_range <= 1) ||
         !(p.tau >= 0 && p.tau <= 1))
@@ -293,6 +306,7 @@ sn_status sn_create(const sn_camera* cam, int W, int H, const sn_params* pin, sn
     g.dcx = cam->cx;
     g.dcy = cam->cy;
     g.dB = cam->baseline;
+    sn::set_st(g, cam, p.st_t);
 
     cudaError_t e = cudaMalloc(&c->ws.err, 2 * sizeof(int));
     if (e == cudaSuccess) {

@@ -173,6 +173,64 @@ __device__ __forceinline__ void star_support(const int* c, int TWR, int Dc, int 
     }
 }
 
+// ST edge test (Sec. III-D, simple thresholding) of a pixel from its own
+// and its 4-neighbours' codes: an invalid neighbour makes an edge; otherwise
+// the pixel is an edge iff |((z_l + z_r) + (z_u + z_d)) - 4 z_c| > t with
+// z = F / D, F = 256 fx B, as evaluated in FP64 in exactly that order.  The
+// FP32 evaluation (each z within 2^-23 relative, each sum one rounding)
+// differs from that value by less than 2^-21.4 S, S the sum of the terms'
+// magnitudes, and |L| - t rounds within 2^-24 (S + t); outside the band
+// 2^-19 (S + t) it decides, inside the FP64 expression does (IEEE
+// round-to-nearest operations, no contraction).
+__device__ __forceinline__ bool st_edge(const Geo& g, int Dc, int Dl, int Dr, int Du, int Dd) {
+    if (Dc <= 0 || Dl <= 0 || Dr <= 0 || Du <= 0 || Dd <= 0) return true;
+    const float F = g.st_Ff;
+    const float zc = F * __frcp_rn((float)Dc), zl = F * __frcp_rn((float)Dl), zr = F * __frcp_rn((float)Dr);
+    const float zu = F * __frcp_rn((float)Du), zd = F * __frcp_rn((float)Dd);
+    const float S = zl + zr + zu + zd + 4.0f * zc;
+    const float L = ((zl + zr) + (zu + zd)) - 4.0f * zc;
+    const float dev = fabsf(L) - g.st_tf;
+    const float band = 0x1p-19f * (S + g.st_tf);
+    if (dev > band) return true;
+    if (dev < -band) return false;
+    const double F64 = g.st_F;
+    const double dzc = __ddiv_rn(F64, (double)Dc), dzl = __ddiv_rn(F64, (double)Dl);
+    const double dzr = __ddiv_rn(F64, (double)Dr), dzu = __ddiv_rn(F64, (double)Du);
+    const double dzd = __ddiv_rn(F64, (double)Dd);
+    const double c = __dadd_rn(__dadd_rn(dzl, dzr), __dadd_rn(dzu, dzd));
+    return fabs(__dsub_rn(c, __dmul_rn(4.0, dzc))) > g.st_t;
+}
+
+// Star-fill with the ST stop on an int tile: a ray stops before the first
+// invalid or edge pixel.  e points at the centre's entry of an edge-byte
+// array laid out like the tile.
+__device__ __forceinline__ void star_support_st(const int* c, const uint8_t* e, int TWR, int Dc,
+                                                const StarTable& T, int dirs, int steps, AffSums& s) {
+    aff_zero(s);
+    unsigned long long bits = 0ull;
+    for (int j = 0; j < dirs; j++) {
+        const int e0 = j * steps;
+        for (int k = 0; k < steps; k++) {
+            const int en = e0 + k;
+            const int cls = T.cls[en];
+            if (cls == 0) continue;  // same pixel as the previous step
+            const int ou = T.ou[en], ov = T.ov[en];
+            const int Di = c[ov * TWR + ou];
+            if (Di <= 0 || e[ov * TWR + ou]) break;
+            if (cls == 1)
+                aff_add(s, ou, ov, Di - Dc);
+            else
+                bits |= 1ull << T.bit[en];
+        }
+    }
+    for (int b = 0; b < T.nshared; b++) {
+        if ((bits >> b) & 1ull) {
+            const int ou = T.sou[b], ov = T.sov[b];
+            aff_add(s, ou, ov, c[ov * TWR + ou] - Dc);
+        }
+    }
+}
+
 // int64 -> float through two 32-bit conversions of |x| (the direct 64-bit
 // conversion uses the slow FP64 pipe): correctly rounded for |x| < 2^32, at
 // most ~1.5 ulp off above that (|x| < 2^55).

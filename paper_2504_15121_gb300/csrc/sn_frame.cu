@@ -183,6 +183,36 @@ __device__ __forceinline__ void star_table(const int2* c, int stride, int Dc, fl
     }
 }
 
+// Star table with the ST stop on the packed tile: a ray stops before the
+// first invalid or edge pixel (ec: the centre's entry of the edge bytes,
+// laid out like the tile).
+__device__ __forceinline__ void star_table_st(const int2* c, const uint8_t* ec, int stride, int Dc,
+                                              const StarTable& T, int dirs, int steps, AffSums& s) {
+    aff_zero(s);
+    unsigned long long bits = 0ull;
+    for (int j = 0; j < dirs; j++) {
+        const int e0 = j * steps;
+        for (int k = 0; k < steps; k++) {
+            const int e = e0 + k;
+            const int cls = T.cls[e];
+            if (cls == 0) continue;
+            const int ou = T.ou[e], ov = T.ov[e];
+            const int Di = c[ov * stride + ou].x;
+            if (Di <= 0 || ec[ov * stride + ou]) break;
+            if (cls == 1)
+                aff_add(s, ou, ov, Di - Dc);
+            else
+                bits |= 1ull << T.bit[e];
+        }
+    }
+    for (int b = 0; b < T.nshared; b++) {
+        if ((bits >> b) & 1ull) {
+            const int ou = T.sou[b], ov = T.sov[b];
+            aff_add(s, ou, ov, c[ov * stride + ou].x - Dc);
+        }
+    }
+}
+
 __device__ __forceinline__ void fixed_packed(const int2* c, int stride, int R, int Dc, AffSums& s) {
     aff_zero(s);
     for (int ov = -R; ov <= R; ov++) {
@@ -328,7 +358,7 @@ __device__ __forceinline__ void emit(const Geo& g, const FrameOut& o, int x, int
 // star-fill), two-pass fit, normal, point.  c points at the pixel in the tile.
 template <int VAR, int R, int RD>
 __device__ __forceinline__ void plain_pixel(const Geo& g, const StarTable& T, const int2* c, int TWR, int x, int y,
-                                            PixOut& r) {
+                                            PixOut& r, const uint8_t* ec = nullptr) {
     pix_zero(r);
     const int2 cc = c[0];
     const int Dc = cc.x;
@@ -340,7 +370,9 @@ __device__ __forceinline__ void plain_pixel(const Geo& g, const StarTable& T, co
     if (fit) r.m |= SN_MASK_DENOISED;
     r.dtil = ((float)Dc + dcf) * (1.0f / 256.0f);
     AffSums s;
-    if constexpr (VAR >= 2) {
+    if constexpr (VAR == 4) {
+        star_table_st(c, ec, TWR, Dc, T, g.dirs, g.steps, s);
+    } else if constexpr (VAR >= 2) {
         static_assert(R == 10, "the M = 8, s = 10 star needs a halo of 10");
         star8<10, kTW + 2 * R>(c, Dc, __int_as_float(cc.y), make_thr(g, Dc), s);
     } else if constexpr (VAR == 1) {
@@ -443,18 +475,21 @@ static_assert(learned_layout(0).q - learned_layout(0).feat >= sizeof(int) * 10 *
 static_assert(4 * kH1Ld * 16 * kH1Tiles >= sizeof(float) * kQH * kTW, "row minima of q");
 
 // VAR: 0 fixed window, 1 star table, 2 compile-time M = 8, s = 10 star,
-// 3 = 2 with the learned gate.  R: halo radius at compile time (0 = runtime).
+// 3 = 2 with the learned gate, 4 star table with the ST stop.  R: halo
+// radius at compile time (0 = runtime).
 // RD: denoise radius (0 = runtime).
 template <int IN, int VAR, int R, int RD>
 __global__ void __launch_bounds__(kThreads, 2)
     k_frame(const Geo g, const __grid_constant__ StarTable T, const char* __restrict__ disp, size_t dp,
             const FrameOut o, const GateView gv) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : g.steps);
+    // ST needs the edge bit of every pixel a ray can reach: one more halo row
+    const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : (VAR == 4 ? g.steps + 1 : g.steps));
     const int TWR = kTW + 2 * Rr, THR = kTH + 2 * Rr;
     int2* tile = reinterpret_cast<int2*>(smem);
     int* Ls = reinterpret_cast<int*>(smem + sizeof(int2) * (size_t)TWR * THR);  // union-find parents
     unsigned* Lrow = reinterpret_cast<unsigned*>(Ls + kThreads);                  // left-edge mask per row
+    uint8_t* Est = reinterpret_cast<uint8_t*>(Lrow + kTH);                        // ST edge bytes (VAR 4)
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
     const int tid = threadIdx.y * kTW + threadIdx.x;
     if (o.count && (blockIdx.x | blockIdx.y | tid) == 0) *o.count = 0;
@@ -469,6 +504,16 @@ __global__ void __launch_bounds__(kThreads, 2)
         tile[i] = make_int2(D, __float_as_int(w));
     }
     __syncthreads();
+    if constexpr (VAR == 4) {
+        for (int i = tid; i < n; i += kThreads) {
+            const int ly = i / TWR, lx = i - ly * TWR;
+            bool e = true;  // the outer ring is never reached by a ray
+            if (lx > 0 && lx < TWR - 1 && ly > 0 && ly < THR - 1)
+                e = st_edge(g, tile[i].x, tile[i - 1].x, tile[i + 1].x, tile[i - TWR].x, tile[i + TWR].x);
+            Est[i] = e;
+        }
+        __syncthreads();
+    }
 
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const bool inside = x < g.W && y < g.H;
@@ -491,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     if constexpr (VAR != 3) {
         if (inside) {
             PixOut r;
-            plain_pixel<VAR, R, RD>(g, T, c, TWR, x, y, r);
+            plain_pixel<VAR, R, RD>(g, T, c, TWR, x, y, r, Est + (c - tile));
             emit(g, o, x, y, r);
         }
     } else {
@@ -742,8 +787,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 }
 
-__host__ __device__ constexpr size_t frame_smem(int Rr) {
-    return sizeof(int2) * (size_t)(kTW + 2 * Rr) * (kTH + 2 * Rr) + sizeof(int) * (kThreads + kTH);
+// tile (D, 1/D), union-find parents, row masks (+ one ST edge byte per tile entry)
+__host__ __device__ constexpr size_t frame_smem(int Rr, bool st = false) {
+    return sizeof(int2) * (size_t)(kTW + 2 * Rr) * (kTH + 2 * Rr) + sizeof(int) * (kThreads + kTH) +
+           (st ? (size_t)(kTW + 2 * Rr) * (kTH + 2 * Rr) : 0);
 }
 
 // Raises a kernel's dynamic shared-memory limit once per device, to the most
@@ -765,10 +812,10 @@ cudaError_t smem_limit_once(Kernel k, size_t bytes, std::atomic<unsigned long lo
 template <int IN, int VAR, int R, int RD>
 cudaError_t launch_in(const Geo& g, const StarTable& t, const char* d, size_t dp, const FrameOut& o,
                       const GateView& gv, cudaStream_t s) {
-    constexpr int Rmax = R > 0 ? R : (VAR == 0 ? 15 : kMaxSteps);
-    const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : g.steps);
-    const size_t bytes = VAR == 3 ? learned_layout(frame_smem(R)).end : frame_smem(Rr);
-    const size_t bytes_max = VAR == 3 ? learned_layout(frame_smem(R)).end : frame_smem(Rmax);
+    constexpr int Rmax = R > 0 ? R : (VAR == 0 ? 15 : (VAR == 4 ? kMaxSteps + 1 : kMaxSteps));
+    const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : (VAR == 4 ? g.steps + 1 : g.steps));
+    const size_t bytes = VAR == 3 ? learned_layout(frame_smem(R)).end : frame_smem(Rr, VAR == 4);
+    const size_t bytes_max = VAR == 3 ? learned_layout(frame_smem(R)).end : frame_smem(Rmax, VAR == 4);
     const dim3 grid((g.W + kTW - 1) / kTW, (g.H + kTH - 1) / kTH), block(kTW, kTH);
     static std::atomic<unsigned long long> done{0};
     const cudaError_t e = smem_limit_once(k_frame<IN, VAR, R, RD>, bytes_max, done);
@@ -820,6 +867,8 @@ cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const voi
                        : launch_var<2, 10, 0>(g, t, disp, dp, o, none, s);
     else if (g.support == SN_SUPPORT_STARFILL_CD)
         e = launch_var<1, 0, 0>(g, t, disp, dp, o, none, s);
+    else if (g.support == SN_SUPPORT_STARFILL_ST)
+        e = launch_var<4, 0, 0>(g, t, disp, dp, o, none, s);
     else
         e = launch_var<0, 0, 0>(g, t, disp, dp, o, none, s);
     mk.after(s);

@@ -33,6 +33,9 @@ struct Geo {
     float fx, fy, cx, cy, B;
     float fy_over_fx, inv_fx, B_fx_over_fy, fxB;
     double dfx, dfy, dcx, dcy, dB;
+    // ST stop: depth z = st_F / D (metres); edge iff |Laplacian of z| > st_t
+    double st_F, st_t;
+    float st_Ff, st_tf;
     int* err;  // device error word
 };
 

@@ -42,11 +42,23 @@ __global__ void __launch_bounds__(kTW* kTH)
              size_t dp, const float* __restrict__ den, size_t denp, char* __restrict__ nrm,
              size_t np, uint8_t* __restrict__ mask, size_t mp, int mask_or) {
     extern __shared__ int tile[];
-    const int R = SUP == SN_SUPPORT_FIXED ? g.r_a : g.steps;
+    // ST needs the edge bit of every pixel a ray can reach: one more halo row
+    const int R = SUP == SN_SUPPORT_FIXED ? g.r_a : (SUP == SN_SUPPORT_STARFILL_ST ? g.steps + 1 : g.steps);
     const int TWR = kTW + 2 * R, THR = kTH + 2 * R;
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
     load_tile<IN>(tile, TWR, THR, disp, dp, x0 - R, y0 - R, g.W, g.H);
     __syncthreads();
+    uint8_t* E = reinterpret_cast<uint8_t*>(tile + TWR * THR);  // ST edge bytes, laid out like the tile
+    if (SUP == SN_SUPPORT_STARFILL_ST) {
+        for (int i = threadIdx.y * kTW + threadIdx.x; i < TWR * THR; i += kTW * kTH) {
+            const int ly = i / TWR, lx = i - ly * TWR;
+            bool e = true;  // the outer ring is never reached by a ray
+            if (lx > 0 && lx < TWR - 1 && ly > 0 && ly < THR - 1)
+                e = st_edge(g, tile[i], tile[i - 1], tile[i + 1], tile[i - TWR], tile[i + TWR]);
+            E[i] = e;
+        }
+        __syncthreads();
+    }
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     if (x >= g.W || y >= g.H) return;
     const int* c = tile + (threadIdx.y + R) * TWR + threadIdx.x + R;
@@ -60,6 +72,8 @@ __global__ void __launch_bounds__(kTW* kTH)
         AffSums s;
         if (SUP == SN_SUPPORT_FIXED)
             fixed_support(c, TWR, R, Dc, s);
+        else if (SUP == SN_SUPPORT_STARFILL_ST)
+            star_support_st(c, E + (c - tile), TWR, Dc, T, g.dirs, g.steps, s);
         else
             star_support(c, TWR, Dc, g.K_cd, T, g.dirs, g.steps, s);
         bool fp64;
@@ -246,6 +260,8 @@ static void affine_dispatch(const Geo& g, const StarTable& t, const char* d, siz
                             size_t smem, cudaStream_t s) {
     if (g.support == SN_SUPPORT_FIXED)
         k_affine<IN, SN_SUPPORT_FIXED><<<grid2(g), dim3(kTW, kTH), smem, s>>>(g, t, d, dp, den, denp, nrm, np, mask, mp, mor);
+    else if (g.support == SN_SUPPORT_STARFILL_ST)
+        k_affine<IN, SN_SUPPORT_STARFILL_ST><<<grid2(g), dim3(kTW, kTH), smem, s>>>(g, t, d, dp, den, denp, nrm, np, mask, mp, mor);
     else
         k_affine<IN, SN_SUPPORT_STARFILL_CD><<<grid2(g), dim3(kTW, kTH), smem, s>>>(g, t, d, dp, den, denp, nrm, np, mask, mp, mor);
 }
@@ -253,8 +269,10 @@ static void affine_dispatch(const Geo& g, const StarTable& t, const char* d, siz
 cudaError_t launch_affine(const Geo& g, const StarTable& t, const void* disp, size_t dp,
                           const float* den, size_t denp, void* nrm, size_t np, uint8_t* mask,
                           size_t mp, bool mask_or, cudaStream_t s, Marks& mk) {
-    const int R = g.support == SN_SUPPORT_FIXED ? g.r_a : g.steps;
-    const size_t smem = sizeof(int) * (kTW + 2 * R) * (kTH + 2 * R);
+    const bool st = g.support == SN_SUPPORT_STARFILL_ST;
+    const int R = g.support == SN_SUPPORT_FIXED ? g.r_a : (st ? g.steps + 1 : g.steps);
+    // tile ints (+ one edge byte per tile entry for ST); at most 33 KB (s = 30)
+    const size_t smem = (sizeof(int) + (st ? 1 : 0)) * (kTW + 2 * R) * (kTH + 2 * R);
     const char* d = static_cast<const char*>(disp);
     char* n = static_cast<char*>(nrm);
     switch (g.in_dtype) {

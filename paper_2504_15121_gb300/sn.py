@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libsn.so")
 
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_EBUSY, SN_ENOTSUP = range(7)
-SN_SUPPORT_FIXED, SN_SUPPORT_STARFILL_CD = 0, 1
+SN_SUPPORT_FIXED, SN_SUPPORT_STARFILL_CD, SN_SUPPORT_STARFILL_ST = 0, 1, 2
 SN_IN_F32, SN_IN_F16, SN_IN_U16X256 = 0, 1, 2
 SN_NORMALS_F32X3, SN_NORMALS_SNORM16X4 = 0, 1
 SN_MASK_VALID, SN_MASK_NORMAL, SN_MASK_FP64, SN_MASK_LEARNED, SN_MASK_DENOISED = 1, 2, 4, 8, 16
@@ -39,7 +39,7 @@ class sn_params(C.Structure):
     _fields_ = [("r_denoise", C.c_int), ("r_affine", C.c_int), ("support", C.c_int),
                 ("dirs", C.c_int), ("steps", C.c_int), ("k_cd", C.c_float), ("k_pair", C.c_float),
                 ("k_range", C.c_float), ("tau", C.c_float), ("in_dtype", C.c_int),
-                ("normal_fmt", C.c_int), ("learned", C.c_int)]
+                ("normal_fmt", C.c_int), ("learned", C.c_int), ("st_t", C.c_float)]
 
 
 class sn_frame_in(C.Structure):

@@ -26,7 +26,7 @@ def oracle_params(p) -> oracle.Params:
     """The oracle's parameter record for a library sn_params."""
     return oracle.Params(r_denoise=p.r_denoise, r_affine=p.r_affine, support=p.support,
                          dirs=p.dirs, steps=p.steps, k_cd=float(p.k_cd), k_pair=float(p.k_pair),
-                         k_range=float(p.k_range))
+                         k_range=float(p.k_range), st_t=float(p.st_t))
 
 
 def run_gpu(pipe, disp_np):

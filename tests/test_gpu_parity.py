@@ -68,6 +68,33 @@ def test_starfill_s30_d16_full_size(P):
     print(f"s30 d16: normals mean {mean:.2e} max {mx:.2e} deg")
 
 
+@pytest.mark.parametrize("name", ["mixed_1482x994", "driving_2048x1024"])
+def test_starfill_st_full_size(P, name):
+    # ST s10 d8 t0.1 (Table perf-disc): rays stop at depth-Laplacian edges
+    s = make_scene(name, frame=3)
+    g, ref = chain(P, s.disp, s.camera, support=2, st_t=0.1)
+    mean, mx = compare_frame(g, ref)
+    print(f"ST {name}: normals mean {mean:.2e} max {mx:.2e} deg")
+
+
+def test_st_threshold_at_the_laplacian(P):
+    # t set to the FP32-rounded |Laplacian| of chosen pixels, so that the
+    # kernel's FP32 band cannot decide there and the exact FP64 expression
+    # does; the edge bytes decide the supports, hence the normals and masks
+    rng = np.random.default_rng(21)
+    H, W = 40, 48
+    D = (9000 + 40 * np.arange(W)[None, :] + rng.integers(-60, 60, (H, W))).astype(np.int32)
+    F = 256.0 * CAM.fx * CAM.baseline
+    z = F / D.astype(np.float64)
+    for (v, u) in [(20, 24), (7, 9), (31, 40)]:
+        L = ((z[v, u - 1] + z[v, u + 1]) + (z[v - 1, u] + z[v + 1, u])) - 4.0 * z[v, u]
+        t = float(np.float32(abs(L)))
+        g, ref = chain(P, codes_to_f32(D), CAM, support=2, st_t=t)
+        compare_frame(g, ref)
+        E = oracle.st_edges(D, CAM, t)
+        assert 0 < E[1:-1, 1:-1].mean() < 1
+
+
 def test_driving_u16_and_f16_inputs(P):
     s = make_scene("driving_2048x1024", frame=1)
     for arr, dt in ((s.disp_u16, P.sn.SN_IN_U16X256), (s.disp_f16, P.sn.SN_IN_F16)):
@@ -140,6 +167,9 @@ def test_constant_and_planes(P):
     dict(support=1, dirs=16, steps=6),
     dict(support=1, dirs=4, steps=3, k_cd=0.02),
     dict(support=1, dirs=12, steps=7, k_cd=0.3),
+    dict(support=2),
+    dict(support=2, dirs=16, steps=30, st_t=0.05),
+    dict(support=2, dirs=5, steps=4, st_t=1.0),
     dict(support=0, r_affine=1),
     dict(support=0, r_affine=7),
     dict(support=0, r_affine=15),
@@ -229,10 +259,11 @@ def test_components_adversarial(P, shape):
 
 
 # ------------------------------------------------------------ stage entry points
-def test_stage_entry_points(P):
+@pytest.mark.parametrize("support", [1, 2])
+def test_stage_entry_points(P, support):
     s = make_scene("mixed_1482x994", frame=2)
     H, W = s.disp.shape
-    pipe = P.Pipeline(s.camera, W, H)
+    pipe = P.Pipeline(s.camera, W, H, support=support)
     sn = P.sn
     try:
         disp = pipe.upload(s.disp)

@@ -62,12 +62,14 @@ def test_defaults(sn):
     assert (p.r_denoise, p.r_affine, p.support, p.dirs, p.steps) == (2, 4, sn.SN_SUPPORT_STARFILL_CD, 8, 10)
     assert abs(p.k_cd - 0.1) < 1e-7 and abs(p.k_pair - 0.05) < 1e-7 and abs(p.tau - 0.9) < 1e-7
     assert (p.in_dtype, p.normal_fmt, p.learned) == (sn.SN_IN_F32, sn.SN_NORMALS_F32X3, 0)
+    assert abs(p.st_t - 0.1) < 1e-7
 
 
 @pytest.mark.parametrize("bad", [
     dict(W=0), dict(H=-1), dict(W=20000), dict(r_denoise=0), dict(r_denoise=5), dict(r_affine=16),
     dict(dirs=3), dict(dirs=17), dict(steps=31), dict(k_cd=-0.1), dict(k_pair=1.5), dict(support=7),
-    dict(in_dtype=9), dict(normal_fmt=3), dict(fx=0.0), dict(baseline=-1.0)])
+    dict(in_dtype=9), dict(normal_fmt=3), dict(fx=0.0), dict(baseline=-1.0), dict(support=3),
+    dict(support=2, st_t=-1.0), dict(support=2, st_t=float("nan"))])
 def test_create_rejects_bad_arguments(sn, bad):
     bad = dict(bad)
     W, H = bad.pop("W", 64), bad.pop("H", 48)
