@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-resolution batch")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     return ap.parse_args()
 
@@ -152,25 +153,35 @@ def make_inputs(n_distinct: int, rank: int):
 
 
 def cpu_baseline(scenes, seconds: float):
-    """The FP64 oracle as it stands, all host cores, on whole frames of the
-    same workload until `seconds` of CPU work have been spent."""
+    """The FP64 oracle as it stands on whole frames of the same workload: on
+    all host cores until `seconds` of work have been spent, then on one core
+    for a quarter of that (a bounded sample of whole frames)."""
     import oracle
     cores = os.cpu_count() or 1
-    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+
+    def timed(threads, budget):
+        used = oracle.set_threads(threads)
+        px, n = 0, 0
+        t0 = time.perf_counter()
+        while True:
+            s = scenes[n % len(scenes)]
+            oracle.run_frame(s.disp, s.camera)
+            px += s.W * s.H
+            n += 1
+            if time.perf_counter() - t0 >= budget:
+                break
+        dt = time.perf_counter() - t0
+        return px / dt / 1e6, used, n, dt
+
     oracle.build()
-    px, n = 0, 0
-    t0 = time.perf_counter()
-    while True:
-        s = scenes[n % len(scenes)]
-        oracle.run_frame(s.disp, s.camera)
-        px += s.W * s.H
-        n += 1
-        if time.perf_counter() - t0 >= seconds:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": px / dt / 1e6, "unit": "MPix/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
-            "kind": "oracle",
-            "sample": f"{n} whole {WORKLOAD} frames (FP32 input, full chain), {dt:.1f} s"}
+    v, used, n, dt = timed(cores, seconds)
+    v1, _, n1, dt1 = timed(1, seconds / 4)
+    oracle.set_threads(cores)
+    return {"value": v, "unit": "MPix/s", "cores": used, "kind": "oracle",
+            "sample": f"{n} whole {WORKLOAD} frames (FP32 input, full chain), {dt:.1f} s",
+            "single_thread": {"value": v1, "unit": "MPix/s", "cores": 1,
+                              "sample": f"{n1} whole frames, {dt1:.1f} s"},
+            "host": f"{cores} cores, {os.uname().machine}"}
 
 
 # ---------------------------------------------------------------- reference arm
@@ -315,6 +326,8 @@ def run_ours(args):
     # the comparison estimators of Sec. IV on the same scenes (normals only)
     comparators = {"cross": time_comparator(scenes, args, "cross", 0, world),
                    "pca_9x9": time_comparator(scenes, args, "pca", 4, world)}
+    # mixed-resolution batch of 64 frames, one graph launch per step
+    mixed = run_mixed_batch(args) if world == 1 and not args.no_mixed else None
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
@@ -365,6 +378,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "forms": forms,
             "comparators": comparators,
+            "mixed_batch": mixed,
             "clocks": clk,
             "e2e": e2e,
             "serving": serving,
@@ -513,6 +527,80 @@ def time_comparator(scenes, args, which, r, world):
         sn.sn_destroy(ctx)
     return {"value": world * steps * F * s0.W * s0.H / (ms / 1e3) / 1e6, "unit": "MPix/s",
             "what": "normals + mask only", "gt_error_deg": gt}
+
+
+MIXED_SIZES = ("planes_320x240", "planes_640x480", "mixed_1482x994", "driving_2048x1024")
+
+
+def run_mixed_batch(args, seed=0):
+    """64 frames, 16 of each size (4 distinct seeded scenes per size, each
+    used 4 times) in seeded shuffled order: the plain and the learned chain,
+    each whole batch captured as one CUDA graph (one launch per step, the
+    frames spread over the graph's streams).  MPix/s over the 63,268,160
+    pixels of a step and the mean angular error against ground truth."""
+    import torch
+    from scenes import make_scene
+    from paper_2504_15121_gb300 import Pipeline
+    rng = np.random.default_rng([4, seed])
+    scenes = {n: [make_scene(n, frame=100 + i) for i in range(4)] for n in MIXED_SIZES}
+    order = [(n, i % 4) for n in MIXED_SIZES for i in range(16)]
+    order = [order[k] for k in rng.permutation(len(order))]
+    px = sum(scenes[n][0].W * scenes[n][0].H for n, _ in order)
+    out = {"frames": len(order), "pixels_per_step": int(px),
+           "order": "seeded shuffle of 16 frames of each of " + ", ".join(MIXED_SIZES)}
+    for form, params in (("plain_f32", {}), ("learned_f32", dict(learned=1))):
+        pipes = {n: Pipeline(scenes[n][0].camera, scenes[n][0].W, scenes[n][0].H, **params) for n in MIXED_SIZES}
+        try:
+            disp = {n: [pipes[n].upload(sc.disp) for sc in scenes[n]] for n in MIXED_SIZES}
+            bufs = [pipes[n].buffers() for n, _ in order]
+            main = torch.cuda.current_stream()
+            streams = [torch.cuda.Stream() for _ in range(args.streams)]
+
+            def step():
+                cur = torch.cuda.current_stream()
+                ev = cur.record_event()
+                for st in streams:
+                    st.wait_event(ev)
+                for k, (n, i) in enumerate(order):
+                    pipes[n].run_frame(disp[n][i], bufs[k], stream=streams[k % len(streams)], write_den=False)
+                for st in streams:
+                    cur.wait_stream(st)
+            for _ in range(args.warmup):
+                step()
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            cap = torch.cuda.Stream()
+            with torch.cuda.stream(cap):
+                graph.capture_begin()
+                step()
+                graph.capture_end()
+            torch.cuda.synchronize()
+            for _ in range(2):
+                graph.replay()
+            torch.cuda.synchronize()
+            steps = max(3, args.steps // 4)
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(main)
+            for _ in range(steps):
+                graph.replay()
+            t1.record(main)
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1)
+            errs = []
+            for k, (n, i) in enumerate(order):
+                e = gt_error_deg([bufs[k]], [scenes[n][i]])
+                errs.append((e["mean"], e["pixels"], e["certified"]))
+            npx = sum(p for _, p, _ in errs)
+            out[form] = {"value": steps * px / (ms / 1e3) / 1e6, "unit": "MPix/s", "ms_per_step": ms / steps,
+                         "graph_launches_per_step": 1,
+                         "gt_error_deg": sum(m * p for m, p, _ in errs) / max(npx, 1),
+                         "certified": float(np.mean([c for _, _, c in errs]))}
+            del graph
+        finally:
+            for pp in pipes.values():
+                pp.close()
+    out["learned_vs_plain"] = out["learned_f32"]["value"] / out["plain_f32"]["value"]
+    return out
 
 
 def gt_error_deg(outs, scenes):

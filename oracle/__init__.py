@@ -81,6 +81,8 @@ def lib():
         L.orc_ingest.restype = C.c_int
         L.orc_learned_radius.argtypes = []
         L.orc_learned_radius.restype = C.c_int
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_set_threads.restype = C.c_int
         L.orc_denoise.argtypes = [p, C.c_int, C.c_int, C.POINTER(_Params), p, p]
         L.orc_star_offsets.argtypes = [C.c_int, C.c_int, p, p]
         L.orc_star_offsets.restype = C.c_int
@@ -215,6 +217,12 @@ class Frame:
     labels: np.ndarray
     mask: np.ndarray
     n_components: int
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops (n <= 0: unchanged); returns
+    the count in effect."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def learned_radius() -> int:

@@ -45,6 +45,7 @@
  * back to the raw centre value; no passage of the paper fixes it.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -66,6 +67,15 @@ enum {
 #define ORC_LEARNED_RADIUS 6
 
 int orc_learned_radius(void) { return ORC_LEARNED_RADIUS; }
+
+/* Host threads of the OpenMP loops (for timing the oracle single-threaded
+ * and on all cores); returns the count in effect. */
+int orc_set_threads(int n)
+{
+    if (n > 0)
+        omp_set_num_threads(n);
+    return omp_get_max_threads();
+}
 
 typedef struct {
     double fx, fy, cx, cy, baseline;
