@@ -84,3 +84,29 @@ def test_learned_needs_weights_and_default_star(P):
             sn.sn_load_gate_weights(ctx, b"SNGW" + bytes(20))
     finally:
         sn.sn_destroy(ctx)
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (7, 5), (17, 33), (40, 129), (70, 45)])
+def test_learned_ragged(P, H, W):
+    # frames smaller than, and not multiples of, the 32x16 tile: gate
+    # decisions and the gated chain still match the oracle
+    from paper_2504_15121_gb300 import gate as G
+    from scenes import Camera
+    theta = G.load_weights().astype(np.float64)
+    rng = np.random.default_rng(H * 131 + W)
+    base = rng.integers(6000, 6400, (H, W))
+    blocks = rng.integers(0, 2, (H // 8 + 1, W // 8 + 1)).repeat(8, 0).repeat(8, 1)[:H, :W]
+    D = (base * (1 + 0.3 * blocks)).astype(np.int32)
+    D[rng.random((H, W)) < 0.05] = 0
+    disp = (D / 256.0).astype(np.float32)
+    cam = Camera(300.0, 300.0, W / 2, H / 2, 0.1)
+    pipe = P.Pipeline(cam, W, H, learned=1)
+    try:
+        g = run_gpu(pipe, disp)
+    finally:
+        pipe.close()
+    gpu_gate = (g["mask"] & oracle.M_LEARNED) > 0
+    og, q, qmin = ogate.gate_image(D, theta, TAU, oracle.learned_radius())
+    clear = np.abs(qmin - TAU) >= 5e-3
+    assert not ((gpu_gate != og) & clear).any()
+    compare_frame(g, oracle.run_frame(disp, cam, gate=gpu_gate))

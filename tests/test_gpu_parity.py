@@ -127,7 +127,7 @@ def test_snorm16_output(P):
 
 # ------------------------------------------------------------ tiny and ragged
 @pytest.mark.parametrize("H,W", [(1, 1), (1, 7), (7, 1), (5, 7), (17, 33), (40, 65), (9, 129)])
-@pytest.mark.parametrize("support", [1, 0])
+@pytest.mark.parametrize("support", [1, 0, 2])
 def test_ragged_random(P, H, W, support):
     rng = np.random.default_rng(H * 1000 + W)
     base = rng.integers(4000, 4400, (H, W))
