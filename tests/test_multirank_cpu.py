@@ -1,0 +1,74 @@
+"""Multi-rank host logic of bench.py on CPU: two gloo ranks, as torchrun
+launches them for --gpus 2 (replicas only: frames are independent, so the
+only cross-rank traffic is the barrier and the max-over-ranks time).
+
+* the job time is the slowest rank's, on every rank;
+* whole-job throughput counts every rank's pixels over that time;
+* replicas render disjoint seeded frames;
+* the reference arm does its work on rank 0 only.
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import sys
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        ms = bench.max_over_ranks(10.0 + 3.0 * rank, dist)      # rank 1 is slower
+        value = bench.whole_job_mpix(world, 1000000, ms)
+        scenes = bench.make_inputs(1, rank)
+        dist.barrier()
+        q.put((rank, ms, value, float(np.asarray(scenes[0].disp, np.float64).sum())))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, ms0, v0, s0), (r1, ms1, v1, s1) = out
+    assert ms0 == ms1 == 13.0                       # the slowest rank's time everywhere
+    assert v0 == v1 == pytest.approx(2 * 1e6 / 0.013 / 1e6)
+    assert s0 != s1                                 # disjoint frames
+
+
+def test_single_process_has_no_reduction():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(7.5, None) == 7.5
+    assert bench.whole_job_mpix(1, 2_097_152, 1000.0) == pytest.approx(2.097152)
+
+
+def test_reference_arm_other_ranks_do_nothing(monkeypatch):
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    args = bench.argparse.Namespace(steps=1, warmup=0, gpus=2)
+    assert bench.run_reference(args) is None        # returns at once: no oracle work
