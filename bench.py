@@ -670,7 +670,8 @@ def run_serving(args):
         srv = serve.Server(cams, memory_budget=6 << 30, max_slots_per_camera=6, n_streams=4, queue_depth=256)
         try:
             res = {"x1": srv.simulate(pools, duration_s=args.serve_seconds, rate_scale=1.0, seed=1)}
-            for k in (8, 24):
+            # rate sweep: x48 offers more than the device sustains (saturation)
+            for k in (8, 24, 48):
                 res[f"x{k}"] = srv.simulate(pools, duration_s=1.0, rate_scale=float(k), seed=k)
             srv.check()
         finally:
@@ -679,7 +680,7 @@ def run_serving(args):
                      for k, v in res.items()}
     out["how"] = ("8 cameras: 2x 640x480 @120 Hz, 4x 1482x994 @30 Hz, 2x 2048x1024 @30 Hz; Poisson "
                   "arrivals; latency = arrival (pinned host frame) -> outputs ready on device; "
-                  "x8/x24 = every camera's rate multiplied")
+                  "x8/x24/x48 = every camera's rate multiplied (x48 saturates)")
     return out
 
 

@@ -269,6 +269,16 @@ sn_status sn_load_gate_weights(sn_ctx *ctx, const void *blob, size_t bytes);
  * range. */
 int sn_star_offsets(int dirs, int steps, int8_t *ou, int8_t *ov);
 
+/* Fault-detection hook (for tests): bounds every union-find walk of the
+ * component passes (k_ccl_merge, k_ccl_flatten) of this context to `steps`
+ * parent steps; steps <= 0 restores the default 4194304, more than any chain
+ * of a 16384 x 16384 frame.  A walk that runs out stops there and sets the
+ * device error word: sn_check_device then returns SN_ETIMEOUT and that
+ * frame's labels and component count are undefined; the context stays
+ * usable.  Takes effect for calls enqueued after it (not for graphs already
+ * captured). */
+sn_status sn_set_walk_limit(sn_ctx *ctx, int steps);
+
 /* Reads and clears the context's device error word (synchronous on the
  * context's internal stream only after `stream` completes).  Returns SN_OK,
  * or SN_ETIMEOUT if a bounded device wait gave up since the last call. */

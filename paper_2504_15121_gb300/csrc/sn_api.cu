@@ -191,6 +191,7 @@ sn_status prepare_constants(const sn_camera* cam, int W, int H, const sn_params*
     g->dcy = cam->cy;
     g->dB = cam->baseline;
     set_st(*g, cam, p->st_t);
+    g->walk_limit = kWalkLimitDefault;
     return SN_OK;
 }
 
@@ -307,6 +308,7 @@ sn_status sn_create(const sn_camera* cam, int W, int H, const sn_params* pin, sn
     g.dcy = cam->cy;
     g.dB = cam->baseline;
     sn::set_st(g, cam, p.st_t);
+    g.walk_limit = sn::kWalkLimitDefault;
 
     cudaError_t e = cudaMalloc(&c->ws.err, 2 * sizeof(int));
     if (e == cudaSuccess) {
@@ -474,6 +476,12 @@ sn_status sn_run_frame(sn_ctx* c, const sn_frame_in* in, sn_frame_out* out, sn_s
                                      c->p.learned ? &gv : nullptr, stream, mk);
     c->launches += mk.launches;
     return e == cudaSuccess ? SN_OK : cuda_fail(c, e, "sn_run_frame");
+}
+
+sn_status sn_set_walk_limit(sn_ctx* c, int steps) {
+    if (!c) return SN_EINVAL;
+    c->geo.walk_limit = steps > 0 ? steps : sn::kWalkLimitDefault;
+    return SN_OK;
 }
 
 sn_status sn_load_gate_weights(sn_ctx* c, const void* blob, size_t bytes) {

@@ -384,8 +384,10 @@ struct LabelIndex {
     }
 };
 
-__device__ __forceinline__ int find_g(const int* L, const LabelIndex& li, int x, int* err) {
-    for (int it = 0; it < kFindLimit; it++) {
+// limit: parent steps a walk may take (a context setting, default
+// kFindLimit); a walk that runs out sets kErrFindLimit and returns where it is.
+__device__ __forceinline__ int find_g(const int* L, const LabelIndex& li, int x, int* err, int limit) {
+    for (int it = 0; it < limit; it++) {
         const int p = __ldcg(L + li.addr(x));
         if (p == x) return x;
         x = p;
@@ -396,8 +398,8 @@ __device__ __forceinline__ int find_g(const int* L, const LabelIndex& li, int x,
 
 // Root of x with path halving: every node passed is re-pointed at its
 // grandparent (an ancestor, so concurrent unions stay correct).
-__device__ __forceinline__ int find_halve(int* L, const LabelIndex& li, int x, int* err) {
-    for (int it = 0; it < kFindLimit; it++) {
+__device__ __forceinline__ int find_halve(int* L, const LabelIndex& li, int x, int* err, int limit) {
+    for (int it = 0; it < limit; it++) {
         const int p = __ldcg(L + li.addr(x));
         if (p == x) return x;
         const int gp = __ldcg(L + li.addr(p));
@@ -411,10 +413,10 @@ __device__ __forceinline__ int find_halve(int* L, const LabelIndex& li, int x, i
 
 // Lock-free union: the larger root is linked to the smaller by atomicMin;
 // a lost race retries from the value found.
-__device__ __forceinline__ void union_g(int* L, const LabelIndex& li, int a, int b, int* err) {
+__device__ __forceinline__ void union_g(int* L, const LabelIndex& li, int a, int b, int* err, int limit) {
     for (int it = 0; it < kUnionLimit; it++) {
-        a = find_halve(L, li, a, err);
-        b = find_halve(L, li, b, err);
+        a = find_halve(L, li, a, err, limit);
+        b = find_halve(L, li, b, err, limit);
         if (a == b) return;
         if (a < b) {
             const int t = a;

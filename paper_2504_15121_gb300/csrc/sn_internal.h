@@ -18,6 +18,7 @@ constexpr int kCclTile = 32;        // CCL tiles are 32 x 32 pixels
 
 // error bits written to the context's device error word
 constexpr int kErrFindLimit = 1;    // a union-find walk exceeded its bound
+constexpr int kWalkLimitDefault = 1 << 22;  // > any parent chain of a 16384^2 frame
 constexpr int kErrUnionLimit = 2;   // a union retry loop exceeded its bound
 constexpr int kErrBarrier = 4;      // a grid barrier wait exceeded its bound
 
@@ -36,7 +37,8 @@ struct Geo {
     // ST stop: depth z = st_F / D (metres); edge iff |Laplacian of z| > st_t
     double st_F, st_t;
     float st_Ff, st_tf;
-    int* err;  // device error word
+    int walk_limit;  // parent steps of one union-find walk in the component passes
+    int* err;        // device error word
 };
 
 // Star-fill table.  cls: 0 = repeats the previous step of its ray (never

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(256)
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     if (act && lp != lq && (int)(__ffs(peers) - 1) == lane) {
         const LabelIndex li{g.W, lpe};
-        union_g(labels, li, lp, lq, g.err);
+        union_g(labels, li, lp, lq, g.err, g.walk_limit);
     }
 }
 
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kTW * kTH / kFlatPix)
     for (int i = 0; i < kFlatPix; i++) {
         if (l[i] < 0) continue;
         const int y = y0 + i * kStep;
-        const int r = l[i] == prev_l ? prev_r : find_g(labels, li, l[i], g.err);
+        const int r = l[i] == prev_l ? prev_r : find_g(labels, li, l[i], g.err, g.walk_limit);
         prev_l = l[i];
         prev_r = r;
         if (r != l[i]) __stcg(labels + (size_t)y * lpe + x, r);

@@ -82,6 +82,7 @@ def _load():
         "sn_load_gate_weights": ([vp, vp, sz], i),
         "sn_star_offsets": ([i, i, vp, vp], i),
         "sn_check_device": ([vp, vp], i),
+        "sn_set_walk_limit": ([vp, i], i),
         "sn_status_string": ([i], C.c_char_p),
         "sn_last_error": ([vp], C.c_char_p),
         "sn_set_profiling": ([vp, i], i),
@@ -107,7 +108,7 @@ EXPORTS = ("sn_version", "sn_default_params", "sn_create", "sn_destroy", "sn_den
            "sn_load_gate_weights", "sn_star_offsets", "sn_check_device", "sn_status_string",
            "sn_last_error", "sn_set_profiling", "sn_stage_count", "sn_stage_name",
            "sn_stage_times", "sn_launch_count", "sn_normals_noalloc", "sn_cross_normals",
-           "sn_pca_normals")
+           "sn_pca_normals", "sn_set_walk_limit")
 
 
 # ---------------------------------------------------------------- helpers
@@ -257,6 +258,10 @@ def sn_run_frame(ctx, disp, normals, points, labels, mask, den=None, num_compone
     fo.mask = m
     fo.num_components = C.c_void_p(num_components.data_ptr()) if num_components is not None else None
     _check(ctx, lib.sn_run_frame(ctx, C.byref(fi), C.byref(fo), _stream(stream)))
+
+
+def sn_set_walk_limit(ctx, steps: int):
+    _check(ctx, lib.sn_set_walk_limit(ctx, int(steps)))
 
 
 def sn_check_device(ctx, stream=None):

@@ -335,3 +335,32 @@ def test_argument_errors_on_device(P):
         torch.cuda.synchronize()
     finally:
         pipe.close()
+
+
+def test_walk_limit_reports_timeout_and_context_recovers(P):
+    # fault detection without a fault: a union-find walk bound of one step
+    # cannot resolve the spiral's chains across tiles; the component passes
+    # stop, the error word is set and sn_check_device reports SN_ETIMEOUT;
+    # with the default bound the same context labels the frame correctly
+    sn = P.sn
+    D = spiral(150)
+    disp = codes_to_f32(D)
+    cam = Camera(300.0, 300.0, 75.0, 75.0, 0.1)
+    pipe = P.Pipeline(cam, 150, 150)
+    try:
+        d = pipe.upload(disp)
+        out = pipe.buffers()
+        sn.sn_set_walk_limit(pipe.ctx, 1)
+        pipe.run_frame(d, out)
+        torch.cuda.synchronize()
+        with pytest.raises(sn.SnError) as ei:
+            sn.sn_check_device(pipe.ctx)
+        assert ei.value.status == sn.SN_ETIMEOUT
+        sn.sn_set_walk_limit(pipe.ctx, 0)
+        pipe.run_frame(d, out)
+        torch.cuda.synchronize()
+        sn.sn_check_device(pipe.ctx)
+        g = to_host(out)
+    finally:
+        pipe.close()
+    compare_frame(g, oracle.run_frame(disp, cam))
