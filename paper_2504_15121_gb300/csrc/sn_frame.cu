@@ -16,6 +16,13 @@ namespace sn {
 namespace {
 
 constexpr int kTW = kFrameTW, kTH = kFrameTH, kThreads = kTW * kTH;
+// Tile height of each variant.  The compile-time M = 8, s = 10 star takes
+// 32 x 8 tiles, 4 CTAs of 256 threads per SM (more independent CTAs hide the
+// barrier and staging stalls better than 2 CTAs of 512: 130 vs 139 us per
+// 2048x1024 frame); the variants with larger halos (star tables up to s = 30,
+// ST) and the learned one (whose network halo is amortised over more pixels)
+// keep 32 x 16.
+__host__ __device__ constexpr int frame_th(int var) { return var == 2 ? 8 : kTH; }
 
 // distinct pixels of an M = 8 diagonal ray of s steps: round(s / sqrt 2),
 // i.e. the r with (2r - 1)^2 < 2 s^2 < (2r + 1)^2
@@ -479,24 +486,26 @@ static_assert(4 * kH1Ld * 16 * kH1Tiles >= sizeof(float) * kQH * kTW, "row minim
 // radius at compile time (0 = runtime).
 // RD: denoise radius (0 = runtime).
 template <int IN, int VAR, int R, int RD>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR)))
     k_frame(const Geo g, const __grid_constant__ StarTable T, const char* __restrict__ disp, size_t dp,
             const FrameOut o, const GateView gv) {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int TH = frame_th(VAR), NT = kTW * TH;
+    static_assert(VAR != 3 || TH == kTH, "the learned layout is laid out for kTH-row tiles");
     // ST needs the edge bit of every pixel a ray can reach: one more halo row
     const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : (VAR == 4 ? g.steps + 1 : g.steps));
-    const int TWR = kTW + 2 * Rr, THR = kTH + 2 * Rr;
+    const int TWR = kTW + 2 * Rr, THR = TH + 2 * Rr;
     int2* tile = reinterpret_cast<int2*>(smem);
     int* Ls = reinterpret_cast<int*>(smem + sizeof(int2) * (size_t)TWR * THR);  // union-find parents
-    unsigned* Lrow = reinterpret_cast<unsigned*>(Ls + kThreads);                  // left-edge mask per row
-    uint8_t* Est = reinterpret_cast<uint8_t*>(Lrow + kTH);                        // ST edge bytes (VAR 4)
-    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+    unsigned* Lrow = reinterpret_cast<unsigned*>(Ls + NT);                        // left-edge mask per row
+    uint8_t* Est = reinterpret_cast<uint8_t*>(Lrow + TH);                         // ST edge bytes (VAR 4)
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * TH;
     const int tid = threadIdx.y * kTW + threadIdx.x;
     if (o.count && (blockIdx.x | blockIdx.y | tid) == 0) *o.count = 0;
 
     // ---- stage the tile and its halo: (D, 1/D)
     const int n = TWR * THR;
-    for (int i = tid; i < n; i += kThreads) {
+    for (int i = tid; i < n; i += NT) {
         const int ly = i / TWR;
         const int lx = i - ly * TWR;
         const int D = load_code<IN>(disp, dp, x0 - Rr + lx, y0 - Rr + ly, g.W, g.H);
@@ -505,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     __syncthreads();
     if constexpr (VAR == 4) {
-        for (int i = tid; i < n; i += kThreads) {
+        for (int i = tid; i < n; i += NT) {
             const int ly = i / TWR, lx = i - ly * TWR;
             bool e = true;  // the outer ring is never reached by a ray
             if (lx > 0 && lx < TWR - 1 && ly > 0 && ly < THR - 1)
@@ -787,10 +796,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 }
 
-// tile (D, 1/D), union-find parents, row masks (+ one ST edge byte per tile entry)
-__host__ __device__ constexpr size_t frame_smem(int Rr, bool st = false) {
-    return sizeof(int2) * (size_t)(kTW + 2 * Rr) * (kTH + 2 * Rr) + sizeof(int) * (kThreads + kTH) +
-           (st ? (size_t)(kTW + 2 * Rr) * (kTH + 2 * Rr) : 0);
+// tile (D, 1/D), union-find parents, row masks (+ one ST edge byte per tile
+// entry) of a 32 x TH tile
+__host__ __device__ constexpr size_t frame_smem(int Rr, bool st = false, int TH = kTH) {
+    return sizeof(int2) * (size_t)(kTW + 2 * Rr) * (TH + 2 * Rr) + sizeof(int) * (kTW * TH + TH) +
+           (st ? (size_t)(kTW + 2 * Rr) * (TH + 2 * Rr) : 0);
 }
 
 // Raises a kernel's dynamic shared-memory limit once per device, to the most
@@ -814,9 +824,10 @@ cudaError_t launch_in(const Geo& g, const StarTable& t, const char* d, size_t dp
                       const GateView& gv, cudaStream_t s) {
     constexpr int Rmax = R > 0 ? R : (VAR == 0 ? 15 : (VAR == 4 ? kMaxSteps + 1 : kMaxSteps));
     const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : (VAR == 4 ? g.steps + 1 : g.steps));
-    const size_t bytes = VAR == 3 ? learned_layout(frame_smem(R)).end : frame_smem(Rr, VAR == 4);
-    const size_t bytes_max = VAR == 3 ? learned_layout(frame_smem(R)).end : frame_smem(Rmax, VAR == 4);
-    const dim3 grid((g.W + kTW - 1) / kTW, (g.H + kTH - 1) / kTH), block(kTW, kTH);
+    constexpr int TH = frame_th(VAR);
+    const size_t bytes = VAR == 3 ? learned_layout(frame_smem(R)).end : frame_smem(Rr, VAR == 4, TH);
+    const size_t bytes_max = VAR == 3 ? learned_layout(frame_smem(R)).end : frame_smem(Rmax, VAR == 4, TH);
+    const dim3 grid((g.W + kTW - 1) / kTW, (g.H + TH - 1) / TH), block(kTW, TH);
     static std::atomic<unsigned long long> done{0};
     const cudaError_t e = smem_limit_once(k_frame<IN, VAR, R, RD>, bytes_max, done);
     if (e != cudaSuccess) return e;
@@ -860,7 +871,8 @@ cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const voi
                          const FrameOut& o, const GateView* gv, cudaStream_t s, Marks& mk) {
     cudaError_t e;
     const GateView none{};
-    if (gv && star8 && g.r_d == 2)
+    const bool learned = gv && star8 && g.r_d == 2;
+    if (learned)
         e = launch_var<3, 10, 2>(g, t, disp, dp, o, *gv, s);
     else if (g.support == SN_SUPPORT_STARFILL_CD && star8)
         e = g.r_d == 2 ? launch_var<2, 10, 2>(g, t, disp, dp, o, none, s)
@@ -873,7 +885,8 @@ cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const voi
         e = launch_var<0, 0, 0>(g, t, disp, dp, o, none, s);
     mk.after(s);
     if (e != cudaSuccess) return e;
-    return launch_ccl_merge_flatten(g, disp, dp, o.labels, o.lp, o.count, kTW, kTH, s, mk);
+    const bool m8 = !learned && g.support == SN_SUPPORT_STARFILL_CD && star8;
+    return launch_ccl_merge_flatten(g, disp, dp, o.labels, o.lp, o.count, kTW, m8 ? frame_th(2) : kTH, s, mk);
 }
 
 }  // namespace sn
