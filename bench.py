@@ -480,7 +480,7 @@ def time_form(scenes, args, params, pick, bytes_per_px, dist, world):
             "frame_ms_p99": fm[min(len(fm) - 1, int(0.99 * (len(fm) - 1) + 0.5))] if fm else None,
             "algo_bytes_per_px": bytes_per_px,
             "gt_error_deg": gt,
-            "params": {k: int(v) for k, v in params.items()}}
+            "params": {k: (v if isinstance(v, float) else int(v)) for k, v in params.items()}}
 
 
 def time_comparator(scenes, args, which, r, world):
