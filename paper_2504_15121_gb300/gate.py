@@ -194,7 +194,7 @@ def one_surface_labels(d_true: np.ndarray, D: np.ndarray) -> np.ndarray:
 
 
 def _scene_samples(args):
-    name, scale, frame, per_class, seed = args
+    name, scale, frame, per_class, seed, pos_ratio = args
     from scenes import make_scene
     s = make_scene(name, frame=frame, scale=scale, seed=seed)
     D = codes(s.disp)
@@ -205,7 +205,7 @@ def _scene_samples(args):
     pos = np.flatnonzero(lab.ravel())
     neg = np.flatnonzero((~lab).ravel())
     take = []
-    for idx, n in ((pos, per_class), (neg, per_class)):
+    for idx, n in ((pos, int(round(per_class * pos_ratio))), (neg, per_class)):
         if idx.size:
             take.append(rng.choice(idx, size=min(n, idx.size), replace=False))
     sel = np.concatenate(take) if take else np.zeros(0, int)
@@ -215,14 +215,15 @@ def _scene_samples(args):
     return patches.astype(np.int32), lab.ravel()[sel].astype(np.float32)
 
 
-def make_training_set(n_scenes=2000, per_class=256, seed=0, workers=None):
-    """Balanced patches from n_scenes seeded scenes (all recipes, reduced
-    sizes).  Uses a spawn-started process pool (safe after CUDA init)."""
+def make_training_set(n_scenes=2000, per_class=256, seed=0, workers=None, pos_ratio=1.0):
+    """Patches from n_scenes seeded scenes (all recipes, reduced sizes):
+    per scene `per_class` negatives and `pos_ratio` times as many positives.
+    Uses a spawn-started process pool (safe after CUDA init)."""
     import multiprocessing as mp
     jobs = []
     for i in range(n_scenes):
         name, scale = TRAIN_RECIPES[i % len(TRAIN_RECIPES)]
-        jobs.append((name, scale, 1000 + i, per_class, seed))
+        jobs.append((name, scale, 1000 + i, per_class, seed, pos_ratio))
     workers = workers or max(1, min(16, (os.cpu_count() or 2)))
     with mp.get_context("spawn").Pool(workers) as pool:
         parts = pool.map(_scene_samples, jobs, chunksize=8)
@@ -291,16 +292,17 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     ap.add_argument("--checkpoint", default=None)
+    ap.add_argument("--pos-ratio", type=float, default=1.0, help="positives per negative in the training set")
     a = ap.parse_args()
     t0 = time.time()
-    X, y = make_training_set(a.scenes, a.per_class, a.seed)
+    X, y = make_training_set(a.scenes, a.per_class, a.seed, pos_ratio=a.pos_ratio)
     print(f"{len(y)} samples, {y.mean():.3f} positive, built in {time.time() - t0:.1f} s", flush=True)
     Xv, yv = make_training_set(64, 256, a.seed + 1)
     theta, hist = train(X, y, a.epochs, a.batch, a.lr, a.seed, checkpoint=a.checkpoint)
     acc, prec = accuracy(theta, Xv, yv, 0.5)
     acc9, prec9 = accuracy(theta, Xv, yv, 0.9)
     meta = dict(version=VERSION, scenes=a.scenes, per_class=a.per_class, epochs=a.epochs, batch=a.batch,
-                lr=a.lr, seed=a.seed, samples=int(len(y)), loss=hist, recipes=TRAIN_RECIPES,
+                lr=a.lr, seed=a.seed, samples=int(len(y)), loss=hist, recipes=TRAIN_RECIPES, pos_ratio=a.pos_ratio,
                 val_scenes=64, val_seed=a.seed + 1, val_accuracy_tau05=acc, val_precision_tau05=prec,
                 val_accuracy_tau09=acc9, val_precision_tau09=prec9)
     save_weights(a.out, theta, meta)
