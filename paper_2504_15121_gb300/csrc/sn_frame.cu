@@ -604,60 +604,96 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
         const __nv_bfloat16* w1row = W1s + ((lane & 7) + ((lane >> 4) << 3)) * kW1Ld + ((lane >> 3) & 1) * 8;
         const __nv_bfloat16* w2row = W2s + ((lane & 7) + ((lane >> 4) << 3)) * kW2Ld + ((lane >> 3) & 1) * 8;
         // layer 1: h1 = relu(conv3x3(feat) W1 + b1) on the tile + (kQM + 1) region; rows of
-        // the last m-tile past the region repeat its last pixel (their results are dropped)
-        for (int mt = warp; mt < kH1Tiles; mt += kThreads / 32) {
-            const int r = min(mt * 16 + (lane & 15), kH1N - 1);
-            const int hx = r % kH1W, hy = r / kH1W;
-            const uint4* fa = feat + hy * kFeatW + hx + 2 * (lane >> 4);
-            float acc0[4] = {b1a, b1b, b1a, b1b}, acc1[4] = {b1c, b1d, b1c, b1d};
+        // the last m-tile past the region repeat its last pixel (their results are dropped).
+        // A warp takes two m-tiles at a time (independent MMA chains, shared B fragments).
+        constexpr int kWarps = kThreads / 32;
+        for (int mt0 = warp; mt0 < kH1Tiles; mt0 += 2 * kWarps) {
+            const uint4* fa[2];
+            float acc[2][2][4];
 #pragma unroll
-            for (int st = 0; st < 3; st++) {
-                unsigned a[4], b[4];
-                ldsm_x4(a, fa + st * kFeatW);
-                ldsm_x4(b, w1row + 16 * st);
-                mma_bf16(acc0, a, b[0], b[1]);
-                mma_bf16(acc1, a, b[2], b[3]);
+            for (int j = 0; j < 2; j++) {
+                const int r = min((mt0 + j * kWarps) * 16 + (lane & 15), kH1N - 1);
+                const int hx = r % kH1W, hy = r / kH1W;
+                fa[j] = feat + hy * kFeatW + hx + 2 * (lane >> 4);
+                acc[j][0][0] = acc[j][0][2] = b1a;
+                acc[j][0][1] = acc[j][0][3] = b1b;
+                acc[j][1][0] = acc[j][1][2] = b1c;
+                acc[j][1][1] = acc[j][1][3] = b1d;
             }
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int rr = mt * 16 + gq + 8 * h;
-                if (rr < kH1N) {
-                    const __nv_bfloat162 v0 = __floats2bfloat162_rn(fmaxf(acc0[2 * h], 0.0f), fmaxf(acc0[2 * h + 1], 0.0f));
-                    const __nv_bfloat162 v1 = __floats2bfloat162_rn(fmaxf(acc1[2 * h], 0.0f), fmaxf(acc1[2 * h + 1], 0.0f));
-                    h1w[rr * kH1Ld + tq] = *reinterpret_cast<const unsigned*>(&v0);
-                    h1w[rr * kH1Ld + 4 + tq] = *reinterpret_cast<const unsigned*>(&v1);
+            for (int st = 0; st < 3; st++) {
+                unsigned b[4];
+                ldsm_x4(b, w1row + 16 * st);
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    unsigned a[4];
+                    ldsm_x4(a, fa[j] + st * kFeatW);
+                    mma_bf16(acc[j][0], a, b[0], b[1]);
+                    mma_bf16(acc[j][1], a, b[2], b[3]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int rr = (mt0 + j * kWarps) * 16 + gq + 8 * h;
+                    if (rr < kH1N) {
+                        const __nv_bfloat162 v0 =
+                            __floats2bfloat162_rn(fmaxf(acc[j][0][2 * h], 0.0f), fmaxf(acc[j][0][2 * h + 1], 0.0f));
+                        const __nv_bfloat162 v1 =
+                            __floats2bfloat162_rn(fmaxf(acc[j][1][2 * h], 0.0f), fmaxf(acc[j][1][2 * h + 1], 0.0f));
+                        h1w[rr * kH1Ld + tq] = *reinterpret_cast<const unsigned*>(&v0);
+                        h1w[rr * kH1Ld + 4 + tq] = *reinterpret_cast<const unsigned*>(&v1);
+                    }
                 }
             }
         }
         __syncthreads();
         // layer 2 and head: q = sigmoid(relu(conv3x3(h1) W2 + b2) . W3 + b3) on
-        // the tile + kQM region (rows of the last m-tile past it repeat its last pixel)
+        // the tile + kQM region (rows of the last m-tile past it repeat its last
+        // pixel); two m-tiles per warp at a time, as above
         {
             const float b2a = __ldg(gv.b2 + 2 * tq), b2b = __ldg(gv.b2 + 2 * tq + 1);
             const float b2c = __ldg(gv.b2 + 8 + 2 * tq), b2d = __ldg(gv.b2 + 9 + 2 * tq);
             const float w3a = __ldg(gv.W3 + 2 * tq), w3b = __ldg(gv.W3 + 2 * tq + 1);
             const float w3c = __ldg(gv.W3 + 8 + 2 * tq), w3d = __ldg(gv.W3 + 9 + 2 * tq);
             const float b3 = __ldg(gv.b3);
-            for (int mt = warp; mt < kQTiles; mt += kThreads / 32) {
-                const int r = min(mt * 16 + (lane & 15), kQN - 1);
-                const int qx = r % kQW, qy = r / kQW;
-                const unsigned* ha = h1w + (qy * kH1W + qx) * kH1Ld + (lane >> 4) * 4;
-                float acc0[4] = {b2a, b2b, b2a, b2b}, acc1[4] = {b2c, b2d, b2c, b2d};
+            for (int mt0 = warp; mt0 < kQTiles; mt0 += 2 * kWarps) {
+                const unsigned* ha[2];
+                float acc[2][2][4];
 #pragma unroll
-                for (int tap = 0; tap < 9; tap++) {
-                    unsigned a[4], b[4];
-                    ldsm_x4(a, ha + ((tap / 3) * kH1W + tap % 3) * kH1Ld);
-                    ldsm_x4(b, w2row + 16 * tap);
-                    mma_bf16(acc0, a, b[0], b[1]);
-                    mma_bf16(acc1, a, b[2], b[3]);
+                for (int j = 0; j < 2; j++) {
+                    const int r = min((mt0 + j * kWarps) * 16 + (lane & 15), kQN - 1);
+                    const int qx = r % kQW, qy = r / kQW;
+                    ha[j] = h1w + (qy * kH1W + qx) * kH1Ld + (lane >> 4) * 4;
+                    acc[j][0][0] = acc[j][0][2] = b2a;
+                    acc[j][0][1] = acc[j][0][3] = b2b;
+                    acc[j][1][0] = acc[j][1][2] = b2c;
+                    acc[j][1][1] = acc[j][1][3] = b2d;
                 }
 #pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    float part = w3a * fmaxf(acc0[2 * h], 0.0f) + w3b * fmaxf(acc0[2 * h + 1], 0.0f) +
-                                 w3c * fmaxf(acc1[2 * h], 0.0f) + w3d * fmaxf(acc1[2 * h + 1], 0.0f);
-                    part += __shfl_xor_sync(0xffffffffu, part, 1);
-                    part += __shfl_xor_sync(0xffffffffu, part, 2);
-                    if (tq == 0) qs[mt * 16 + gq + 8 * h] = 1.0f / (1.0f + __expf(-(part + b3)));
+                for (int tap = 0; tap < 9; tap++) {
+                    unsigned b[4];
+                    ldsm_x4(b, w2row + 16 * tap);
+#pragma unroll
+                    for (int j = 0; j < 2; j++) {
+                        unsigned a[4];
+                        ldsm_x4(a, ha[j] + ((tap / 3) * kH1W + tap % 3) * kH1Ld);
+                        mma_bf16(acc[j][0], a, b[0], b[1]);
+                        mma_bf16(acc[j][1], a, b[2], b[3]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    const int mt = mt0 + j * kWarps;
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        float part = w3a * fmaxf(acc[j][0][2 * h], 0.0f) + w3b * fmaxf(acc[j][0][2 * h + 1], 0.0f) +
+                                     w3c * fmaxf(acc[j][1][2 * h], 0.0f) + w3d * fmaxf(acc[j][1][2 * h + 1], 0.0f);
+                        part += __shfl_xor_sync(0xffffffffu, part, 1);
+                        part += __shfl_xor_sync(0xffffffffu, part, 2);
+                        if (tq == 0 && mt < kQTiles) qs[mt * 16 + gq + 8 * h] = 1.0f / (1.0f + __expf(-(part + b3)));
+                    }
                 }
             }
         }
