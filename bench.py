@@ -339,8 +339,10 @@ def run_ours(args):
     for f in forms.values():
         f["vs_plain"] = f["value"] / value
     # the comparison estimators of Sec. IV on the same scenes (normals only)
-    comparators = {"cross": time_comparator(scenes, args, "cross", 0, world),
-                   "pca_9x9": time_comparator(scenes, args, "pca", 4, world)}
+    comparators = None
+    if world == 1:
+        comparators = {"cross": time_comparator(scenes, args, "cross", 0, world),
+                       "pca_9x9": time_comparator(scenes, args, "pca", 4, world)}
     # mixed-resolution batch of 64 frames, one graph launch per step
     mixed = run_mixed_batch(args) if world == 1 and not args.no_mixed else None
 
