@@ -343,6 +343,7 @@ def run_ours(args):
     if world == 1:
         comparators = {"cross": time_comparator(scenes, args, "cross", 0, world),
                        "pca_9x9": time_comparator(scenes, args, "pca", 4, world)}
+    stage_calls = time_stage_calls(scenes, args) if world == 1 else None
     # mixed-resolution batch of 64 frames, one graph launch per step
     mixed = run_mixed_batch(args) if world == 1 and not args.no_mixed else None
 
@@ -395,6 +396,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "forms": forms,
             "comparators": comparators,
+            "stage_calls": stage_calls,
             "mixed_batch": mixed,
             "clocks": clk,
             "e2e": e2e,
@@ -615,6 +617,65 @@ def run_mixed_batch(args, seed=0):
             for pp in pipes.values():
                 pp.close()
     out["learned_vs_plain"] = out["learned_f32"]["value"] / out["plain_f32"]["value"]
+    return out
+
+
+# compulsory bytes per pixel of each stage entry point (FP32 form)
+STAGE_BYTES = {"sn_denoise": 4 + 4 + 1, "sn_affine_normals": 4 + 4 + 12 + 1, "sn_components": 4 + 4,
+               "sn_pointcloud": 4 + 1 + 12}
+
+
+def time_stage_calls(scenes, args):
+    """Each stage entry point on its own (default method, same scenes, one
+    stream): device time per frame from CUDA events around a run of calls,
+    MPix/s and the fraction of the measured HBM bandwidth its compulsory
+    bytes reach."""
+    import torch
+    from paper_2504_15121_gb300 import sn
+    peaks, _ = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    s0 = scenes[0]
+    W, H = s0.W, s0.H
+    ctx = sn.sn_create(s0.camera, W, H, sn.default_params())
+    out = {}
+    try:
+        disp = []
+        for s in scenes:
+            t = sn.empty_image(H, W, torch.float32)
+            t.copy_(torch.from_numpy(s.disp))
+            disp.append(t)
+        den = [sn.empty_image(H, W, torch.float32) for _ in scenes]
+        m1 = [sn.empty_image(H, W, torch.uint8) for _ in scenes]
+        nrm = sn.empty_planes(3, H, W)
+        m2 = sn.empty_image(H, W, torch.uint8)
+        lab = sn.empty_image(H, W, torch.int32)
+        pts = sn.empty_planes(3, H, W)
+        for i in range(len(scenes)):
+            sn.sn_denoise(ctx, disp[i], den[i], m1[i])
+        calls = {
+            "sn_denoise": lambda i: sn.sn_denoise(ctx, disp[i], den[i], m1[i]),
+            "sn_affine_normals": lambda i: sn.sn_affine_normals(ctx, disp[i], den[i], nrm, m2),
+            "sn_components": lambda i: sn.sn_components(ctx, disp[i], lab, None),
+            "sn_pointcloud": lambda i: sn.sn_pointcloud(ctx, den[i], m1[i], pts),
+        }
+        reps = max(8, args.steps // 8)
+        for name, call in calls.items():
+            for i in range(4):
+                call(i % len(scenes))
+            torch.cuda.synchronize()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record()
+            for i in range(reps):
+                call(i % len(scenes))
+            t1.record()
+            torch.cuda.synchronize()
+            us = t0.elapsed_time(t1) / reps * 1e3
+            gbs = STAGE_BYTES[name] * W * H / (us * 1e-6) / 1e9
+            out[name] = {"us_per_frame": us, "mpix_s": W * H / us, "algo_bytes_per_px": STAGE_BYTES[name],
+                         "hbm_frac": gbs / hbm}
+        sn.sn_check_device(ctx)
+    finally:
+        sn.sn_destroy(ctx)
     return out
 
 
