@@ -882,6 +882,93 @@ cudaError_t launch_var(const Geo& g, const StarTable& t, const void* disp, size_
     }
 }
 
+// ---------------------------------------------------------------- stage kernels on the fast paths
+// sn_denoise with the 5x5 window and sn_affine_normals with the M = 8, s = 10
+// star, on the fused kernel's code: the popcount denoise and the branch-free
+// compile-time rays over a (D, 1/D) tile.  32 x 8 tiles, 4 CTAs per SM.
+constexpr int kSTH = 8;
+
+template <int IN, int R>
+__device__ __forceinline__ void stage_pairs(int2* tile, const char* disp, size_t dp, int x0, int y0, const Geo& g,
+                                            bool with_rcp) {
+    constexpr int TW = kTW + 2 * R, N = TW * (kSTH + 2 * R);
+    for (int i = threadIdx.y * kTW + threadIdx.x; i < N; i += kTW * kSTH) {
+        const int ly = i / TW, lx = i - ly * TW;
+        const int D = load_code<IN>(disp, dp, x0 - R + lx, y0 - R + ly, g.W, g.H);
+        const float w = !with_rcp ? 0.0f : (D > 0 ? rcp_approx((float)D) : __int_as_float(0x7f800000));
+        tile[i] = make_int2(D, __float_as_int(w));
+    }
+}
+
+template <int IN>
+__global__ void __launch_bounds__(kTW* kSTH, 4)
+    k_denoise5(const Geo g, const char* __restrict__ disp, size_t dp, float* __restrict__ den, size_t denp,
+               uint8_t* __restrict__ mask, size_t mp) {
+    constexpr int R = 2, TW = kTW + 2 * R;
+    __shared__ int2 tile[TW * (kSTH + 2 * R)];
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kSTH;
+    stage_pairs<IN, R>(tile, disp, dp, x0, y0, g, false);
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= g.W || y >= g.H) return;
+    const int2* c = tile + (threadIdx.y + R) * TW + threadIdx.x + R;
+    const int Dc = c[0].x;
+    float out = 0.0f;
+    uint8_t m = 0;
+    if (Dc > 0) {
+        long long num, det;
+        const bool fit = denoise_exact<2>(c, TW, 2, Dc, g.K_range, num, det);
+        const float dcf = fit ? i64_to_f32(num) / i64_to_f32(det) : 0.0f;
+        out = ((float)Dc + dcf) * (1.0f / 256.0f);
+        m = SN_MASK_VALID | (fit ? SN_MASK_DENOISED : 0);
+    }
+    reinterpret_cast<float*>(reinterpret_cast<char*>(den) + (size_t)y * denp)[x] = out;
+    mask[(size_t)y * mp + x] = m;
+}
+
+template <int IN>
+__global__ void __launch_bounds__(kTW* kSTH, 4)
+    k_affine_star8(const Geo g, const char* __restrict__ disp, size_t dp, const float* __restrict__ den,
+                   size_t denp, char* __restrict__ nrm, size_t np, uint8_t* __restrict__ mask, size_t mp,
+                   int mask_or) {
+    constexpr int R = 10, TW = kTW + 2 * R;
+    __shared__ int2 tile[TW * (kSTH + 2 * R)];
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kSTH;
+    stage_pairs<IN, R>(tile, disp, dp, x0, y0, g, true);
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= g.W || y >= g.H) return;
+    const int2* c = tile + (threadIdx.y + R) * TW + threadIdx.x + R;
+    const int Dc = c[0].x;
+    float n[3] = {0.0f, 0.0f, 0.0f};
+    uint8_t m = 0;
+    if (Dc > 0) {
+        m = SN_MASK_VALID;
+        const float dtil =
+            __ldg(reinterpret_cast<const float*>(reinterpret_cast<const char*>(den) + (size_t)y * denp) + x);
+        AffSums s;
+        star8<10, TW>(c, Dc, __int_as_float(c[0].y), make_thr(g, Dc), s);
+        bool fp64;
+        if (solve_normal(s, Dc, dtil, x, y, g, n, fp64)) m |= SN_MASK_NORMAL | (fp64 ? SN_MASK_FP64 : 0);
+    }
+    if (g.normal_fmt == SN_NORMALS_F32X3) {
+        const size_t plane = (size_t)g.H * np;
+        float* p0 = reinterpret_cast<float*>(nrm + (size_t)y * np) + x;
+        p0[0] = n[0];
+        *reinterpret_cast<float*>(reinterpret_cast<char*>(p0) + plane) = n[1];
+        *reinterpret_cast<float*>(reinterpret_cast<char*>(p0) + 2 * plane) = n[2];
+    } else {
+        short4 q;
+        q.x = snorm16(n[0]);
+        q.y = snorm16(n[1]);
+        q.z = snorm16(n[2]);
+        q.w = 0;
+        reinterpret_cast<short4*>(nrm + (size_t)y * np)[x] = q;
+    }
+    uint8_t* mo = mask + (size_t)y * mp + x;
+    *mo = mask_or ? (uint8_t)(*mo | m) : m;
+}
+
 }  // namespace
 
 bool star_is_m8(const StarTable& t, int dirs, int steps) {
@@ -923,6 +1010,33 @@ cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const voi
     if (e != cudaSuccess) return e;
     const bool m8 = !learned && g.support == SN_SUPPORT_STARFILL_CD && star8;
     return launch_ccl_merge_flatten(g, disp, dp, o.labels, o.lp, o.count, kTW, m8 ? frame_th(2) : kTH, s, mk);
+}
+
+
+cudaError_t launch_denoise5(const Geo& g, const void* disp, size_t dp, float* den, size_t denp, uint8_t* mask,
+                            size_t mp, cudaStream_t s) {
+    const dim3 grid((g.W + kTW - 1) / kTW, (g.H + kSTH - 1) / kSTH), block(kTW, kSTH);
+    const char* d = static_cast<const char*>(disp);
+    switch (g.in_dtype) {
+        case SN_IN_F32: k_denoise5<SN_IN_F32><<<grid, block, 0, s>>>(g, d, dp, den, denp, mask, mp); break;
+        case SN_IN_F16: k_denoise5<SN_IN_F16><<<grid, block, 0, s>>>(g, d, dp, den, denp, mask, mp); break;
+        default: k_denoise5<SN_IN_U16X256><<<grid, block, 0, s>>>(g, d, dp, den, denp, mask, mp); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_affine_star8(const Geo& g, const void* disp, size_t dp, const float* den, size_t denp, void* nrm,
+                                size_t np, uint8_t* mask, size_t mp, bool mask_or, cudaStream_t s) {
+    const dim3 grid((g.W + kTW - 1) / kTW, (g.H + kSTH - 1) / kSTH), block(kTW, kSTH);
+    const char* d = static_cast<const char*>(disp);
+    char* n = static_cast<char*>(nrm);
+    const int mo = mask_or ? 1 : 0;
+    switch (g.in_dtype) {
+        case SN_IN_F32: k_affine_star8<SN_IN_F32><<<grid, block, 0, s>>>(g, d, dp, den, denp, n, np, mask, mp, mo); break;
+        case SN_IN_F16: k_affine_star8<SN_IN_F16><<<grid, block, 0, s>>>(g, d, dp, den, denp, n, np, mask, mp, mo); break;
+        default: k_affine_star8<SN_IN_U16X256><<<grid, block, 0, s>>>(g, d, dp, den, denp, n, np, mask, mp, mo); break;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace sn

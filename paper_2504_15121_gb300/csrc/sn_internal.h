@@ -94,6 +94,11 @@ cudaError_t launch_points(const Geo& g, const float* den, size_t denp, const uin
 // three stage slots: tile-local union-find, border merge, flatten
 cudaError_t launch_components(const Geo& g, const void* disp, size_t dp, int32_t* labels,
                               size_t lp, int32_t* count, cudaStream_t s, Marks& mk);
+// stage kernels on the fused kernel's fast paths (5x5 denoise; M = 8, s = 10 star)
+cudaError_t launch_denoise5(const Geo& g, const void* disp, size_t dp, float* den, size_t denp, uint8_t* mask,
+                            size_t mp, cudaStream_t s);
+cudaError_t launch_affine_star8(const Geo& g, const void* disp, size_t dp, const float* den, size_t denp, void* nrm,
+                                size_t np, uint8_t* mask, size_t mp, bool mask_or, cudaStream_t s);
 // comparison estimators (one stage slot each)
 cudaError_t launch_cross(const Geo& g, const void* disp, size_t dp, void* nrm, size_t np, uint8_t* mask,
                          size_t mp, cudaStream_t s, Marks& mk);

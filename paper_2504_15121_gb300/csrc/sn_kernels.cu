@@ -126,33 +126,58 @@ template <int IN>
 __global__ void __launch_bounds__(kCclTile * 8)
     k_ccl_local(const Geo g, const char* __restrict__ disp, size_t dp, int* __restrict__ labels,
                 size_t lpe, int* __restrict__ count) {
+    // Each warp labels rows ty, ty + 8, ty + 16, ty + 24 of the 32 x 32 tile:
+    // the pixels joined to their left neighbour form runs, labelled by the
+    // run's first lane (from a ballot of left edges); then vertical edges join
+    // the runs of adjacent rows in a shared-memory union-find (an edge implied
+    // by its left neighbour's is skipped).
+    constexpr int kRows = kCclTile / 8;
     __shared__ int Ds[kCclTile * kCclTile];
     __shared__ int Ls[kCclTile * kCclTile];
+    __shared__ unsigned Lrow[kCclTile];
     const int x0 = blockIdx.x * kCclTile, y0 = blockIdx.y * kCclTile;
-    const int tx = threadIdx.x;
-    if (count && blockIdx.x == 0 && blockIdx.y == 0 && tx == 0 && threadIdx.y == 0) *count = 0;
-    for (int r = threadIdx.y; r < kCclTile; r += 8) {
-        const int i = r * kCclTile + tx;
-        const int D = load_code<IN>(disp, dp, x0 + tx, y0 + r, g.W, g.H);
-        Ds[i] = D;
-        Ls[i] = D > 0 ? i : -1;
+    const int lane = threadIdx.x;
+    if (count && blockIdx.x == 0 && blockIdx.y == 0 && lane == 0 && threadIdx.y == 0) *count = 0;
+#pragma unroll
+    for (int k = 0; k < kRows; k++) {
+        const int r = threadIdx.y + 8 * k;
+        Ds[r * kCclTile + lane] = load_code<IN>(disp, dp, x0 + lane, y0 + r, g.W, g.H);
     }
     __syncthreads();
-    for (int r = threadIdx.y; r < kCclTile; r += 8) {
-        const int i = r * kCclTile + tx;
+    const unsigned upto = 0xffffffffu >> (31 - lane);
+    int run[kRows];
+    bool eU[kRows];
+    unsigned Lb[kRows], Ub[kRows];
+#pragma unroll
+    for (int k = 0; k < kRows; k++) {
+        const int r = threadIdx.y + 8 * k, i = r * kCclTile + lane;
         const int D = Ds[i];
-        if (D <= 0) continue;
-        if (tx + 1 < kCclTile && pair_edge(D, Ds[i + 1], g.K_pair)) union_s(Ls, i, i + 1, g.err);
-        if (r + 1 < kCclTile && pair_edge(D, Ds[i + kCclTile], g.K_pair)) union_s(Ls, i, i + kCclTile, g.err);
+        const bool eL = lane > 0 && pair_edge(D, Ds[i - 1], g.K_pair);
+        eU[k] = r > 0 && pair_edge(D, Ds[i - kCclTile], g.K_pair);
+        Lb[k] = __ballot_sync(0xffffffffu, eL);
+        Ub[k] = __ballot_sync(0xffffffffu, eU[k]);
+        run[k] = r * kCclTile + (31 - __clz(~Lb[k] & upto));
+        Ls[i] = D > 0 ? run[k] : -1;
+        if (lane == 0) Lrow[r] = Lb[k];
     }
     __syncthreads();
-    for (int r = threadIdx.y; r < kCclTile; r += 8) {
-        const int x = x0 + tx, y = y0 + r;
+#pragma unroll
+    for (int k = 0; k < kRows; k++) {
+        if (!eU[k]) continue;
+        const int r = threadIdx.y + 8 * k;
+        const unsigned Lup = Lrow[r - 1];
+        const bool implied = lane > 0 && ((Ub[k] >> (lane - 1)) & 1u) && ((Lb[k] >> lane) & 1u) && ((Lup >> lane) & 1u);
+        if (!implied) union_s(Ls, run[k], (r - 1) * kCclTile + (31 - __clz(~Lup & upto)), g.err);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kRows; k++) {
+        const int r = threadIdx.y + 8 * k;
+        const int x = x0 + lane, y = y0 + r;
         if (x >= g.W || y >= g.H) continue;
-        const int i = r * kCclTile + tx;
         int out = -1;
-        if (Ds[i] > 0) {
-            const int root = find_s(Ls, i);
+        if (Ds[r * kCclTile + lane] > 0) {
+            const int root = find_s(Ls, run[k]);
             out = (y0 + root / kCclTile) * g.W + x0 + (root % kCclTile);
         }
         labels[(size_t)y * lpe + x] = out;
@@ -242,6 +267,11 @@ static dim3 grid2(const Geo& g) { return dim3((g.W + kTW - 1) / kTW, (g.H + kTH 
 
 cudaError_t launch_denoise(const Geo& g, const void* disp, size_t dp, float* den, size_t denp,
                            uint8_t* mask, size_t mp, cudaStream_t s, Marks& mk) {
+    if (g.r_d == 2) {
+        const cudaError_t e = launch_denoise5(g, disp, dp, den, denp, mask, mp, s);
+        mk.after(s);
+        return e;
+    }
     const int R = g.r_d;
     const size_t smem = sizeof(int) * (kTW + 2 * R) * (kTH + 2 * R);
     const char* d = static_cast<const char*>(disp);
@@ -269,6 +299,11 @@ static void affine_dispatch(const Geo& g, const StarTable& t, const char* d, siz
 cudaError_t launch_affine(const Geo& g, const StarTable& t, const void* disp, size_t dp,
                           const float* den, size_t denp, void* nrm, size_t np, uint8_t* mask,
                           size_t mp, bool mask_or, cudaStream_t s, Marks& mk) {
+    if (g.support == SN_SUPPORT_STARFILL_CD && star_is_m8(t, g.dirs, g.steps)) {
+        const cudaError_t e = launch_affine_star8(g, disp, dp, den, denp, nrm, np, mask, mp, mask_or, s);
+        mk.after(s);
+        return e;
+    }
     const bool st = g.support == SN_SUPPORT_STARFILL_ST;
     const int R = g.support == SN_SUPPORT_FIXED ? g.r_a : (st ? g.steps + 1 : g.steps);
     // tile ints (+ one edge byte per tile entry for ST); at most 33 KB (s = 30)
