@@ -32,20 +32,22 @@ METRIC = "MPix/s (2048x1024 stereo normals chain)"
 # algorithmic bytes per pixel of each launch of sn_run_frame (compulsory
 # reads and writes of that kernel)
 ALGO_BYTES = {
-    "frame": 4 + 12 + 12 + 1 + 4,         # disp in; normals, points, mask, tile-local labels out
+    "frame": 4 + 12 + 12 + 1,             # disp in; normals, points, mask out
+    "ccl_local": 4 + 4,                   # disparity in, tile-local labels out
     "ccl_merge": 0,                       # tile borders only
     "ccl_flatten": 4 + 4,                 # labels in and out
 }
 FRAME_ALGO_BYTES = 33                      # disp 4 + normals 12 + points 12 + labels 4 + mask 1
 # Algorithmic integer/FP operations per pixel of the fused frame kernel for
 # the default method (5x5 range-gated denoise, star-fill M = 8, s = 10,
-# two-pass fit, normal, point, component edges), counted from the method's
+# two-pass fit, normal, point), counted from the method's
 # definition: denoise 24 neighbours x 15 (validity, range gate, 6 moment and
 # 3 data sums) + 30 (3x3 solve) = 390; star-fill 80 steps x 8 (validity,
 # running min and max, covered-depth test) = 640; fit over ~68 support
 # pixels x 9 (6 moment sums, residual, 2 data FMAs) + 40 (2x2 solve, normal,
-# point) = 652; component edges and unions 13; ingest 5.
-ALGO_OPS_PER_PX = {"frame": 1700}
+# point) = 652; ingest 5 (the component edges and unions belong to
+# k_ccl_local, not to this kernel).
+ALGO_OPS_PER_PX = {"frame": 1687}
 # One instruction per lane per clock: 152 SMs x 4 schedulers x 32 lanes.
 SM_COUNT, LANES_PER_SM = 152, 128
 

@@ -10,9 +10,9 @@
 #include "sn_internal.h"
 
 namespace {
-constexpr int kStages = 3;         // kernel launches of one sn_run_frame
+constexpr int kStages = 4;         // kernel launches of one sn_run_frame
 constexpr int kProfFrames = 4096;  // frames recorded between two sn_stage_times calls
-const char* const kStageNames[kStages] = {"frame", "ccl_merge", "ccl_flatten"};
+const char* const kStageNames[kStages] = {"frame", "ccl_local", "ccl_merge", "ccl_flatten"};
 }  // namespace
 
 struct sn_ctx {

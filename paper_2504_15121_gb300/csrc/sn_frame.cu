@@ -1,6 +1,9 @@
 // Fused frame kernel: one pass over 32 x 16 pixel tiles computes the
 // denoised disparity, the support (fixed window or star-fill), the affine
-// fit, the normal, the point, the mask and the tile-local component labels.
+// fit, the normal, the point and the mask.  The component labels come from
+// the separate run-based passes (k_ccl_local, k_ccl_merge, k_ccl_flatten),
+// launched after it on the same stream: they need only the ingested codes,
+// and outside this kernel they keep its registers and shared memory free.
 // The tile and its halo are staged once in shared memory as (D, 1/D) pairs:
 // D is the exact integer disparity code used by every sum and decision,
 // 1/D (FP32, correctly rounded; +inf for invalid) carries the covered-depth
@@ -439,8 +442,8 @@ __device__ __forceinline__ void fast_pixel(const Geo& g, int Dc, const WinSums& 
 // one surface (their union is the window).
 constexpr int kFastR = SN_LEARNED_RADIUS, kQM = kFastR - 2;
 static_assert(kFastR >= 3 && kFastR + 2 <= 10, "the features of the q region must lie inside the halo of 10");
-// Shared-memory layout of the learned variant (after the tile, the
-// union-find parents and the row masks; all offsets 16-byte aligned).
+// Shared-memory layout of the learned variant (after the tile; all offsets
+// 16-byte aligned).
 constexpr int kFeatW = kTW + 2 * (kQM + 2), kFeatH = kTH + 2 * (kQM + 2);  // features: tile + kQM + 2
 constexpr int kH1W = kTW + 2 * (kQM + 1), kH1H = kTH + 2 * (kQM + 1);      // layer 1:  tile + kQM + 1
 constexpr int kQW = kTW + 2 * kQM, kQH = kTH + 2 * kQM;                    // q:        tile + kQM
@@ -459,6 +462,11 @@ constexpr int kW1K = 48;
 constexpr int kW1Ld = 56, kW2Ld = 152;      // padded bf16 rows of the weights (conflict-free ldmatrix)
 constexpr int kH1Ld = 12;                   // words per layer-1 row: 16 bf16 + 16 B pad (conflict-free ldmatrix)
 constexpr size_t align16z(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// tile (D, 1/D) (+ one ST edge byte per tile entry) of a 32 x TH tile
+__host__ __device__ constexpr size_t frame_smem(int Rr, bool st = false, int TH = kTH) {
+    return sizeof(int2) * (size_t)(kTW + 2 * Rr) * (TH + 2 * Rr) + (st ? (size_t)(kTW + 2 * Rr) * (TH + 2 * Rr) : 0);
+}
 
 struct LearnedSmem {
     size_t cnt, w1, w2, feat, h1, q, end;
@@ -496,12 +504,9 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
     const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : (VAR == 4 ? g.steps + 1 : g.steps));
     const int TWR = kTW + 2 * Rr, THR = TH + 2 * Rr;
     int2* tile = reinterpret_cast<int2*>(smem);
-    int* Ls = reinterpret_cast<int*>(smem + sizeof(int2) * (size_t)TWR * THR);  // union-find parents
-    unsigned* Lrow = reinterpret_cast<unsigned*>(Ls + NT);                        // left-edge mask per row
-    uint8_t* Est = reinterpret_cast<uint8_t*>(Lrow + TH);                         // ST edge bytes (VAR 4)
+    uint8_t* Est = reinterpret_cast<uint8_t*>(smem + sizeof(int2) * (size_t)TWR * THR);  // ST edge bytes (VAR 4)
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * TH;
     const int tid = threadIdx.y * kTW + threadIdx.x;
-    if (o.count && (blockIdx.x | blockIdx.y | tid) == 0) *o.count = 0;
 
     // ---- stage the tile and its halo: (D, 1/D)
     const int n = TWR * THR;
@@ -529,18 +534,7 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
     const int2* c = tile + (threadIdx.y + Rr) * TWR + threadIdx.x + Rr;
     const int Dc = c[0].x;  // 0 outside the image
 
-    // ---- tile-local components, part 1: each tile row is one warp; the
-    // pixels joined to their left neighbour form runs, labelled by the run's
-    // first lane (found from the ballot of left edges)
     const int lane = threadIdx.x, row = threadIdx.y;
-    const bool eL = lane > 0 && pair_edge(Dc, c[-1].x, g.K_pair);
-    const bool eU = row > 0 && pair_edge(Dc, c[-TWR].x, g.K_pair);
-    const unsigned Lb = __ballot_sync(0xffffffffu, eL);
-    const unsigned Ub = __ballot_sync(0xffffffffu, eU);
-    const unsigned upto = 0xffffffffu >> (31 - lane);
-    const int run = row * kTW + (31 - __clz(~Lb & upto));
-    Ls[tid] = Dc > 0 ? run : -1;
-    if (lane == 0) Lrow[row] = Lb;
 
     if constexpr (VAR != 3) {
         if (inside) {
@@ -551,8 +545,7 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
     } else {
         // ================= learned gate (tensor cores), then the two paths
         constexpr int TW = kTW + 2 * R;
-        constexpr LearnedSmem L = learned_layout(sizeof(int2) * (size_t)(kTW + 2 * R) * (kTH + 2 * R) +
-                                                 sizeof(int) * (kThreads + kTH));
+        constexpr LearnedSmem L = learned_layout(frame_smem(R));  // the launch sizes it the same way
         int* cnt = reinterpret_cast<int*>(smem + L.cnt);
         __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(smem + L.w1);
         __nv_bfloat16* W2s = reinterpret_cast<__nv_bfloat16*>(smem + L.w2);
@@ -811,32 +804,6 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
             emit(g, o, x0 + px, y0 + py, r);
         }
     }
-
-    // ---- tile-local components, part 2: join the runs of adjacent rows.  A
-    // vertical edge is skipped when the pixel to its left has one too and
-    // both rows are joined there (the left edge already unites the same runs).
-    __syncthreads();
-    if (eU) {
-        const unsigned Lup = Lrow[row - 1];
-        const bool implied = lane > 0 && ((Ub >> (lane - 1)) & 1u) && ((Lb >> lane) & 1u) && ((Lup >> lane) & 1u);
-        if (!implied) union_s(Ls, run, (row - 1) * kTW + (31 - __clz(~Lup & upto)), g.err);
-    }
-    __syncthreads();
-    if (inside) {
-        int lab = -1;
-        if (Dc > 0) {
-            const int r = find_s(Ls, run);
-            lab = (y0 + r / kTW) * g.W + x0 + (r % kTW);
-        }
-        o.labels[(size_t)y * (o.lp / 4) + x] = lab;
-    }
-}
-
-// tile (D, 1/D), union-find parents, row masks (+ one ST edge byte per tile
-// entry) of a 32 x TH tile
-__host__ __device__ constexpr size_t frame_smem(int Rr, bool st = false, int TH = kTH) {
-    return sizeof(int2) * (size_t)(kTW + 2 * Rr) * (TH + 2 * Rr) + sizeof(int) * (kTW * TH + TH) +
-           (st ? (size_t)(kTW + 2 * Rr) * (TH + 2 * Rr) : 0);
 }
 
 // Raises a kernel's dynamic shared-memory limit once per device, to the most
@@ -1008,8 +975,7 @@ cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const voi
         e = launch_var<0, 0, 0>(g, t, disp, dp, o, none, s);
     mk.after(s);
     if (e != cudaSuccess) return e;
-    const bool m8 = !learned && g.support == SN_SUPPORT_STARFILL_CD && star8;
-    return launch_ccl_merge_flatten(g, disp, dp, o.labels, o.lp, o.count, kTW, m8 ? frame_th(2) : kTH, s, mk);
+    return launch_components(g, disp, dp, o.labels, o.lp, o.count, s, mk);
 }
 
 
