@@ -234,7 +234,13 @@ typedef struct {
 
 /* The whole chain on one frame: the results of sn_denoise, sn_affine_normals,
  * sn_components and sn_pointcloud on the same input, with the mask carrying
- * all their bits.  Enqueued as a few fused kernels on `stream`. */
+ * all their bits.  Four kernel launches, ordered after earlier work on
+ * `stream` and before later work on it: the fused frame kernel on `stream`,
+ * and the three component passes (which read only the disparity) on one of
+ * the context's side streams, forked from `stream` and joined back to it by
+ * events, so that they run concurrently with the frame kernel.  Legal under
+ * CUDA stream capture (the fork and join become graph edges).  While
+ * profiling is on (sn_set_profiling), all four launches stay on `stream`. */
 sn_status sn_run_frame(sn_ctx *ctx, const sn_frame_in *in, sn_frame_out *out, sn_stream stream);
 
 /* Allocation-free denoise + normals.  The paper has no counterpart: this is
@@ -285,8 +291,8 @@ sn_status sn_set_walk_limit(sn_ctx *ctx, int steps);
 sn_status sn_check_device(sn_ctx *ctx, sn_stream stream);
 
 /* Stage timing, for benchmarks and serving statistics.  While profiling is
- * on, sn_run_frame records a CUDA event on its stream before its first and
- * after each of its kernel launches (stage i = the i-th launch, named by
+ * on, sn_run_frame enqueues all its launches on its stream and records a
+ * CUDA event before its first and after each of them (stage i = the i-th launch, named by
  * sn_stage_name).  sn_stage_times waits for the recorded events, writes the
  * summed milliseconds of each stage since the previous call into ms[0..n-1]
  * (n >= sn_stage_count), the number of frames into *frames, the duration of

@@ -12,6 +12,7 @@
 namespace {
 constexpr int kStages = 4;         // kernel launches of one sn_run_frame
 constexpr int kProfFrames = 4096;  // frames recorded between two sn_stage_times calls
+constexpr int kAux = 4;            // side streams the component passes of sn_run_frame fork onto
 const char* const kStageNames[kStages] = {"frame", "ccl_local", "ccl_merge", "ccl_flatten"};
 }  // namespace
 
@@ -31,6 +32,12 @@ struct sn_ctx {
     bool prof;
     cudaEvent_t* ev;  // kProfFrames x (kStages + 1)
     int prof_frames;
+    // The component passes read only the disparity, so sn_run_frame runs
+    // them on a side stream forked from the caller's (events fork and join),
+    // concurrently with the frame kernel; frames take the side streams in turn.
+    cudaStream_t aux[kAux];
+    cudaEvent_t fork_ev[kAux], join_ev[kAux];
+    int aux_next;
     char msg[512];
 };
 
@@ -319,6 +326,13 @@ sn_status sn_create(const sn_camera* cam, int W, int H, const sn_params* pin, sn
         c->ws.den_pitch = ((size_t)W * 4 + 15) & ~(size_t)15;
         e = cudaMalloc(&c->ws.den, c->ws.den_pitch * H);
     }
+    int prio_lo = 0, prio_hi = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    for (int i = 0; i < kAux && e == cudaSuccess; i++) {
+        e = cudaStreamCreateWithPriority(&c->aux[i], cudaStreamNonBlocking, prio_hi);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork_ev[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming);
+    }
     if (e == cudaSuccess && p.learned) {
         e = sn::gate_alloc(c->gate);
         if (e == cudaSuccess) e = cudaMalloc(&c->gate_theta, sizeof(float) * sn::kGateParams);
@@ -339,6 +353,11 @@ sn_status sn_destroy(sn_ctx* c) {
     if (c->ev) {
         for (int i = 0; i < kProfFrames * (kStages + 1); i++) cudaEventDestroy(c->ev[i]);
         delete[] c->ev;
+    }
+    for (int i = 0; i < kAux; i++) {
+        if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
+        if (c->fork_ev[i]) cudaEventDestroy(c->fork_ev[i]);
+        if (c->join_ev[i]) cudaEventDestroy(c->join_ev[i]);
     }
     if (c->ws.err) cudaFree(c->ws.err);
     if (c->ws.den) cudaFree(c->ws.den);
@@ -472,8 +491,25 @@ sn_status sn_run_frame(sn_ctx* c, const sn_frame_in* in, sn_frame_out* out, sn_s
         if (!c->gate_loaded) return fail(c, SN_EINVAL, "learned context: gate weights not loaded");
         gv = sn::GateView{c->gate.W1g, c->gate.W2g, c->gate.b1, c->gate.b2, c->gate.W3, c->gate.b3, c->p.tau};
     }
-    cudaError_t e = sn::launch_frame(c->geo, c->star, c->star8, in->disp, in->disp_pitch, fo,
-                                     c->p.learned ? &gv : nullptr, stream, mk);
+    const sn::GateView* g = c->p.learned ? &gv : nullptr;
+    cudaError_t e;
+    if (mk.ev) {
+        // profiled frames keep all launches on the caller's stream, so that
+        // the events between them time each kernel alone
+        e = sn::launch_frame(c->geo, c->star, c->star8, in->disp, in->disp_pitch, fo, g, stream, mk);
+        if (e == cudaSuccess)
+            e = sn::launch_components(c->geo, in->disp, in->disp_pitch, fo.labels, fo.lp, fo.count, stream, mk);
+    } else {
+        const int i = c->aux_next;
+        c->aux_next = (i + 1) % kAux;
+        e = cudaEventRecord(c->fork_ev[i], stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux[i], c->fork_ev[i], 0);
+        if (e == cudaSuccess)
+            e = sn::launch_components(c->geo, in->disp, in->disp_pitch, fo.labels, fo.lp, fo.count, c->aux[i], mk);
+        if (e == cudaSuccess) e = cudaEventRecord(c->join_ev[i], c->aux[i]);
+        if (e == cudaSuccess) e = sn::launch_frame(c->geo, c->star, c->star8, in->disp, in->disp_pitch, fo, g, stream, mk);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, c->join_ev[i], 0);
+    }
     c->launches += mk.launches;
     return e == cudaSuccess ? SN_OK : cuda_fail(c, e, "sn_run_frame");
 }

@@ -974,8 +974,7 @@ cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const voi
     else
         e = launch_var<0, 0, 0>(g, t, disp, dp, o, none, s);
     mk.after(s);
-    if (e != cudaSuccess) return e;
-    return launch_components(g, disp, dp, o.labels, o.lp, o.count, s, mk);
+    return e;
 }
 
 

@@ -109,10 +109,10 @@ cudaError_t launch_ccl_merge_flatten(const Geo& g, const void* disp, size_t dp, 
                                      size_t lp, int32_t* count, int tw, int th, cudaStream_t s,
                                      Marks& mk);
 
-// Fused frame kernel (denoise, support, affine, normal, points, mask and
-// tile-local components in one pass over 32 x 16 tiles).  Star-fill with
-// M = 8, s = 10 uses compile-time rays when `star8` is set (the host checks
-// that the context's table is exactly that ray set).
+// Outputs of sn_run_frame.  The fused frame kernel writes den (when given),
+// normals, points and mask; the component passes write labels and count.
+// Star-fill with M = 8, s = 10 uses compile-time rays when `star8` is set
+// (the host checks that the context's table is exactly that ray set).
 struct FrameOut {
     float* den;  // may be null
     size_t denp;
@@ -138,7 +138,9 @@ struct GateView {
     const float* b3;
     float tau;
 };
-// gv == nullptr: plain chain; otherwise the learned variant (star M = 8, s = 10, r_d = 2).
+// The fused frame kernel alone (denoise, support, fit, normal, point, mask;
+// not the labels).  gv == nullptr: plain chain; otherwise the learned
+// variant (star M = 8, s = 10, r_d = 2).
 cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const void* disp, size_t dp,
                          const FrameOut& o, const GateView* gv, cudaStream_t s, Marks& mk);
 bool star_is_m8(const StarTable& t, int dirs, int steps);

@@ -315,6 +315,58 @@ def test_repeatable_and_den_optional(P):
         pipe.close()
 
 
+def test_streams_and_graph_capture(P):
+    # sn_run_frame forks its component passes onto a side stream of the
+    # context and joins them back: frames interleaved on three caller streams
+    # of one context, a profiled (single-stream) run and a CUDA graph capture
+    # with replay all give the oracle's results
+    scenes = [make_scene("planes_640x480", frame=f) for f in range(6)]
+    H, W = scenes[0].disp.shape
+    pipe = P.Pipeline(scenes[0].camera, W, H)
+    try:
+        disp = [pipe.upload(s.disp) for s in scenes]
+        refs = [oracle.run_frame(s.disp, s.camera, oracle_params(pipe.params)) for s in scenes]
+        outs = [pipe.buffers() for _ in scenes]
+        streams = [torch.cuda.Stream() for _ in range(3)]
+        for _ in range(3):
+            for i in range(len(scenes)):
+                pipe.run_frame(disp[i], outs[i], stream=streams[i % 3])
+        torch.cuda.synchronize()
+        P.sn.sn_check_device(pipe.ctx)
+        for o, r in zip(outs, refs):
+            compare_frame(to_host(o), r)
+
+        P.sn.sn_set_profiling(pipe.ctx, True)
+        prof = pipe.buffers()
+        pipe.run_frame(disp[1], prof)
+        torch.cuda.synchronize()
+        P.sn.sn_set_profiling(pipe.ctx, False)
+        compare_frame(to_host(prof), refs[1])
+
+        cap = [pipe.buffers() for _ in scenes]
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            g.capture_begin()
+            for i in range(len(scenes)):
+                pipe.run_frame(disp[i], cap[i], stream=side)
+            g.capture_end()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        for o in cap:
+            for t in (o.normals, o.points, o.labels, o.mask, o.num_components):
+                t.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        P.sn.sn_check_device(pipe.ctx)
+        for o, r in zip(cap, refs):
+            compare_frame(to_host(o), r)
+        del g
+    finally:
+        pipe.close()
+
+
 def test_argument_errors_on_device(P):
     s = make_scene("planes_320x240", frame=0)
     H, W = s.disp.shape
