@@ -13,6 +13,7 @@
 #include <cuda_bf16.h>
 
 #include "sn_device.cuh"
+#include "sn_umma.cuh"
 
 namespace sn {
 
@@ -442,25 +443,36 @@ __device__ __forceinline__ void fast_pixel(const Geo& g, int Dc, const WinSums& 
 // one surface (their union is the window).
 constexpr int kFastR = SN_LEARNED_RADIUS, kQM = kFastR - 2;
 static_assert(kFastR >= 3 && kFastR + 2 <= 10, "the features of the q region must lie inside the halo of 10");
-// Shared-memory layout of the learned variant (after the tile; all offsets
-// 16-byte aligned).
 constexpr int kFeatW = kTW + 2 * (kQM + 2), kFeatH = kTH + 2 * (kQM + 2);  // features: tile + kQM + 2
 constexpr int kH1W = kTW + 2 * (kQM + 1), kH1H = kTH + 2 * (kQM + 1);      // layer 1:  tile + kQM + 1
 constexpr int kQW = kTW + 2 * kQM, kQH = kTH + 2 * kQM;                    // q:        tile + kQM
-constexpr int kFeatN = kFeatW * kFeatH;     // (+ 1 zero row)
-constexpr int kH1N = kH1W * kH1H;
-constexpr int kH1Tiles = (kH1N + 15) / 16;  // m-tiles of 16 pixels
+constexpr int kFeatN = kFeatW * kFeatH;
 constexpr int kQN = kQW * kQH;
-constexpr int kQTiles = (kQN + 15) / 16;
 constexpr int kRSRows = kTH + 2 * kFastR;   // row-sum rows: tile rows -kFastR .. kTH - 1 + kFastR
 constexpr int kRS = kRSRows * kTW;          // row-sum entries per quantity
-// Layer 1 runs with K = 48: k-step s is feature row dy = s, its two 8-wide
-// halves the feature rows of positions dx = 0 and dx = 2, each of which holds
-// its own features and its right neighbour's (so dx = 1 rides along with
-// dx = 0, and the weights of the 4th pixel dx = 3 are zero).
-constexpr int kW1K = 48;
-constexpr int kW1Ld = 56, kW2Ld = 152;      // padded bf16 rows of the weights (conflict-free ldmatrix)
-constexpr int kH1Ld = 12;                   // words per layer-1 row: 16 bf16 + 16 B pad (conflict-free ldmatrix)
+// Both 3x3 convolutions run as implicit GEMMs on the tcgen05 tensor cores
+// (M = 128 rows per MMA, N = 16 channels, K = 16, BF16 in, FP32 in TMEM).
+// Every map is stored row-major with the same pitch kPitch: output row m of a
+// layer is position (m / kPitch, m % kPitch) of its map, and tap (dy, dx) of
+// it reads input row m + dy kPitch + dx, so each tap's A operand is the input
+// map at a constant offset (the columns past kH1W or kQW are computed and
+// dropped).  A map row is 16 bytes per 8 channels: the A operand's core
+// matrices are 8 consecutive rows, 128 bytes apart in M.
+constexpr int kPitch = kFeatW;
+constexpr int kM1 = kH1H * kPitch, kM2 = kQH * kPitch;            // GEMM rows of the two layers
+constexpr int kMT1 = (kM1 + 127) / 128, kMT2 = (kM2 + 127) / 128;  // 128-row MMA tiles
+// Layer 1 runs with K = 48 (3 MMAs per tile): K-step dy reads feature row
+// m + dy kPitch with its 8 channels (the position's own 4 and its right
+// neighbour's) as K 0-7 and row m + dy kPitch + 2 as K 8-15, i.e. the second
+// K core matrix lies 2 rows (32 bytes) after the first; the 4th position's
+// weights are zero.  Layer 2 runs with K = 144: K-step = tap, its channels
+// 0-7 and 8-15 in two planes of the layer-1 map.
+constexpr int kFeatPos = (kMT1 * 128 + 2 * kPitch + 2 + 7) & ~7;  // feature rows layer 1 reads
+constexpr int kH1Pos = ((kMT2 * 128 + 2 * kPitch + 2 > kMT1 * 128 ? kMT2 * 128 + 2 * kPitch + 2 : kMT1 * 128) + 7) & ~7;
+constexpr int kTmemCols = 256;              // 16 columns per MMA tile; a power of two
+static_assert(kFeatPos >= kFeatN && 16 * kMT1 <= kTmemCols && 16 * kMT2 <= kTmemCols, "learned GEMM sizes");
+constexpr uint32_t kNetIdesc = umma::idesc_bf16<128, 16>();
+constexpr int kNetSpin = 1 << 22;           // polls of an MMA completion wait before giving up
 constexpr size_t align16z(size_t b) { return (b + 15) & ~(size_t)15; }
 
 // tile (D, 1/D) (+ one ST edge byte per tile entry) of a 32 x TH tile
@@ -468,26 +480,35 @@ __host__ __device__ constexpr size_t frame_smem(int Rr, bool st = false, int TH 
     return sizeof(int2) * (size_t)(kTW + 2 * Rr) * (TH + 2 * Rr) + (st ? (size_t)(kTW + 2 * Rr) * (TH + 2 * Rr) : 0);
 }
 
+// Shared-memory layout of the learned variant (after the tile; all offsets
+// 16-byte aligned): work-list counter; mbarrier and TMEM address; b1, b2,
+// W3, b3; the B operands of the two layers (16 x 16 BF16 core-matrix blocks
+// of 512 bytes per K-step); the feature map; the two planes of the layer-1
+// map; q.
 struct LearnedSmem {
-    size_t cnt, w1, w2, feat, h1, q, end;
+    size_t cnt, bar, par, w1, w2, feat, h1, q, end;
 };
 __host__ __device__ constexpr LearnedSmem learned_layout(size_t base) {
     LearnedSmem L{};
     L.cnt = align16z(base);
-    L.w1 = align16z(L.cnt + 16);
-    L.w2 = align16z(L.w1 + 2 * 16 * kW1Ld);
-    L.feat = align16z(L.w2 + 2 * 16 * kW2Ld);
-    L.h1 = align16z(L.feat + 16 * (kFeatN + 1));
-    L.q = align16z(L.h1 + 4 * kH1Ld * 16 * kH1Tiles);
-    L.end = align16z(L.q + 4 * 16 * kQTiles);
+    L.bar = align16z(L.cnt + 16);
+    L.par = align16z(L.bar + 16);
+    L.w1 = align16z(L.par + 4 * 49);
+    L.w2 = align16z(L.w1 + 3 * 512);
+    L.feat = align16z(L.w2 + 9 * 512);
+    L.h1 = align16z(L.feat + 16 * kFeatPos);
+    L.q = align16z(L.h1 + 2 * 16 * kH1Pos);
+    L.end = align16z(L.q + 4 * kQN);
     return L;
 }
 // The q region later holds the work list (one int per tile pixel); features
 // and layer 1 later hold the row sums (10 ints per entry) and layer 1 the
-// row minima of q.
-static_assert(16 * kQTiles >= kThreads, "work list");
+// row minima of q.  Two CTAs per SM at most (each holds kTmemCols of the
+// SM's 512 TMEM columns): the shared memory of three would exceed the SM's.
+static_assert(kQN >= kThreads, "work list");
 static_assert(learned_layout(0).q - learned_layout(0).feat >= sizeof(int) * 10 * kRS, "row sums");
-static_assert(4 * kH1Ld * 16 * kH1Tiles >= sizeof(float) * kQH * kTW, "row minima of q");
+static_assert(2 * 16 * kH1Pos >= sizeof(float) * kQH * kTW, "row minima of q");
+static_assert(3 * (learned_layout(frame_smem(10)).end + 1024) > 228 * 1024 && 2 * kTmemCols <= 512, "TMEM per SM");
 
 // VAR: 0 fixed window, 1 star table, 2 compile-time M = 8, s = 10 star,
 // 3 = 2 with the learned gate, 4 star table with the ST stop.  R: halo
@@ -547,28 +568,47 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
         constexpr int TW = kTW + 2 * R;
         constexpr LearnedSmem L = learned_layout(frame_smem(R));  // the launch sizes it the same way
         int* cnt = reinterpret_cast<int*>(smem + L.cnt);
-        __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(smem + L.w1);
-        __nv_bfloat16* W2s = reinterpret_cast<__nv_bfloat16*>(smem + L.w2);
+        uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+        uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.bar + 8);
+        float* par = reinterpret_cast<float*>(smem + L.par);  // b1[16], b2[16], W3[16], b3
+        unsigned char* W1s = smem + L.w1;
+        unsigned char* W2s = smem + L.w2;
         uint4* feat = reinterpret_cast<uint4*>(smem + L.feat);
-        unsigned* h1w = reinterpret_cast<unsigned*>(smem + L.h1);  // kH1Ld words (16 bf16 + pad) per pixel
+        uint4* h1p0 = reinterpret_cast<uint4*>(smem + L.h1);                 // layer 1, channels 0-7
+        uint4* h1p1 = reinterpret_cast<uint4*>(smem + L.h1 + 16 * kH1Pos);  // channels 8-15
         float* qs = reinterpret_cast<float*>(smem + L.q);
         const int warp = tid >> 5;
-        // weights into shared memory (rows padded for conflict-free ldmatrix)
+        // TMEM for the accumulators, the MMA completion barrier
+        if (warp == 0) umma::tmem_alloc(tslot, kTmemCols);
+        if (tid == 0) umma::mbar_init(bar, 1);
+        // B operands: element (n, k) of K-step s at s 512 + (k / 8) 256 +
+        // (n / 8) 128 + (n % 8) 16 + (k % 8) 2 bytes
         {
             // W1g is [16][80] with k = tap * 8 + channel (tap = 3 dy + dx)
-            for (int i = tid; i < 16 * kW1K; i += kThreads) {
-                const int nn = i / kW1K, k = i % kW1K;
-                const int dy = k / 16, dx = 2 * ((k % 16) / 8) + ((k % 8) >= 4), ch = k % 4;
-                W1s[nn * kW1Ld + k] = (dx <= 2 && ch < 3) ? gv.W1g[nn * 80 + (3 * dy + dx) * 8 + ch]
-                                                           : __float2bfloat16(0.0f);
+            for (int i = tid; i < 16 * 48; i += kThreads) {
+                const int nn = i / 48, k = i % 48;
+                const int dy = k / 16, kk = k % 16, dx = 2 * (kk / 8) + ((kk % 8) >= 4), ch = kk % 4;
+                *reinterpret_cast<__nv_bfloat16*>(W1s + dy * 512 + (kk / 8) * 256 + (nn / 8) * 128 + (nn % 8) * 16 +
+                                                  (kk % 8) * 2) =
+                    (dx <= 2 && ch < 3) ? gv.W1g[nn * 80 + (3 * dy + dx) * 8 + ch] : __float2bfloat16(0.0f);
             }
-            const unsigned* w2 = reinterpret_cast<const unsigned*>(gv.W2g);
-            unsigned* w2s = reinterpret_cast<unsigned*>(W2s);
-            for (int i = tid; i < 16 * 72; i += kThreads) w2s[(i / 72) * (kW2Ld / 2) + i % 72] = __ldg(w2 + i);
+            // W2g is [16][144] with k = tap * 16 + channel
+            for (int i = tid; i < 16 * 144; i += kThreads) {
+                const int nn = i / 144, k = i % 144, tap = k / 16, ch = k % 16;
+                *reinterpret_cast<__nv_bfloat16*>(W2s + tap * 512 + (ch / 8) * 256 + (nn / 8) * 128 + (nn % 8) * 16 +
+                                                  (ch % 8) * 2) = gv.W2g[i];
+            }
+            if (tid < 16) {
+                par[tid] = __ldg(gv.b1 + tid);
+                par[16 + tid] = __ldg(gv.b2 + tid);
+                par[32 + tid] = __ldg(gv.W3 + tid);
+            }
+            if (tid == 0) par[48] = __ldg(gv.b3);
         }
         // features of the tile + (kQM + 2) region: position i holds its own
-        // features (channels 0-3) and its right neighbour's (4-7)
-        for (int i = tid; i <= kFeatN; i += kThreads) {
+        // features (channels 0-3) and its right neighbour's (4-7); rows past
+        // the region (read only by dropped GEMM rows) are zero
+        for (int i = tid; i < kFeatPos; i += kThreads) {
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
             if (i < kFeatN) {
                 const int fx = i % kFeatW - (kQM + 2), fy = i / kFeatW - (kQM + 2);
@@ -587,110 +627,83 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
             }
             feat[i] = v;
         }
+        for (int i = kMT1 * 128 + tid; i < kH1Pos; i += kThreads) h1p0[i] = h1p1[i] = make_uint4(0u, 0u, 0u, 0u);
         if (tid == 0) *cnt = 0;
+        umma::fence_proxy_async();
+        umma::fence_before();
         __syncthreads();
-
-        const int gq = lane >> 2, tq = lane & 3;
-        // each lane's output channels: 2 tq, 2 tq + 1 (first n-half), 8 + 2 tq, 9 + 2 tq (second)
-        const float b1a = __ldg(gv.b1 + 2 * tq), b1b = __ldg(gv.b1 + 2 * tq + 1);
-        const float b1c = __ldg(gv.b1 + 8 + 2 * tq), b1d = __ldg(gv.b1 + 9 + 2 * tq);
-        const __nv_bfloat16* w1row = W1s + ((lane & 7) + ((lane >> 4) << 3)) * kW1Ld + ((lane >> 3) & 1) * 8;
-        const __nv_bfloat16* w2row = W2s + ((lane & 7) + ((lane >> 4) << 3)) * kW2Ld + ((lane >> 3) & 1) * 8;
-        // layer 1: h1 = relu(conv3x3(feat) W1 + b1) on the tile + (kQM + 1) region; rows of
-        // the last m-tile past the region repeat its last pixel (their results are dropped).
-        // A warp takes two m-tiles at a time (independent MMA chains, shared B fragments).
-        constexpr int kWarps = kThreads / 32;
-        for (int mt0 = warp; mt0 < kH1Tiles; mt0 += 2 * kWarps) {
-            const uint4* fa[2];
-            float acc[2][2][4];
+        umma::fence_after();
+        const uint32_t tmem = *tslot;
+        const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;  // the TMEM lanes this warp may read
+        // layer 1: h1 = relu(conv3x3(feat) W1 + b1)
+        if (tid == 0) {
+            const uint32_t fa = umma::smem_addr(feat), wa = umma::smem_addr(W1s);
+            for (int t = 0; t < kMT1; t++)
 #pragma unroll
-            for (int j = 0; j < 2; j++) {
-                const int r = min((mt0 + j * kWarps) * 16 + (lane & 15), kH1N - 1);
-                const int hx = r % kH1W, hy = r / kH1W;
-                fa[j] = feat + hy * kFeatW + hx + 2 * (lane >> 4);
-                acc[j][0][0] = acc[j][0][2] = b1a;
-                acc[j][0][1] = acc[j][0][3] = b1b;
-                acc[j][1][0] = acc[j][1][2] = b1c;
-                acc[j][1][1] = acc[j][1][3] = b1d;
-            }
-#pragma unroll
-            for (int st = 0; st < 3; st++) {
-                unsigned b[4];
-                ldsm_x4(b, w1row + 16 * st);
-#pragma unroll
-                for (int j = 0; j < 2; j++) {
-                    unsigned a[4];
-                    ldsm_x4(a, fa[j] + st * kFeatW);
-                    mma_bf16(acc[j][0], a, b[0], b[1]);
-                    mma_bf16(acc[j][1], a, b[2], b[3]);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < 2; j++) {
-#pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    const int rr = (mt0 + j * kWarps) * 16 + gq + 8 * h;
-                    if (rr < kH1N) {
-                        const __nv_bfloat162 v0 =
-                            __floats2bfloat162_rn(fmaxf(acc[j][0][2 * h], 0.0f), fmaxf(acc[j][0][2 * h + 1], 0.0f));
-                        const __nv_bfloat162 v1 =
-                            __floats2bfloat162_rn(fmaxf(acc[j][1][2 * h], 0.0f), fmaxf(acc[j][1][2 * h + 1], 0.0f));
-                        h1w[rr * kH1Ld + tq] = *reinterpret_cast<const unsigned*>(&v0);
-                        h1w[rr * kH1Ld + 4 + tq] = *reinterpret_cast<const unsigned*>(&v1);
-                    }
-                }
-            }
+                for (int dy = 0; dy < 3; dy++)
+                    umma::mma<kNetIdesc>(tmem + 16 * t, umma::desc(fa + 16 * (128 * t + dy * kPitch), 32, 128),
+                                         umma::desc(wa + 512 * dy, 256, 128), dy > 0);
+            umma::commit(bar);
         }
-        __syncthreads();
-        // layer 2 and head: q = sigmoid(relu(conv3x3(h1) W2 + b2) . W3 + b3) on
-        // the tile + kQM region (rows of the last m-tile past it repeat its last
-        // pixel); two m-tiles per warp at a time, as above
-        {
-            const float b2a = __ldg(gv.b2 + 2 * tq), b2b = __ldg(gv.b2 + 2 * tq + 1);
-            const float b2c = __ldg(gv.b2 + 8 + 2 * tq), b2d = __ldg(gv.b2 + 9 + 2 * tq);
-            const float w3a = __ldg(gv.W3 + 2 * tq), w3b = __ldg(gv.W3 + 2 * tq + 1);
-            const float w3c = __ldg(gv.W3 + 8 + 2 * tq), w3d = __ldg(gv.W3 + 9 + 2 * tq);
-            const float b3 = __ldg(gv.b3);
-            for (int mt0 = warp; mt0 < kQTiles; mt0 += 2 * kWarps) {
-                const unsigned* ha[2];
-                float acc[2][2][4];
+        bool net_ok = __syncthreads_and(umma::mbar_wait(bar, 0, kNetSpin));
+        umma::fence_after();
+        if (net_ok) {
+            for (int t = warp >> 2; t < kMT1; t += kThreads / 128) {
+                uint32_t r[16];
+                umma::ld16(tmem + tlane + 16 * t, r);
+                umma::wait_ld();
+                unsigned w[8];
 #pragma unroll
-                for (int j = 0; j < 2; j++) {
-                    const int r = min((mt0 + j * kWarps) * 16 + (lane & 15), kQN - 1);
-                    const int qx = r % kQW, qy = r / kQW;
-                    ha[j] = h1w + (qy * kH1W + qx) * kH1Ld + (lane >> 4) * 4;
-                    acc[j][0][0] = acc[j][0][2] = b2a;
-                    acc[j][0][1] = acc[j][0][3] = b2b;
-                    acc[j][1][0] = acc[j][1][2] = b2c;
-                    acc[j][1][1] = acc[j][1][3] = b2d;
+                for (int c = 0; c < 8; c++) {
+                    const __nv_bfloat162 v = __floats2bfloat162_rn(fmaxf(__uint_as_float(r[2 * c]) + par[2 * c], 0.0f),
+                                                                   fmaxf(__uint_as_float(r[2 * c + 1]) + par[2 * c + 1], 0.0f));
+                    w[c] = *reinterpret_cast<const unsigned*>(&v);
                 }
-#pragma unroll
-                for (int tap = 0; tap < 9; tap++) {
-                    unsigned b[4];
-                    ldsm_x4(b, w2row + 16 * tap);
-#pragma unroll
-                    for (int j = 0; j < 2; j++) {
-                        unsigned a[4];
-                        ldsm_x4(a, ha[j] + ((tap / 3) * kH1W + tap % 3) * kH1Ld);
-                        mma_bf16(acc[j][0], a, b[0], b[1]);
-                        mma_bf16(acc[j][1], a, b[2], b[3]);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < 2; j++) {
-                    const int mt = mt0 + j * kWarps;
-#pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        float part = w3a * fmaxf(acc[j][0][2 * h], 0.0f) + w3b * fmaxf(acc[j][0][2 * h + 1], 0.0f) +
-                                     w3c * fmaxf(acc[j][1][2 * h], 0.0f) + w3d * fmaxf(acc[j][1][2 * h + 1], 0.0f);
-                        part += __shfl_xor_sync(0xffffffffu, part, 1);
-                        part += __shfl_xor_sync(0xffffffffu, part, 2);
-                        if (tq == 0 && mt < kQTiles) qs[mt * 16 + gq + 8 * h] = 1.0f / (1.0f + __expf(-(part + b3)));
-                    }
-                }
+                const int j = 128 * t + (warp & 3) * 32 + lane;
+                h1p0[j] = make_uint4(w[0], w[1], w[2], w[3]);
+                h1p1[j] = make_uint4(w[4], w[5], w[6], w[7]);
             }
+            umma::fence_proxy_async();
+            umma::fence_before();
+            __syncthreads();
+            umma::fence_after();
+            // layer 2 and head: q = sigmoid(relu(conv3x3(h1) W2 + b2) . W3 + b3)
+            if (tid == 0) {
+                const uint32_t ha = umma::smem_addr(h1p0), wa = umma::smem_addr(W2s);
+                for (int t = 0; t < kMT2; t++)
+#pragma unroll
+                    for (int tap = 0; tap < 9; tap++)
+                        umma::mma<kNetIdesc>(
+                            tmem + 16 * t, umma::desc(ha + 16 * (128 * t + (tap / 3) * kPitch + tap % 3), 16 * kH1Pos, 128),
+                            umma::desc(wa + 512 * tap, 256, 128), tap > 0);
+                umma::commit(bar);
+            }
+            net_ok = __syncthreads_and(umma::mbar_wait(bar, 1, kNetSpin));
+            umma::fence_after();
+            if (net_ok) {
+                for (int t = warp >> 2; t < kMT2; t += kThreads / 128) {
+                    uint32_t r[16];
+                    umma::ld16(tmem + tlane + 16 * t, r);
+                    umma::wait_ld();
+                    float part = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < 16; c++) part = fmaf(par[32 + c], fmaxf(__uint_as_float(r[c]) + par[16 + c], 0.0f), part);
+                    const int j = 128 * t + (warp & 3) * 32 + lane, qy = j / kPitch, qx = j - qy * kPitch;
+                    if (qy < kQH && qx < kQW) qs[qy * kQW + qx] = 1.0f / (1.0f + __expf(-(part + par[48])));
+                }
+            } else {
+                umma::mbar_wait(bar, 1, kNetSpin);  // gave up: let the MMAs in flight drain (bounded)
+            }
+        } else {
+            umma::mbar_wait(bar, 0, kNetSpin);  // gave up: let the MMAs in flight drain (bounded)
         }
+        if (!net_ok && tid == 0) atomicOr(g.err, kErrMmaWait);
+        umma::fence_before();
         __syncthreads();
+        if (warp == 0) {
+            umma::fence_after();
+            umma::tmem_dealloc(tmem, kTmemCols);
+        }
         // gate: min of q over the (2 kQM + 1)^2 neighbourhood >= tau, as a
         // row pass (into the dead layer-1 region) and a column pass
         float* qrow = reinterpret_cast<float*>(smem + L.h1);
@@ -707,7 +720,7 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
             float qmin = qrow[row * kTW + lane];
 #pragma unroll
             for (int oy = 1; oy <= 2 * kQM; oy++) qmin = fminf(qmin, qrow[(row + oy) * kTW + lane]);
-            gated = qmin >= gv.tau;
+            gated = net_ok && qmin >= gv.tau;  // no pixel is certified if the network did not finish
         }
         const bool any = __syncthreads_or(gated);
         int* rs = reinterpret_cast<int*>(smem + L.feat);  // features and layer 1 are dead: row sums
