@@ -28,6 +28,7 @@ struct sn_ctx {
     bool star8;  // the star table is the compile-time M = 8, s = 10 ray set
     sn::GateDev gate;    // learned gate weights (learned contexts)
     float* gate_theta;   // their FP32 source on the device
+    void* net_img;       // the weights as the frame kernel's shared memory holds them
     bool gate_loaded;
     bool prof;
     cudaEvent_t* ev;  // kProfFrames x (kStages + 1)
@@ -336,6 +337,7 @@ sn_status sn_create(const sn_camera* cam, int W, int H, const sn_params* pin, sn
     if (e == cudaSuccess && p.learned) {
         e = sn::gate_alloc(c->gate);
         if (e == cudaSuccess) e = cudaMalloc(&c->gate_theta, sizeof(float) * sn::kGateParams);
+        if (e == cudaSuccess) e = cudaMalloc(&c->net_img, sn::kNetImageBytes);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -363,6 +365,7 @@ sn_status sn_destroy(sn_ctx* c) {
     if (c->ws.den) cudaFree(c->ws.den);
     if (c->gate.W1g) sn::gate_free(c->gate);
     if (c->gate_theta) cudaFree(c->gate_theta);
+    if (c->net_img) cudaFree(c->net_img);
     delete c;
     return SN_OK;
 }
@@ -489,7 +492,8 @@ sn_status sn_run_frame(sn_ctx* c, const sn_frame_in* in, sn_frame_out* out, sn_s
     sn::GateView gv{};
     if (c->p.learned) {
         if (!c->gate_loaded) return fail(c, SN_EINVAL, "learned context: gate weights not loaded");
-        gv = sn::GateView{c->gate.W1g, c->gate.W2g, c->gate.b1, c->gate.b2, c->gate.W3, c->gate.b3, c->p.tau};
+        gv = sn::GateView{c->gate.W1g, c->gate.W2g, c->gate.b1, c->gate.b2, c->gate.W3, c->gate.b3, c->p.tau,
+                          c->net_img};
     }
     const sn::GateView* g = c->p.learned ? &gv : nullptr;
     cudaError_t e;
@@ -534,6 +538,11 @@ sn_status sn_load_gate_weights(sn_ctx* c, const void* blob, size_t bytes) {
         return fail(c, SN_EINVAL, "not a version-1 gate weights blob of the expected size");
     cudaError_t e = cudaMemcpy(c->gate_theta, b + 12, sizeof(float) * sn::kGateParams, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = sn::gate_layout(c->gate_theta, c->gate, nullptr);
+    if (e == cudaSuccess) {
+        const sn::GateView gv{c->gate.W1g, c->gate.W2g, c->gate.b1, c->gate.b2, c->gate.W3, c->gate.b3, c->p.tau,
+                              nullptr};
+        e = sn::launch_net_image(gv, c->net_img, nullptr);
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(c, e, "sn_load_gate_weights");
     c->gate_loaded = true;

@@ -104,30 +104,34 @@ __device__ __noinline__ void ray8_exact_tail(const int2* __restrict__ c, int Dc,
 // One ray of the M = 8 star with direction (SU, SV) and L distinct pixels
 // t (SU, SV), t = 1..L.  All L samples are loaded first; the walk is
 // branch-free: a step is taken while the spread is surely below the
-// threshold, and the spread of the first step that is not is kept.  Only if
-// that spread lies inside the rounding band does the exact test decide (and
-// possibly continue the ray).  The data enters as A = sum t D over the
-// included pixels; the moments of the included prefix 1..n are closed forms.
+// threshold.  The running extremes stop moving after the first step that is
+// not taken (the spread only grows, so no later step is taken either), so
+// after the walk they give the spread of that step.  Only if it lies inside
+// the rounding band does the exact test decide (and possibly continue the
+// ray).  The data enters as A = sum t D over the included pixels; the
+// moments of the included prefix 1..n are closed forms.
 template <int SU, int SV, int L, int STRIDE>
 __device__ __forceinline__ void ray8(const int2* __restrict__ c, int Dc, float wc, const Thr& th, AffSums& s) {
     int2 e[L];
 #pragma unroll
     for (int t = 1; t <= L; t++) e[t - 1] = c[(SV * t) * STRIDE + SU * t];
-    float wlo = wc, whi = wc, fdiff = 0.0f;
+    float wlo = wc, whi = wc;
     int A = 0, n = 0;
     bool alive = true;
 #pragma unroll
     for (int t = 1; t <= L; t++) {
         const float w = __int_as_float(e[t - 1].y);
-        wlo = fminf(wlo, w);
-        whi = fmaxf(whi, w);
-        const float diff = whi - wlo;
-        fdiff = alive ? diff : fdiff;
-        alive = alive && diff < th.lo;
-        A += alive ? t * e[t - 1].x : 0;
-        n += alive ? 1 : 0;
+        if (alive) {
+            wlo = fminf(wlo, w);
+            whi = fmaxf(whi, w);
+        }
+        alive = whi - wlo < th.lo;
+        if (alive) {
+            A += t * e[t - 1].x;
+            n++;
+        }
     }
-    if (n < L && !(fdiff > th.hi)) ray8_exact_tail<SU, SV, L, STRIDE>(c, Dc, th.K, &n, &A);
+    if (n < L && !(whi - wlo > th.hi)) ray8_exact_tail<SU, SV, L, STRIDE>(c, Dc, th.K, &n, &A);
     const int T1 = (n * (n + 1)) >> 1;
     const int T2 = (n * (n + 1) * (2 * n + 1)) / 6;
     const int Ad = A - Dc * T1;
@@ -491,8 +495,8 @@ struct LearnedSmem {
 __host__ __device__ constexpr LearnedSmem learned_layout(size_t base) {
     LearnedSmem L{};
     L.cnt = align16z(base);
-    L.bar = align16z(L.cnt + 16);
-    L.par = align16z(L.bar + 16);
+    L.bar = align16z(L.cnt + 16);  // MMA barrier, weights barrier, TMEM address
+    L.par = align16z(L.bar + 32);
     L.w1 = align16z(L.par + 4 * 49);
     L.w2 = align16z(L.w1 + 3 * 512);
     L.feat = align16z(L.w2 + 9 * 512);
@@ -509,6 +513,39 @@ static_assert(kQN >= kThreads, "work list");
 static_assert(learned_layout(0).q - learned_layout(0).feat >= sizeof(int) * 10 * kRS, "row sums");
 static_assert(2 * 16 * kH1Pos >= sizeof(float) * kQH * kTW, "row minima of q");
 static_assert(3 * (learned_layout(frame_smem(10)).end + 1024) > 228 * 1024 && 2 * kTmemCols <= 512, "TMEM per SM");
+// b1, b2, W3, b3 and the two B operands are one contiguous block, copied
+// whole from the image launch_net_image writes
+static_assert(learned_layout(0).w1 - learned_layout(0).par == 208 &&
+                  learned_layout(0).feat - learned_layout(0).par == (size_t)kNetImageBytes,
+              "weights image layout");
+
+// The image: b1, b2, W3, b3 (FP32), then the B operands, element (n, k) of
+// K-step s at s 512 + (k / 8) 256 + (n / 8) 128 + (n % 8) 16 + (k % 8) 2
+// bytes (16 x 16 BF16 in 8 x 16-byte core matrices).  Layer 1, K-step dy:
+// k 0-7 weigh the feature row of position dx = 0 (its channels 0-3) and its
+// right neighbour dx = 1 (4-7), k 8-15 position dx = 2 and dx = 3 (zero).
+__global__ void k_net_image(const GateView gv, unsigned char* __restrict__ img) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float* par = reinterpret_cast<float*>(img);
+    unsigned char* W1s = img + 208;
+    unsigned char* W2s = img + 208 + 3 * 512;
+    if (i < 52) par[i] = i < 16 ? gv.b1[i] : i < 32 ? gv.b2[i - 16] : i < 48 ? gv.W3[i - 32] : i == 48 ? gv.b3[0] : 0.0f;
+    if (i < 16 * 48) {
+        // W1g is [16][80] with k = tap * 8 + channel (tap = 3 dy + dx)
+        const int nn = i / 48, k = i % 48;
+        const int dy = k / 16, kk = k % 16, dx = 2 * (kk / 8) + ((kk % 8) >= 4), ch = kk % 4;
+        *reinterpret_cast<__nv_bfloat16*>(W1s + dy * 512 + (kk / 8) * 256 + (nn / 8) * 128 + (nn % 8) * 16 +
+                                          (kk % 8) * 2) =
+            (dx <= 2 && ch < 3) ? gv.W1g[nn * 80 + (3 * dy + dx) * 8 + ch] : __float2bfloat16(0.0f);
+    }
+    if (i < 16 * 144) {
+        // W2g is [16][144] with k = tap * 16 + channel
+        const int nn = i / 144, k = i % 144, tap = k / 16, ch = k % 16;
+        *reinterpret_cast<__nv_bfloat16*>(W2s + tap * 512 + (ch / 8) * 256 + (nn / 8) * 128 + (nn % 8) * 16 +
+                                          (ch % 8) * 2) = gv.W2g[i];
+    }
+}
+
 
 // VAR: 0 fixed window, 1 star table, 2 compile-time M = 8, s = 10 star,
 // 3 = 2 with the learned gate, 4 star table with the ST stop.  R: halo
@@ -568,43 +605,27 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
         constexpr int TW = kTW + 2 * R;
         constexpr LearnedSmem L = learned_layout(frame_smem(R));  // the launch sizes it the same way
         int* cnt = reinterpret_cast<int*>(smem + L.cnt);
-        uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
-        uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.bar + 8);
-        float* par = reinterpret_cast<float*>(smem + L.par);  // b1[16], b2[16], W3[16], b3
-        unsigned char* W1s = smem + L.w1;
-        unsigned char* W2s = smem + L.w2;
+        uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);       // MMA completion
+        uint64_t* wbar = reinterpret_cast<uint64_t*>(smem + L.bar + 8);  // weights copy
+        uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.bar + 16);
+        const float* par = reinterpret_cast<const float*>(smem + L.par);  // b1[16], b2[16], W3[16], b3
+        const unsigned char* W1s = smem + L.w1;
+        const unsigned char* W2s = smem + L.w2;
         uint4* feat = reinterpret_cast<uint4*>(smem + L.feat);
         uint4* h1p0 = reinterpret_cast<uint4*>(smem + L.h1);                 // layer 1, channels 0-7
         uint4* h1p1 = reinterpret_cast<uint4*>(smem + L.h1 + 16 * kH1Pos);  // channels 8-15
         float* qs = reinterpret_cast<float*>(smem + L.q);
         const int warp = tid >> 5;
-        // TMEM for the accumulators, the MMA completion barrier
+        // TMEM for the accumulators; the barriers; the weights (biases, head
+        // and both B operands) by one bulk copy, overlapped with the features
         if (warp == 0) umma::tmem_alloc(tslot, kTmemCols);
-        if (tid == 0) umma::mbar_init(bar, 1);
-        // B operands: element (n, k) of K-step s at s 512 + (k / 8) 256 +
-        // (n / 8) 128 + (n % 8) 16 + (k % 8) 2 bytes
-        {
-            // W1g is [16][80] with k = tap * 8 + channel (tap = 3 dy + dx)
-            for (int i = tid; i < 16 * 48; i += kThreads) {
-                const int nn = i / 48, k = i % 48;
-                const int dy = k / 16, kk = k % 16, dx = 2 * (kk / 8) + ((kk % 8) >= 4), ch = kk % 4;
-                *reinterpret_cast<__nv_bfloat16*>(W1s + dy * 512 + (kk / 8) * 256 + (nn / 8) * 128 + (nn % 8) * 16 +
-                                                  (kk % 8) * 2) =
-                    (dx <= 2 && ch < 3) ? gv.W1g[nn * 80 + (3 * dy + dx) * 8 + ch] : __float2bfloat16(0.0f);
-            }
-            // W2g is [16][144] with k = tap * 16 + channel
-            for (int i = tid; i < 16 * 144; i += kThreads) {
-                const int nn = i / 144, k = i % 144, tap = k / 16, ch = k % 16;
-                *reinterpret_cast<__nv_bfloat16*>(W2s + tap * 512 + (ch / 8) * 256 + (nn / 8) * 128 + (nn % 8) * 16 +
-                                                  (ch % 8) * 2) = gv.W2g[i];
-            }
-            if (tid < 16) {
-                par[tid] = __ldg(gv.b1 + tid);
-                par[16 + tid] = __ldg(gv.b2 + tid);
-                par[32 + tid] = __ldg(gv.W3 + tid);
-            }
-            if (tid == 0) par[48] = __ldg(gv.b3);
+        if (tid == 0) {
+            umma::mbar_init(bar, 1);
+            umma::mbar_init(wbar, 1);
+            umma::mbar_expect_tx(wbar, kNetImageBytes);
+            umma::bulk_g2s(smem + L.par, gv.net, kNetImageBytes, wbar);
         }
+        __syncthreads();  // no thread polls a barrier before it is initialised
         // features of the tile + (kQM + 2) region: position i holds its own
         // features (channels 0-3) and its right neighbour's (4-7); rows past
         // the region (read only by dropped GEMM rows) are zero
@@ -629,14 +650,15 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
         }
         for (int i = kMT1 * 128 + tid; i < kH1Pos; i += kThreads) h1p0[i] = h1p1[i] = make_uint4(0u, 0u, 0u, 0u);
         if (tid == 0) *cnt = 0;
+        bool net_ok = umma::mbar_wait(wbar, 0, kNetSpin);
         umma::fence_proxy_async();
         umma::fence_before();
-        __syncthreads();
+        net_ok = __syncthreads_and(net_ok);
         umma::fence_after();
         const uint32_t tmem = *tslot;
         const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;  // the TMEM lanes this warp may read
         // layer 1: h1 = relu(conv3x3(feat) W1 + b1)
-        if (tid == 0) {
+        if (net_ok && tid == 0) {
             const uint32_t fa = umma::smem_addr(feat), wa = umma::smem_addr(W1s);
             for (int t = 0; t < kMT1; t++)
 #pragma unroll
@@ -645,7 +667,8 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
                                          umma::desc(wa + 512 * dy, 256, 128), dy > 0);
             umma::commit(bar);
         }
-        bool net_ok = __syncthreads_and(umma::mbar_wait(bar, 0, kNetSpin));
+        const bool weights_ok = net_ok;
+        net_ok = net_ok && __syncthreads_and(umma::mbar_wait(bar, 0, kNetSpin));
         umma::fence_after();
         if (net_ok) {
             for (int t = warp >> 2; t < kMT1; t += kThreads / 128) {
@@ -694,8 +717,10 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
             } else {
                 umma::mbar_wait(bar, 1, kNetSpin);  // gave up: let the MMAs in flight drain (bounded)
             }
-        } else {
+        } else if (weights_ok) {
             umma::mbar_wait(bar, 0, kNetSpin);  // gave up: let the MMAs in flight drain (bounded)
+        } else {
+            umma::mbar_wait(wbar, 0, kNetSpin);  // gave up: let the weights copy drain (bounded)
         }
         if (!net_ok && tid == 0) atomicOr(g.err, kErrMmaWait);
         umma::fence_before();
@@ -968,6 +993,11 @@ bool star_is_m8(const StarTable& t, int dirs, int steps) {
         if (tpos != len[j]) return false;
     }
     return true;
+}
+
+cudaError_t launch_net_image(const GateView& gv, void* img, cudaStream_t s) {
+    k_net_image<<<(16 * 144 + 255) / 256, 256, 0, s>>>(gv, static_cast<unsigned char*>(img));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const void* disp, size_t dp,

@@ -138,7 +138,15 @@ struct GateView {
     const float* W3;
     const float* b3;
     float tau;
+    // The same weights as the frame kernel's shared memory holds them
+    // (kNetImageBytes, written by launch_net_image): b1, b2, W3, b3 (FP32,
+    // padded to 208 bytes), then the B operands of the two convolutions in
+    // tcgen05 core-matrix layout (3 and 9 K-steps of 512 bytes).
+    const void* net;
 };
+constexpr int kNetImageBytes = 208 + 3 * 512 + 9 * 512;
+// Builds the image `net` from the other GateView fields.
+cudaError_t launch_net_image(const GateView& gv, void* img, cudaStream_t s);
 // The fused frame kernel alone (denoise, support, fit, normal, point, mask;
 // not the labels).  gv == nullptr: plain chain; otherwise the learned
 // variant (star M = 8, s = 10, r_d = 2).

@@ -1,7 +1,8 @@
 // Fifth-generation tensor core (tcgen05) primitives used by the learned
 // gate's convolutions: shared-memory matrix descriptors, the instruction
-// descriptor of a BF16 x BF16 -> FP32 MMA, MMA issue and commit, mbarrier
-// init and bounded wait, and tensor-memory (TMEM) allocation and loads.
+// descriptor of a BF16 x BF16 -> FP32 MMA, MMA issue and commit, bulk
+// global -> shared copies, mbarrier init, transaction counts and bounded
+// wait, and tensor-memory (TMEM) allocation and loads.
 // sm_100-family PTX (compiled for sm_103a).
 #pragma once
 
@@ -52,6 +53,22 @@ __device__ __forceinline__ void commit(uint64_t* mbar) {
 __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One arrival on the mbarrier that also expects `bytes` of asynchronous
+// copies to land before its phase completes.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16),
+// completing on the mbarrier's transaction count.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+                 : "memory");
 }
 
 // Waits for the phase with the given parity to complete, for at most
