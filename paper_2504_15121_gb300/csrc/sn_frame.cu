@@ -474,7 +474,8 @@ constexpr int kMT1 = (kM1 + 127) / 128, kMT2 = (kM2 + 127) / 128;  // 128-row MM
 constexpr int kFeatPos = (kMT1 * 128 + 2 * kPitch + 2 + 7) & ~7;  // feature rows layer 1 reads
 constexpr int kH1Pos = ((kMT2 * 128 + 2 * kPitch + 2 > kMT1 * 128 ? kMT2 * 128 + 2 * kPitch + 2 : kMT1 * 128) + 7) & ~7;
 constexpr int kTmemCols = 256;              // 16 columns per MMA tile; a power of two
-static_assert(kFeatPos >= kFeatN && 16 * kMT1 <= kTmemCols && 16 * kMT2 <= kTmemCols, "learned GEMM sizes");
+static_assert(kFeatPos >= kFeatN && 16 * kMT1 <= kTmemCols && kMT2 == kMT1 && kMT1 <= kThreads / 32,
+              "learned GEMM sizes: one issuing warp per tile of both layers");
 constexpr uint32_t kNetIdesc = umma::idesc_bf16<128, 16>();
 constexpr int kNetSpin = 1 << 22;           // polls of an MMA completion wait before giving up
 constexpr size_t align16z(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -495,8 +496,8 @@ struct LearnedSmem {
 __host__ __device__ constexpr LearnedSmem learned_layout(size_t base) {
     LearnedSmem L{};
     L.cnt = align16z(base);
-    L.bar = align16z(L.cnt + 16);  // MMA barrier, weights barrier, TMEM address
-    L.par = align16z(L.bar + 32);
+    L.bar = align16z(L.cnt + 16);  // weights barrier, TMEM address, one MMA barrier per 128-row tile
+    L.par = align16z(L.bar + 16 + 8 * kMT1);
     L.w1 = align16z(L.par + 4 * 49);
     L.w2 = align16z(L.w1 + 3 * 512);
     L.feat = align16z(L.w2 + 9 * 512);
@@ -605,9 +606,10 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
         constexpr int TW = kTW + 2 * R;
         constexpr LearnedSmem L = learned_layout(frame_smem(R));  // the launch sizes it the same way
         int* cnt = reinterpret_cast<int*>(smem + L.cnt);
-        uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);       // MMA completion
-        uint64_t* wbar = reinterpret_cast<uint64_t*>(smem + L.bar + 8);  // weights copy
-        uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.bar + 16);
+        uint64_t* wbar = reinterpret_cast<uint64_t*>(smem + L.bar);  // weights copy
+        uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.bar + 8);
+        // tile t's MMAs: layer 1 completes phase 0, layer 2 phase 1
+        uint64_t* tbar = reinterpret_cast<uint64_t*>(smem + L.bar + 16);
         const float* par = reinterpret_cast<const float*>(smem + L.par);  // b1[16], b2[16], W3[16], b3
         const unsigned char* W1s = smem + L.w1;
         const unsigned char* W2s = smem + L.w2;
@@ -620,7 +622,7 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
         // and both B operands) by one bulk copy, overlapped with the features
         if (warp == 0) umma::tmem_alloc(tslot, kTmemCols);
         if (tid == 0) {
-            umma::mbar_init(bar, 1);
+            for (int t = 0; t < kMT1; t++) umma::mbar_init(tbar + t, 1);
             umma::mbar_init(wbar, 1);
             umma::mbar_expect_tx(wbar, kNetImageBytes);
             umma::bulk_g2s(smem + L.par, gv.net, kNetImageBytes, wbar);
@@ -657,21 +659,25 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
         umma::fence_after();
         const uint32_t tmem = *tslot;
         const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;  // the TMEM lanes this warp may read
-        // layer 1: h1 = relu(conv3x3(feat) W1 + b1)
-        if (net_ok && tid == 0) {
-            const uint32_t fa = umma::smem_addr(feat), wa = umma::smem_addr(W1s);
-            for (int t = 0; t < kMT1; t++)
+        // layer 1: h1 = relu(conv3x3(feat) W1 + b1).  Lane 0 of warp t issues
+        // tile t's MMAs and commits them to tbar[t]; the epilogue of a tile
+        // starts as soon as its own MMAs are done.  A descriptor's start
+        // field counts 16-byte rows, so a tap offset is added to it directly.
+        const bool issued1 = net_ok;
+        if (net_ok && lane == 0 && warp < kMT1) {
+            const uint64_t a0 = umma::desc(umma::smem_addr(feat + 128 * warp), 32, 128);
+            const uint64_t b0 = umma::desc(umma::smem_addr(W1s), 256, 128);
 #pragma unroll
-                for (int dy = 0; dy < 3; dy++)
-                    umma::mma<kNetIdesc>(tmem + 16 * t, umma::desc(fa + 16 * (128 * t + dy * kPitch), 32, 128),
-                                         umma::desc(wa + 512 * dy, 256, 128), dy > 0);
-            umma::commit(bar);
+            for (int dy = 0; dy < 3; dy++)
+                umma::mma<kNetIdesc>(tmem + 16 * warp, a0 + dy * kPitch, b0 + 32 * dy, dy > 0);
+            umma::commit(tbar + warp);
         }
-        const bool weights_ok = net_ok;
-        net_ok = net_ok && __syncthreads_and(umma::mbar_wait(bar, 0, kNetSpin));
-        umma::fence_after();
+        bool ok = true;
         if (net_ok) {
             for (int t = warp >> 2; t < kMT1; t += kThreads / 128) {
+                ok = __all_sync(0xffffffffu, ok && umma::mbar_wait(tbar + t, 0, kNetSpin));  // warp-uniform
+                umma::fence_after();
+                if (!ok) break;
                 uint32_t r[16];
                 umma::ld16(tmem + tlane + 16 * t, r);
                 umma::wait_ld();
@@ -688,39 +694,45 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
             }
             umma::fence_proxy_async();
             umma::fence_before();
-            __syncthreads();
+            net_ok = __syncthreads_and(ok);
             umma::fence_after();
-            // layer 2 and head: q = sigmoid(relu(conv3x3(h1) W2 + b2) . W3 + b3)
-            if (tid == 0) {
-                const uint32_t ha = umma::smem_addr(h1p0), wa = umma::smem_addr(W2s);
-                for (int t = 0; t < kMT2; t++)
+        }
+        // layer 2 and head: q = sigmoid(relu(conv3x3(h1) W2 + b2) . W3 + b3)
+        const bool issued2 = net_ok;
+        if (net_ok && lane == 0 && warp < kMT2) {
+            const uint64_t a0 = umma::desc(umma::smem_addr(h1p0 + 128 * warp), 16 * kH1Pos, 128);
+            const uint64_t b0 = umma::desc(umma::smem_addr(W2s), 256, 128);
 #pragma unroll
-                    for (int tap = 0; tap < 9; tap++)
-                        umma::mma<kNetIdesc>(
-                            tmem + 16 * t, umma::desc(ha + 16 * (128 * t + (tap / 3) * kPitch + tap % 3), 16 * kH1Pos, 128),
-                            umma::desc(wa + 512 * tap, 256, 128), tap > 0);
-                umma::commit(bar);
-            }
-            net_ok = __syncthreads_and(umma::mbar_wait(bar, 1, kNetSpin));
-            umma::fence_after();
-            if (net_ok) {
-                for (int t = warp >> 2; t < kMT2; t += kThreads / 128) {
-                    uint32_t r[16];
-                    umma::ld16(tmem + tlane + 16 * t, r);
-                    umma::wait_ld();
-                    float part = 0.0f;
+            for (int tap = 0; tap < 9; tap++)
+                umma::mma<kNetIdesc>(tmem + 16 * warp, a0 + (tap / 3) * kPitch + tap % 3, b0 + 32 * tap, tap > 0);
+            umma::commit(tbar + warp);
+        }
+        if (net_ok) {
+            for (int t = warp >> 2; t < kMT2; t += kThreads / 128) {
+                ok = __all_sync(0xffffffffu, ok && umma::mbar_wait(tbar + t, 1, kNetSpin));  // warp-uniform
+                umma::fence_after();
+                if (!ok) break;
+                uint32_t r[16];
+                umma::ld16(tmem + tlane + 16 * t, r);
+                umma::wait_ld();
+                float part = 0.0f;
 #pragma unroll
-                    for (int c = 0; c < 16; c++) part = fmaf(par[32 + c], fmaxf(__uint_as_float(r[c]) + par[16 + c], 0.0f), part);
-                    const int j = 128 * t + (warp & 3) * 32 + lane, qy = j / kPitch, qx = j - qy * kPitch;
-                    if (qy < kQH && qx < kQW) qs[qy * kQW + qx] = 1.0f / (1.0f + __expf(-(part + par[48])));
-                }
-            } else {
-                umma::mbar_wait(bar, 1, kNetSpin);  // gave up: let the MMAs in flight drain (bounded)
+                for (int c = 0; c < 16; c++) part = fmaf(par[32 + c], fmaxf(__uint_as_float(r[c]) + par[16 + c], 0.0f), part);
+                const int j = 128 * t + (warp & 3) * 32 + lane, qy = j / kPitch, qx = j - qy * kPitch;
+                if (qy < kQH && qx < kQW) qs[qy * kQW + qx] = 1.0f / (1.0f + __expf(-(part + par[48])));
             }
-        } else if (weights_ok) {
-            umma::mbar_wait(bar, 0, kNetSpin);  // gave up: let the MMAs in flight drain (bounded)
-        } else {
-            umma::mbar_wait(wbar, 0, kNetSpin);  // gave up: let the weights copy drain (bounded)
+            net_ok = __syncthreads_and(ok);
+        }
+        if (!net_ok) {
+            // gave up: let what is in flight drain (bounded) before the TMEM is
+            // freed; the last committed phase implies the earlier one
+            for (int t = 0; t < kMT1; t++) {
+                if (issued2)
+                    umma::mbar_wait(tbar + t, 1, kNetSpin);
+                else if (issued1)
+                    umma::mbar_wait(tbar + t, 0, kNetSpin);
+            }
+            if (!issued1) umma::mbar_wait(wbar, 0, kNetSpin);
         }
         if (!net_ok && tid == 0) atomicOr(g.err, kErrMmaWait);
         umma::fence_before();
