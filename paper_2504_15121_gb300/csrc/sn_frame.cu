@@ -10,7 +10,10 @@
 // test, which in reciprocal form reads 1/Dmin - 1/Dmax > K / (2^16 Dc).
 #include <atomic>
 
+#include <cuda.h>  // CUtensorMap (the encoder is reached through the runtime's driver entry point)
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+#include <mutex>
 
 #include "sn_device.cuh"
 #include "sn_umma.cuh"
@@ -548,6 +551,30 @@ __global__ void k_net_image(const GateView gv, unsigned char* __restrict__ img) 
 }
 
 
+// Tile staging by TMA (variants with a compile-time halo R): one 2-D tensor
+// copy brings the raw disparity box into shared memory, then each thread
+// converts entries to (D, 1/D).  The box starts at x0 - kTmaXPad (a 16-byte
+// boundary: x0 is a multiple of 32) and is kTmaBW wide, so tile column lx
+// (image column x0 - R + lx) is box column lx + kTmaXPad - R; rows y0 - R
+// .. y0 + TH + R - 1.  Outside the image the box reads zero (code 0).
+template <int IN> constexpr int tma_esize() { return IN == SN_IN_F32 ? 4 : 2; }
+template <int IN> constexpr int tma_xpad() { return IN == SN_IN_F32 ? 12 : 16; }
+template <int IN, int R, int TWR> constexpr int tma_bw() {
+    return (tma_xpad<IN>() - R + TWR + 16 / tma_esize<IN>() - 1) / (16 / tma_esize<IN>()) * (16 / tma_esize<IN>());
+}
+constexpr bool frame_tma(int VAR, int R) { return R > 0 && (VAR == 2 || VAR == 3); }
+constexpr size_t align128z(size_t b) { return (b + 127) & ~(size_t)127; }
+// Offset and size of the raw box (then its 8-byte mbarrier) after the
+// variant's other shared memory.
+template <int IN, int VAR, int R>
+__host__ __device__ constexpr size_t tma_raw_off() {
+    return align128z(VAR == 3 ? learned_layout(frame_smem(R)).end : frame_smem(R, false, frame_th(VAR)));
+}
+template <int IN, int VAR, int R>
+__host__ __device__ constexpr int tma_raw_bytes() {
+    return tma_bw<IN, R, kTW + 2 * R>() * (frame_th(VAR) + 2 * R) * tma_esize<IN>();
+}
+
 // VAR: 0 fixed window, 1 star table, 2 compile-time M = 8, s = 10 star,
 // 3 = 2 with the learned gate, 4 star table with the ST stop.  R: halo
 // radius at compile time (0 = runtime).
@@ -555,7 +582,7 @@ __global__ void k_net_image(const GateView gv, unsigned char* __restrict__ img) 
 template <int IN, int VAR, int R, int RD>
 __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR)))
     k_frame(const Geo g, const __grid_constant__ StarTable T, const char* __restrict__ disp, size_t dp,
-            const FrameOut o, const GateView gv) {
+            const FrameOut o, const GateView gv, const __grid_constant__ CUtensorMap dmap) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int TH = frame_th(VAR), NT = kTW * TH;
     static_assert(VAR != 3 || TH == kTH, "the learned layout is laid out for kTH-row tiles");
@@ -569,12 +596,47 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
 
     // ---- stage the tile and its halo: (D, 1/D)
     const int n = TWR * THR;
-    for (int i = tid; i < n; i += NT) {
-        const int ly = i / TWR;
-        const int lx = i - ly * TWR;
-        const int D = load_code<IN>(disp, dp, x0 - Rr + lx, y0 - Rr + ly, g.W, g.H);
-        const float w = D > 0 ? rcp_approx((float)D) : __int_as_float(0x7f800000);
-        tile[i] = make_int2(D, __float_as_int(w));
+    if constexpr (frame_tma(VAR, R)) {
+        constexpr int TWRc = kTW + 2 * R, BW = tma_bw<IN, R, TWRc>();
+        constexpr int kRawBytes = tma_raw_bytes<IN, VAR, R>();
+        unsigned char* raw = smem + tma_raw_off<IN, VAR, R>();
+        uint64_t* sbar = reinterpret_cast<uint64_t*>(raw + kRawBytes);
+        static_assert(kRawBytes % 16 == 0 && (BW * tma_esize<IN>()) % 16 == 0, "TMA box rows of whole 16-byte units");
+        // a TMA destination must be 128-byte aligned; otherwise plain loads
+        const bool aligned = (umma::smem_addr(raw) & 127u) == 0;
+        if (aligned && tid == 0) {
+            umma::mbar_init(sbar, 1);
+            umma::mbar_expect_tx(sbar, kRawBytes);
+            umma::tma_load_2d(raw, &dmap, x0 - tma_xpad<IN>(), y0 - R, sbar);
+        }
+        __syncthreads();  // no thread polls the barrier before it is initialised
+        const bool ok = aligned && umma::mbar_wait(sbar, 0, 1 << 22);
+        if (aligned && !ok) atomicOr(g.err, kErrMmaWait);
+        for (int i = tid; i < n; i += NT) {
+            const int ly = i / TWRc, lx = i - ly * TWRc;
+            const int b = ly * BW + lx + tma_xpad<IN>() - R;
+            int D = 0;
+            if (ok) {
+                if constexpr (IN == SN_IN_F32)
+                    D = code_from_float(reinterpret_cast<const float*>(raw)[b]);
+                else if constexpr (IN == SN_IN_F16)
+                    D = code_from_float(__half2float(reinterpret_cast<const __half*>(raw)[b]));
+                else
+                    D = reinterpret_cast<const unsigned short*>(raw)[b];
+            } else if (!aligned) {
+                D = load_code<IN>(disp, dp, x0 - R + lx, y0 - R + ly, g.W, g.H);
+            }
+            const float w = D > 0 ? rcp_approx((float)D) : __int_as_float(0x7f800000);
+            tile[i] = make_int2(D, __float_as_int(w));
+        }
+    } else {
+        for (int i = tid; i < n; i += NT) {
+            const int ly = i / TWR;
+            const int lx = i - ly * TWR;
+            const int D = load_code<IN>(disp, dp, x0 - Rr + lx, y0 - Rr + ly, g.W, g.H);
+            const float w = D > 0 ? rcp_approx((float)D) : __int_as_float(0x7f800000);
+            tile[i] = make_int2(D, __float_as_int(w));
+        }
     }
     __syncthreads();
     if constexpr (VAR == 4) {
@@ -856,6 +918,35 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
     }
 }
 
+// Tensor map of a disparity image for the TMA tile staging: W x H elements
+// of the input type, rows `pitch` bytes apart (16-byte aligned base and
+// pitch, checked by the C-ABI layer), box bw x bh, zero outside the image.
+cudaError_t encode_disp_map(CUtensorMap* m, const void* disp, size_t pitch, int W, int H, int in_dtype, int bw,
+                            int bh) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!encode) return cudaErrorNotSupported;
+    const CUtensorMapDataType type = in_dtype == SN_IN_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                     : in_dtype == SN_IN_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                             : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(m, type, 2, const_cast<void*>(disp), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 // Raises a kernel's dynamic shared-memory limit once per device, to the most
 // any parameter set of its variant can ask for (so no launch, and no launch
 // under stream capture, changes function attributes).  `done` is the
@@ -878,13 +969,20 @@ cudaError_t launch_in(const Geo& g, const StarTable& t, const char* d, size_t dp
     constexpr int Rmax = R > 0 ? R : (VAR == 0 ? 15 : (VAR == 4 ? kMaxSteps + 1 : kMaxSteps));
     const int Rr = R > 0 ? R : max(g.r_d, VAR == 0 ? g.r_a : (VAR == 4 ? g.steps + 1 : g.steps));
     constexpr int TH = frame_th(VAR);
-    const size_t bytes = VAR == 3 ? learned_layout(frame_smem(R)).end : frame_smem(Rr, VAR == 4, TH);
-    const size_t bytes_max = VAR == 3 ? learned_layout(frame_smem(R)).end : frame_smem(Rmax, VAR == 4, TH);
+    constexpr bool kTma = frame_tma(VAR, R);
+    const size_t bytes = kTma ? tma_raw_off<IN, VAR, R>() + tma_raw_bytes<IN, VAR, R>() + 16
+                              : (VAR == 3 ? learned_layout(frame_smem(R)).end : frame_smem(Rr, VAR == 4, TH));
+    const size_t bytes_max = kTma ? bytes : (VAR == 3 ? learned_layout(frame_smem(R)).end : frame_smem(Rmax, VAR == 4, TH));
+    CUtensorMap dmap{};
+    if constexpr (kTma) {
+        const cudaError_t me = encode_disp_map(&dmap, d, dp, g.W, g.H, IN, tma_bw<IN, R, kTW + 2 * R>(), TH + 2 * R);
+        if (me != cudaSuccess) return me;
+    }
     const dim3 grid((g.W + kTW - 1) / kTW, (g.H + TH - 1) / TH), block(kTW, TH);
     static std::atomic<unsigned long long> done{0};
     const cudaError_t e = smem_limit_once(k_frame<IN, VAR, R, RD>, bytes_max, done);
     if (e != cudaSuccess) return e;
-    k_frame<IN, VAR, R, RD><<<grid, block, bytes, s>>>(g, t, d, dp, o, gv);
+    k_frame<IN, VAR, R, RD><<<grid, block, bytes, s>>>(g, t, d, dp, o, gv, dmap);
     return cudaGetLastError();
 }
 

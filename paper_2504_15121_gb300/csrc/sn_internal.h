@@ -21,7 +21,7 @@ constexpr int kErrFindLimit = 1;    // a union-find walk exceeded its bound
 constexpr int kWalkLimitDefault = 1 << 22;  // > any parent chain of a 16384^2 frame
 constexpr int kErrUnionLimit = 2;   // a union retry loop exceeded its bound
 constexpr int kErrBarrier = 4;      // a grid barrier wait exceeded its bound
-constexpr int kErrMmaWait = 8;      // a tensor-core completion wait exceeded its bound
+constexpr int kErrMmaWait = 8;      // a tensor-core or TMA completion wait exceeded its bound
 
 // Per-context constants read by every kernel (passed by value).
 struct Geo {

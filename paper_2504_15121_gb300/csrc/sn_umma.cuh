@@ -1,8 +1,8 @@
 // Fifth-generation tensor core (tcgen05) primitives used by the learned
 // gate's convolutions: shared-memory matrix descriptors, the instruction
-// descriptor of a BF16 x BF16 -> FP32 MMA, MMA issue and commit, bulk
-// global -> shared copies, mbarrier init, transaction counts and bounded
-// wait, and tensor-memory (TMEM) allocation and loads.
+// descriptor of a BF16 x BF16 -> FP32 MMA, MMA issue and commit, bulk and
+// tiled-tensor (TMA) global -> shared copies, mbarrier init, transaction
+// counts and bounded wait, and tensor-memory (TMEM) allocation and loads.
 // sm_100-family PTX (compiled for sm_103a).
 #pragma once
 
@@ -69,6 +69,18 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                      smem_addr(dst)),
                  "l"(src), "r"(bytes), "r"(smem_addr(mbar))
                  : "memory");
+}
+
+// 2-D tiled tensor copy global -> shared (TMA) of the box at (x, y) of the
+// tensor map (elements outside the tensor read as zero), completing on the
+// mbarrier's transaction count.  x times the element size must be a
+// multiple of 16 bytes; dst 128-byte aligned.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, uint64_t* mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_addr(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_addr(mbar))
+        : "memory");
 }
 
 // Waits for the phase with the given parity to complete, for at most
