@@ -918,35 +918,6 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
     }
 }
 
-// Tensor map of a disparity image for the TMA tile staging: W x H elements
-// of the input type, rows `pitch` bytes apart (16-byte aligned base and
-// pitch, checked by the C-ABI layer), box bw x bh, zero outside the image.
-cudaError_t encode_disp_map(CUtensorMap* m, const void* disp, size_t pitch, int W, int H, int in_dtype, int bw,
-                            int bh) {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    });
-    if (!encode) return cudaErrorNotSupported;
-    const CUtensorMapDataType type = in_dtype == SN_IN_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                     : in_dtype == SN_IN_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                                             : CU_TENSOR_MAP_DATA_TYPE_UINT16;
-    const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
-    const cuuint64_t strides[1] = {(cuuint64_t)pitch};
-    const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = encode(m, type, 2, const_cast<void*>(disp), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 // Raises a kernel's dynamic shared-memory limit once per device, to the most
 // any parameter set of its variant can ask for (so no launch, and no launch
 // under stream capture, changes function attributes).  `done` is the
@@ -1085,6 +1056,36 @@ __global__ void __launch_bounds__(kTW* kSTH, 4)
 }
 
 }  // namespace
+
+// Tensor map of a disparity image for the TMA tile staging: W x H elements
+// of the input type, rows `pitch` bytes apart (16-byte aligned base and
+// pitch, checked by the C-ABI layer), box bw x bh, zero outside the image.
+cudaError_t encode_disp_map(CUtensorMap* m, const void* disp, size_t pitch, int W, int H, int in_dtype, int bw,
+                            int bh) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!encode) return cudaErrorNotSupported;
+    const CUtensorMapDataType type = in_dtype == SN_IN_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                     : in_dtype == SN_IN_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                             : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(m, type, 2, const_cast<void*>(disp), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 
 bool star_is_m8(const StarTable& t, int dirs, int steps) {
     if (dirs != 8 || steps != 10) return false;

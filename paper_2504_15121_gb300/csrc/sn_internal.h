@@ -1,6 +1,7 @@
 // Internal declarations shared by the C-ABI layer and the kernels.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -153,5 +154,10 @@ cudaError_t launch_net_image(const GateView& gv, void* img, cudaStream_t s);
 cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const void* disp, size_t dp,
                          const FrameOut& o, const GateView* gv, cudaStream_t s, Marks& mk);
 bool star_is_m8(const StarTable& t, int dirs, int steps);
+// Tensor map of a disparity image (the context's input type) for TMA tile
+// loads: W x H elements, rows `pitch` bytes apart (16-byte aligned base and
+// pitch), box bw x bh elements, zero outside the image.
+cudaError_t encode_disp_map(CUtensorMap* m, const void* disp, size_t pitch, int W, int H, int in_dtype, int bw,
+                            int bh);
 
 }  // namespace sn

@@ -3,6 +3,7 @@
 // connected-component labelling (tile-local union-find in shared memory,
 // border merge with global atomics, flatten).
 #include "sn_device.cuh"
+#include "sn_umma.cuh"
 
 namespace sn {
 
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(kTW* kTH)
 template <int IN>
 __global__ void __launch_bounds__(kCclTile * 8)
     k_ccl_local(const Geo g, const char* __restrict__ disp, size_t dp, int* __restrict__ labels,
-                size_t lpe, int* __restrict__ count) {
+                size_t lpe, int* __restrict__ count, const __grid_constant__ CUtensorMap dmap, int use_tma) {
     // Each warp labels rows ty, ty + 8, ty + 16, ty + 24 of the 32 x 32 tile:
     // the pixels joined to their left neighbour form runs, labelled by the
     // run's first lane (from a ballot of left edges); then vertical edges join
@@ -135,13 +136,40 @@ __global__ void __launch_bounds__(kCclTile * 8)
     __shared__ int Ds[kCclTile * kCclTile];
     __shared__ int Ls[kCclTile * kCclTile];
     __shared__ unsigned Lrow[kCclTile];
+    // the tile's raw disparities by one TMA copy (zero outside the image;
+    // the box starts on a 32-element column, a 16-byte boundary)
+    constexpr int kES = IN == SN_IN_F32 ? 4 : 2;
+    __shared__ __align__(128) unsigned char raw[kCclTile * kCclTile * kES];
+    __shared__ uint64_t sbar;
     const int x0 = blockIdx.x * kCclTile, y0 = blockIdx.y * kCclTile;
-    const int lane = threadIdx.x;
-    if (count && blockIdx.x == 0 && blockIdx.y == 0 && lane == 0 && threadIdx.y == 0) *count = 0;
+    const int lane = threadIdx.x, tid = threadIdx.y * kCclTile + lane;
+    if (count && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) *count = 0;
+    const bool tma = use_tma && (umma::smem_addr(raw) & 127u) == 0;
+    if (tma) {
+        if (tid == 0) {
+            umma::mbar_init(&sbar, 1);
+            umma::mbar_expect_tx(&sbar, sizeof(raw));
+            umma::tma_load_2d(raw, &dmap, x0, y0, &sbar);
+        }
+        __syncthreads();  // no thread polls the barrier before it is initialised
+    }
+    const bool ok = tma && umma::mbar_wait(&sbar, 0, 1 << 22);
+    if (tma && !ok && tid == 0) atomicOr(g.err, kErrMmaWait);
 #pragma unroll
     for (int k = 0; k < kRows; k++) {
-        const int r = threadIdx.y + 8 * k;
-        Ds[r * kCclTile + lane] = load_code<IN>(disp, dp, x0 + lane, y0 + r, g.W, g.H);
+        const int r = threadIdx.y + 8 * k, i = r * kCclTile + lane;
+        int D = 0;
+        if (ok) {
+            if constexpr (IN == SN_IN_F32)
+                D = code_from_float(reinterpret_cast<const float*>(raw)[i]);
+            else if constexpr (IN == SN_IN_F16)
+                D = code_from_float(__half2float(reinterpret_cast<const __half*>(raw)[i]));
+            else
+                D = reinterpret_cast<const unsigned short*>(raw)[i];
+        } else if (!tma) {
+            D = load_code<IN>(disp, dp, x0 + lane, y0 + r, g.W, g.H);
+        }
+        Ds[i] = D;
     }
     __syncthreads();
     const unsigned upto = 0xffffffffu >> (31 - lane);
@@ -352,10 +380,12 @@ cudaError_t launch_components(const Geo& g, const void* disp, size_t dp, int32_t
     const size_t lpe = lp / sizeof(int32_t);
     const char* d = static_cast<const char*>(disp);
     const dim3 lg(nbx, nby), lb(kCclTile, 8);
+    CUtensorMap dmap{};
+    const int tma = encode_disp_map(&dmap, disp, dp, g.W, g.H, g.in_dtype, kCclTile, kCclTile) == cudaSuccess;
     switch (g.in_dtype) {
-        case SN_IN_F32: k_ccl_local<SN_IN_F32><<<lg, lb, 0, s>>>(g, d, dp, labels, lpe, count); break;
-        case SN_IN_F16: k_ccl_local<SN_IN_F16><<<lg, lb, 0, s>>>(g, d, dp, labels, lpe, count); break;
-        default: k_ccl_local<SN_IN_U16X256><<<lg, lb, 0, s>>>(g, d, dp, labels, lpe, count); break;
+        case SN_IN_F32: k_ccl_local<SN_IN_F32><<<lg, lb, 0, s>>>(g, d, dp, labels, lpe, count, dmap, tma); break;
+        case SN_IN_F16: k_ccl_local<SN_IN_F16><<<lg, lb, 0, s>>>(g, d, dp, labels, lpe, count, dmap, tma); break;
+        default: k_ccl_local<SN_IN_U16X256><<<lg, lb, 0, s>>>(g, d, dp, labels, lpe, count, dmap, tma); break;
     }
     mk.after(s);
     cudaError_t e = cudaGetLastError();
