@@ -59,6 +59,16 @@ __device__ __forceinline__ bool pair_edge(int a, int b, int K) {
     return ((unsigned long long)diff << 16) <= (unsigned long long)(unsigned)K * mn;
 }
 
+// The same test from per-pixel thresholds t = floor(K D / 2^16): for
+// integers, 2^16 |a - b| <= K m  <=>  |a - b| <= floor(K m / 2^16), and
+// floor(K m / 2^16) with m = min(a, b) is min(t_a, t_b) (it is monotone).
+__device__ __forceinline__ int pair_thr(int D, int K) {
+    return (int)(((unsigned long long)(unsigned)K * (unsigned)D) >> 16);
+}
+__device__ __forceinline__ bool pair_edge_t(int a, int ta, int b, int tb) {
+    return a > 0 && b > 0 && abs(a - b) <= min(ta, tb);
+}
+
 // covered-depth stop: (nmax - nmin) Dc 2^16 > K nmin nmax
 __device__ __forceinline__ bool cd_stop(int nmin, int nmax, int Dc, int K) {
     const unsigned long long lhs = ((unsigned long long)(unsigned)(nmax - nmin) * (unsigned)Dc) << 16;

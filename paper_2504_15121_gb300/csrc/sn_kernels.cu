@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(kCclTile * 8)
     constexpr int kRows = kCclTile / 8;
     __shared__ int Ds[kCclTile * kCclTile];
     __shared__ int Ls[kCclTile * kCclTile];
+    __shared__ int Ts[kCclTile * kCclTile];  // pair_thr of every code
     __shared__ unsigned Lrow[kCclTile];
     // the tile's raw disparities by one TMA copy (zero outside the image;
     // the box starts on a 32-element column, a 16-byte boundary)
@@ -170,6 +171,7 @@ __global__ void __launch_bounds__(kCclTile * 8)
             D = load_code<IN>(disp, dp, x0 + lane, y0 + r, g.W, g.H);
         }
         Ds[i] = D;
+        Ts[i] = pair_thr(D, g.K_pair);
     }
     __syncthreads();
     const unsigned upto = 0xffffffffu >> (31 - lane);
@@ -179,9 +181,9 @@ __global__ void __launch_bounds__(kCclTile * 8)
 #pragma unroll
     for (int k = 0; k < kRows; k++) {
         const int r = threadIdx.y + 8 * k, i = r * kCclTile + lane;
-        const int D = Ds[i];
-        const bool eL = lane > 0 && pair_edge(D, Ds[i - 1], g.K_pair);
-        eU[k] = r > 0 && pair_edge(D, Ds[i - kCclTile], g.K_pair);
+        const int D = Ds[i], t = Ts[i];
+        const bool eL = lane > 0 && pair_edge_t(D, t, Ds[i - 1], Ts[i - 1]);
+        eU[k] = r > 0 && pair_edge_t(D, t, Ds[i - kCclTile], Ts[i - kCclTile]);
         Lb[k] = __ballot_sync(0xffffffffu, eL);
         Ub[k] = __ballot_sync(0xffffffffu, eU[k]);
         run[k] = r * kCclTile + (31 - __clz(~Lb[k] & upto));
