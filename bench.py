@@ -808,27 +808,16 @@ def run_e2e(pipe, scenes, args, world, dist):
         t = torch.from_numpy(s.disp).pin_memory()
         host_in.append(t)
     NS = 2  # the host copies are bandwidth-bound: 2 streams measured best (2: 5.9, 4: 5.6, 8: 5.4 GPix/s)
-    outs = [pipe.buffers() for _ in range(NS)]
-    dins = [sn.empty_image(H, W, torch.float32) for _ in range(NS)]
-    host_out = [dict(normals=torch.empty((3, H, W), dtype=torch.float32).pin_memory(),
-                     points=torch.empty((3, H, W), dtype=torch.float32).pin_memory(),
-                     labels=torch.empty((H, W), dtype=torch.int32).pin_memory(),
-                     mask=torch.empty((H, W), dtype=torch.uint8).pin_memory()) for _ in range(NS)]
+    host_out = [pipe.host_buffers() for _ in range(NS)]
     streams = [torch.cuda.Stream() for _ in range(NS)]
     h2d = W * H * 4
-    d2h = W * H * (12 + 12 + 4 + 1)
+    d2h = W * H * (12 + 12 + 4 + 1) + 4
 
     def frame(f):
+        # the C ABI on host buffers: copy in, sn_run_frame, copy out, all on
+        # the stream (the context's staging buffers rotate)
         i = f % NS
-        st = streams[i]
-        with torch.cuda.stream(st):
-            dins[i].copy_(host_in[f % len(host_in)], non_blocking=True)
-            pipe.run_frame(dins[i], outs[i], stream=st, write_den=False)
-            o, ho = outs[i], host_out[i]
-            ho["normals"].copy_(o.normals, non_blocking=True)
-            ho["points"].copy_(o.points, non_blocking=True)
-            ho["labels"].copy_(o.labels, non_blocking=True)
-            ho["mask"].copy_(o.mask, non_blocking=True)
+        pipe.run_frame_host(host_in[f % len(host_in)], host_out[i], stream=streams[i])
 
     steps = max(3, args.steps // 4)
     for f in range(NS * F):
@@ -851,9 +840,9 @@ def run_e2e(pipe, scenes, args, world, dist):
     return {"value": value, "unit": "MPix/s", "h2d_bytes_per_step": F * h2d,
             "d2h_bytes_per_step": F * d2h, "steps": steps,
             "link": dict(link, bound_mpix_s=bound * world, frac=value / (bound * world)),
-            "how": "pinned host disparity -> device, sn_run_frame, normals/points/labels/mask -> "
-                   f"pinned host; {NS} streams taking frames in turn; host wall clock with a device sync "
-                   "per step"}
+            "how": "sn_run_frame_host (C ABI on host buffers): pinned host disparity -> device, "
+                   "the chain, normals/points/labels/mask/count -> pinned host; "
+                   f"{NS} streams taking frames in turn; host wall clock with a device sync per step"}
 
 
 def main():

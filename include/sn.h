@@ -243,6 +243,23 @@ typedef struct {
  * profiling is on (sn_set_profiling), all four launches stay on `stream`. */
 sn_status sn_run_frame(sn_ctx *ctx, const sn_frame_in *in, sn_frame_out *out, sn_stream stream);
 
+/* sn_run_frame on HOST buffers: copies the disparity (in->disp, host) to
+ * the device, runs sn_run_frame, and copies normals, points, labels, mask
+ * and, if out->num_components is not NULL, the component count (host
+ * int32) back into the host buffers of `out`; everything is enqueued on
+ * `stream` (the results are in place once `stream` has passed the call).
+ * Host buffers have the layout of sn_run_frame's outputs with any pitch
+ * >= W x element size and no alignment requirement; page-locked (pinned)
+ * host memory makes the copies asynchronous, pageable memory makes them
+ * synchronous.  out->den must be NULL.  The context cycles through 4 sets
+ * of device staging buffers (frames on up to 4 streams in flight at once);
+ * a set is reused only after its previous frame's copies are done (event
+ * wait on `stream`).  The first call allocates the staging buffers (not
+ * under stream capture); later calls allocate nothing.  Errors as
+ * sn_run_frame, plus SN_EINVAL for a NULL host pointer or a short pitch and
+ * SN_ENOMEM if the staging buffers cannot be allocated. */
+sn_status sn_run_frame_host(sn_ctx *ctx, const sn_frame_in *in, sn_frame_out *out, sn_stream stream);
+
 /* Allocation-free denoise + normals.  The paper has no counterpart: this is
  * for callers that cannot call cudaMalloc -- a plugin whose host application
  * owns all device memory through its own pool, or a real-time loop that must

@@ -13,6 +13,25 @@ namespace {
 constexpr int kStages = 4;         // kernel launches of one sn_run_frame
 constexpr int kProfFrames = 4096;  // frames recorded between two sn_stage_times calls
 constexpr int kAux = 4;            // side streams the component passes of sn_run_frame fork onto
+constexpr int kHostSlots = 4;      // device staging sets of sn_run_frame_host
+
+// Device staging of one sn_run_frame_host frame; `done` is recorded after
+// its copies back to the host.
+struct HostSlot {
+    void* in;
+    size_t in_p;
+    void* nrm;
+    size_t nrm_p;
+    float* pts;
+    size_t pts_p;
+    int32_t* lab;
+    size_t lab_p;
+    uint8_t* mask;
+    size_t mask_p;
+    int32_t* count;
+    cudaEvent_t done;
+    bool used;
+};
 const char* const kStageNames[kStages] = {"frame", "ccl_local", "ccl_merge", "ccl_flatten"};
 }  // namespace
 
@@ -39,10 +58,28 @@ struct sn_ctx {
     cudaStream_t aux[kAux];
     cudaEvent_t fork_ev[kAux], join_ev[kAux];
     int aux_next;
+    HostSlot hs[kHostSlots];  // allocated by the first sn_run_frame_host
+    bool hs_ready;
+    int hs_next;
     char msg[512];
 };
 
 namespace {
+
+void free_host_slots(sn_ctx* c) {
+    for (int i = 0; i < kHostSlots; i++) {
+        HostSlot& h = c->hs[i];
+        cudaFree(h.in);
+        cudaFree(h.nrm);
+        cudaFree(h.pts);
+        cudaFree(h.lab);
+        cudaFree(h.mask);
+        cudaFree(h.count);
+        if (h.done) cudaEventDestroy(h.done);
+        h = HostSlot{};
+    }
+    c->hs_ready = false;
+}
 
 int kfix(float k) { return (int)nearbyint((double)k * 65536.0); }
 
@@ -356,6 +393,7 @@ sn_status sn_destroy(sn_ctx* c) {
         for (int i = 0; i < kProfFrames * (kStages + 1); i++) cudaEventDestroy(c->ev[i]);
         delete[] c->ev;
     }
+    free_host_slots(c);
     for (int i = 0; i < kAux; i++) {
         if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
         if (c->fork_ev[i]) cudaEventDestroy(c->fork_ev[i]);
@@ -516,6 +554,83 @@ sn_status sn_run_frame(sn_ctx* c, const sn_frame_in* in, sn_frame_out* out, sn_s
     }
     c->launches += mk.launches;
     return e == cudaSuccess ? SN_OK : cuda_fail(c, e, "sn_run_frame");
+}
+
+namespace {
+
+cudaError_t alloc_host_slots(sn_ctx* c) {
+    const size_t W = (size_t)c->W, H = (size_t)c->H;
+    const bool f32 = c->p.normal_fmt == SN_NORMALS_F32X3;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kHostSlots && e == cudaSuccess; i++) {
+        HostSlot& h = c->hs[i];
+        e = cudaMallocPitch(&h.in, &h.in_p, W * in_elem(c->p.in_dtype), H);
+        if (e == cudaSuccess) e = cudaMallocPitch(&h.nrm, &h.nrm_p, W * nrm_elem(c->p.normal_fmt), f32 ? 3 * H : H);
+        if (e == cudaSuccess) e = cudaMallocPitch((void**)&h.pts, &h.pts_p, W * 4, 3 * H);
+        if (e == cudaSuccess) e = cudaMallocPitch((void**)&h.lab, &h.lab_p, W * 4, H);
+        if (e == cudaSuccess) e = cudaMallocPitch((void**)&h.mask, &h.mask_p, W, H);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&h.count, 16);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.done, cudaEventDisableTiming);
+    }
+    return e;
+}
+
+}  // namespace
+
+sn_status sn_run_frame_host(sn_ctx* c, const sn_frame_in* in, sn_frame_out* out, sn_stream stream) {
+    if (!c || !in || !out) return SN_EINVAL;
+    const size_t W = (size_t)c->W, H = (size_t)c->H;
+    const bool f32 = c->p.normal_fmt == SN_NORMALS_F32X3;
+    const size_t ie = in_elem(c->p.in_dtype), ne = nrm_elem(c->p.normal_fmt);
+    if (out->den) return fail(c, SN_EINVAL, "sn_run_frame_host: den must be NULL");
+    if (!in->disp || in->disp_pitch < W * ie) return fail(c, SN_EINVAL, "host disp: NULL or pitch too short");
+    if (!out->normals || out->normals_pitch < W * ne) return fail(c, SN_EINVAL, "host normals: NULL or pitch too short");
+    if (!out->points || out->points_pitch < W * 4) return fail(c, SN_EINVAL, "host points: NULL or pitch too short");
+    if (!out->labels || out->labels_pitch < W * 4) return fail(c, SN_EINVAL, "host labels: NULL or pitch too short");
+    if (!out->mask || out->mask_pitch < W) return fail(c, SN_EINVAL, "host mask: NULL or pitch too short");
+    if (!c->hs_ready) {
+        const cudaError_t e = alloc_host_slots(c);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            free_host_slots(c);
+            return fail(c, SN_ENOMEM, "sn_run_frame_host: staging buffers");
+        }
+        c->hs_ready = true;
+    }
+    HostSlot& h = c->hs[c->hs_next];
+    c->hs_next = (c->hs_next + 1) % kHostSlots;
+    cudaError_t e = h.used ? cudaStreamWaitEvent(stream, h.done, 0) : cudaSuccess;
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(h.in, h.in_p, in->disp, in->disp_pitch, W * ie, H, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sn_run_frame_host: copy in");
+    sn_frame_in fi{h.in, h.in_p};
+    sn_frame_out fo{};
+    fo.normals = h.nrm;
+    fo.normals_pitch = h.nrm_p;
+    fo.points = h.pts;
+    fo.points_pitch = h.pts_p;
+    fo.labels = h.lab;
+    fo.labels_pitch = h.lab_p;
+    fo.mask = h.mask;
+    fo.mask_pitch = h.mask_p;
+    fo.num_components = out->num_components ? h.count : nullptr;
+    const sn_status st = sn_run_frame(c, &fi, &fo, stream);
+    if (st != SN_OK) return st;
+    e = cudaMemcpy2DAsync(out->normals, out->normals_pitch, h.nrm, h.nrm_p, W * ne, f32 ? 3 * H : H,
+                          cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(out->points, out->points_pitch, h.pts, h.pts_p, W * 4, 3 * H, cudaMemcpyDeviceToHost,
+                              stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(out->labels, out->labels_pitch, h.lab, h.lab_p, W * 4, H, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(out->mask, out->mask_pitch, h.mask, h.mask_p, W, H, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess && out->num_components)
+        e = cudaMemcpyAsync(out->num_components, h.count, sizeof(int32_t), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h.done, stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sn_run_frame_host: copy out");
+    h.used = true;
+    return SN_OK;
 }
 
 sn_status sn_set_walk_limit(sn_ctx* c, int steps) {

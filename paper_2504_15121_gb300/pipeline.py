@@ -33,6 +33,18 @@ class FrameBuffers:
         )
 
 
+def host_buffers(W: int, H: int, normal_fmt: int = sn.SN_NORMALS_F32X3, pin: bool = True) -> FrameBuffers:
+    """Host outputs of one frame for sn_run_frame_host (contiguous; pinned by
+    default, so that the copies are asynchronous); den is not used."""
+    def host(shape, dtype):
+        t = torch.empty(shape, dtype=dtype)
+        return t.pin_memory() if pin else t
+    nrm = host((3, H, W), torch.float32) if normal_fmt == sn.SN_NORMALS_F32X3 else host((H, W, 4), torch.int16)
+    return FrameBuffers(den=None, normals=nrm, points=host((3, H, W), torch.float32),
+                        labels=host((H, W), torch.int32), mask=host((H, W), torch.uint8),
+                        num_components=host((1,), torch.int32))
+
+
 _IN_DTYPE = {torch.float32: sn.SN_IN_F32, torch.float16: sn.SN_IN_F16, torch.int16: sn.SN_IN_U16X256,
              torch.uint16: sn.SN_IN_U16X256}
 
@@ -65,6 +77,15 @@ class Pipeline:
 
     def buffers(self, device="cuda") -> FrameBuffers:
         return FrameBuffers.allocate(self.W, self.H, self.params.normal_fmt, device)
+
+    def host_buffers(self, pin: bool = True) -> FrameBuffers:
+        return host_buffers(self.W, self.H, self.params.normal_fmt, pin)
+
+    def run_frame_host(self, disp: torch.Tensor, out: FrameBuffers, stream=None):
+        """sn_run_frame_host: host disparity in, host outputs (see host_buffers)."""
+        sn.sn_run_frame_host(self.ctx, disp, out.normals, out.points, out.labels, out.mask,
+                             num_components=out.num_components, stream=stream)
+        return out
 
     def upload(self, disp_np, device="cuda") -> torch.Tensor:
         """Copy a host disparity map into a pitched device image."""

@@ -79,6 +79,7 @@ def _load():
         "sn_pca_normals": ([vp, vp, sz, i, vp, sz, vp, sz, vp], i),
         "sn_pointcloud": ([vp, vp, sz, vp, sz, vp, sz, vp], i),
         "sn_run_frame": ([vp, C.POINTER(sn_frame_in), C.POINTER(sn_frame_out), vp], i),
+        "sn_run_frame_host": ([vp, C.POINTER(sn_frame_in), C.POINTER(sn_frame_out), vp], i),
         "sn_load_gate_weights": ([vp, vp, sz], i),
         "sn_star_offsets": ([i, i, vp, vp], i),
         "sn_check_device": ([vp, vp], i),
@@ -108,7 +109,7 @@ EXPORTS = ("sn_version", "sn_default_params", "sn_create", "sn_destroy", "sn_den
            "sn_load_gate_weights", "sn_star_offsets", "sn_check_device", "sn_status_string",
            "sn_last_error", "sn_set_profiling", "sn_stage_count", "sn_stage_name",
            "sn_stage_times", "sn_launch_count", "sn_normals_noalloc", "sn_cross_normals",
-           "sn_pca_normals", "sn_set_walk_limit")
+           "sn_pca_normals", "sn_set_walk_limit", "sn_run_frame_host")
 
 
 # ---------------------------------------------------------------- helpers
@@ -258,6 +259,27 @@ def sn_run_frame(ctx, disp, normals, points, labels, mask, den=None, num_compone
     fo.mask = m
     fo.num_components = C.c_void_p(num_components.data_ptr()) if num_components is not None else None
     _check(ctx, lib.sn_run_frame(ctx, C.byref(fi), C.byref(fo), _stream(stream)))
+
+
+def sn_run_frame_host(ctx, disp, normals, points, labels, mask, num_components=None, stream=None):
+    """sn_run_frame on host (CPU) tensors, pinned for asynchronous copies;
+    same layouts as sn_run_frame's device outputs."""
+    for t in (disp, normals, points, labels, mask) + ((num_components,) if num_components is not None else ()):
+        assert not t.is_cuda, "sn_run_frame_host takes host tensors"
+    fi = sn_frame_in()
+    d, fi.disp_pitch = _img(disp)
+    fi.disp = d
+    fo = sn_frame_out()
+    n, fo.normals_pitch = _img(normals)
+    fo.normals = n
+    p, fo.points_pitch = _img(points)
+    fo.points = p
+    l, fo.labels_pitch = _img(labels)
+    fo.labels = l
+    m, fo.mask_pitch = _img(mask)
+    fo.mask = m
+    fo.num_components = C.c_void_p(num_components.data_ptr()) if num_components is not None else None
+    _check(ctx, lib.sn_run_frame_host(ctx, C.byref(fi), C.byref(fo), _stream(stream)))
 
 
 def sn_set_walk_limit(ctx, steps: int):

@@ -367,6 +367,45 @@ def test_streams_and_graph_capture(P):
         pipe.close()
 
 
+def test_run_frame_host(P):
+    # the C ABI on host buffers: copies in and out around sn_run_frame on the
+    # caller's stream; six frames on two streams cycle through the context's
+    # four staging sets; pinned and pageable host memory; results equal the
+    # device call's bit for bit
+    scenes = [make_scene("planes_640x480", frame=f) for f in range(6)]
+    H, W = scenes[0].disp.shape
+    pipe = P.Pipeline(scenes[0].camera, W, H)
+    try:
+        ref = []
+        for sc in scenes:
+            o = pipe.buffers()
+            pipe.run_frame(pipe.upload(sc.disp), o, write_den=False)
+            torch.cuda.synchronize()
+            ref.append(to_host(o))
+        streams = [torch.cuda.Stream() for _ in range(2)]
+        for pin in (True, False):
+            ins = [torch.from_numpy(sc.disp).pin_memory() if pin else torch.from_numpy(sc.disp) for sc in scenes]
+            outs = [pipe.host_buffers(pin=pin) for _ in scenes]
+            for i in range(len(scenes)):
+                pipe.run_frame_host(ins[i], outs[i], stream=streams[i % 2])
+            torch.cuda.synchronize()
+            P.sn.sn_check_device(pipe.ctx)
+            for o, r in zip(outs, ref):
+                assert np.array_equal(o.normals.permute(1, 2, 0).numpy().astype(np.float64), r["normals"])
+                assert np.array_equal(o.points.permute(1, 2, 0).numpy().astype(np.float64), r["points"])
+                assert np.array_equal(o.labels.numpy(), r["labels"])
+                assert np.array_equal(o.mask.numpy(), r["mask"])
+                assert int(o.num_components.item()) == r["n_components"]
+        # argument errors are found on the host before anything is enqueued
+        o = pipe.host_buffers()
+        short = torch.zeros((H, W // 2), dtype=torch.float32)  # rows shorter than the frame
+        with pytest.raises(P.sn.SnError) as ei:
+            P.sn.sn_run_frame_host(pipe.ctx, short, o.normals, o.points, o.labels, o.mask)
+        assert ei.value.status == P.sn.SN_EINVAL
+    finally:
+        pipe.close()
+
+
 def test_argument_errors_on_device(P):
     s = make_scene("planes_320x240", frame=0)
     H, W = s.disp.shape
