@@ -1,13 +1,14 @@
-// Fused frame kernel: one pass over 32 x 16 pixel tiles computes the
-// denoised disparity, the support (fixed window or star-fill), the affine
-// fit, the normal, the point and the mask.  The component labels come from
-// the separate run-based passes (k_ccl_local, k_ccl_merge, k_ccl_flatten),
-// launched after it on the same stream: they need only the ingested codes,
-// and outside this kernel they keep its registers and shared memory free.
-// The tile and its halo are staged once in shared memory as (D, 1/D) pairs:
-// D is the exact integer disparity code used by every sum and decision,
-// 1/D (FP32, correctly rounded; +inf for invalid) carries the covered-depth
-// test, which in reciprocal form reads 1/Dmin - 1/Dmax > K / (2^16 Dc).
+// Fused frame kernel: one pass over 32 x 8 (compile-time star) or 32 x 16
+// pixel tiles computes the denoised disparity, the support (fixed window or
+// star-fill), the affine fit, the normal, the point and the mask.  The
+// component labels come from the separate run-based passes (k_ccl_local,
+// k_ccl_merge, k_ccl_flatten), which need only the ingested codes and run
+// beside this kernel on a side stream.  The tile and its halo are staged
+// once in shared memory (by one TMA copy where the halo is fixed at compile
+// time) as (D, 1/D) pairs: D is the exact integer disparity code used by
+// every sum and decision, 1/D (FP32, within 1 ulp; +inf for invalid)
+// carries the covered-depth test, which in reciprocal form reads
+// 1/Dmin - 1/Dmax > K / (2^16 Dc).
 #include <atomic>
 
 #include <cuda.h>  // CUtensorMap (the encoder is reached through the runtime's driver entry point)
