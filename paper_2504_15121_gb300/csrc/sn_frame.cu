@@ -30,7 +30,7 @@ constexpr int kTW = kFrameTW, kTH = kFrameTH, kThreads = kTW * kTH;
 // 2048x1024 frame); the variants with larger halos (star tables up to s = 30,
 // ST) and the learned one (whose network halo is amortised over more pixels)
 // keep 32 x 16.
-__host__ __device__ constexpr int frame_th(int var) { return var == 2 ? 8 : kTH; }
+__host__ __device__ constexpr int frame_th(int var) { return var == 2 || var == 5 ? 8 : kTH; }
 
 // distinct pixels of an M = 8 diagonal ray of s steps: round(s / sqrt 2),
 // i.e. the r with (2r - 1)^2 < 2 s^2 < (2r + 1)^2
@@ -391,6 +391,13 @@ __device__ __forceinline__ void plain_pixel(const Geo& g, const StarTable& T, co
     AffSums s;
     if constexpr (VAR == 4) {
         star_table_st(c, ec, TWR, Dc, T, g.dirs, g.steps, s);
+    } else if constexpr (VAR == 5) {
+        // ST stop on the compile-time star: invalid and edge pixels carry
+        // 1/D = +inf in this tile, so a ray is alive while its spread is
+        // finite (lo = +inf) and never enters the exact tail (hi = -inf)
+        static_assert(R == 11, "the M = 8, s = 10 star with the ST stop needs a halo of 11");
+        const Thr st{-__int_as_float(0x7f800000), __int_as_float(0x7f800000), 0};
+        star8<10, kTW + 2 * R>(c, Dc, rcp_approx((float)Dc), st, s);
     } else if constexpr (VAR >= 2) {
         static_assert(R == 10, "the M = 8, s = 10 star needs a halo of 10");
         star8<10, kTW + 2 * R>(c, Dc, __int_as_float(cc.y), make_thr(g, Dc), s);
@@ -607,7 +614,7 @@ __device__ __forceinline__ void stage_tile(int2* tile, unsigned char* raw, const
     }
     __syncthreads();
 }
-constexpr bool frame_tma(int VAR, int R) { return R > 0 && (VAR == 2 || VAR == 3); }
+constexpr bool frame_tma(int VAR, int R) { return R > 0 && (VAR == 2 || VAR == 3 || VAR == 5); }
 constexpr size_t align128z(size_t b) { return (b + 127) & ~(size_t)127; }
 // Offset and size of the raw box (then its 8-byte mbarrier) after the
 // variant's other shared memory.
@@ -621,7 +628,8 @@ __host__ __device__ constexpr int tma_raw_bytes() {
 }
 
 // VAR: 0 fixed window, 1 star table, 2 compile-time M = 8, s = 10 star,
-// 3 = 2 with the learned gate, 4 star table with the ST stop.  R: halo
+// 3 = 2 with the learned gate, 4 star table with the ST stop, 5 = 2 with the
+// ST stop instead of the covered-depth test.  R: halo
 // radius at compile time (0 = runtime).
 // RD: denoise radius (0 = runtime).
 template <int IN, int VAR, int R, int RD>
@@ -650,6 +658,19 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
             const int D = load_code<IN>(disp, dp, x0 - Rr + lx, y0 - Rr + ly, g.W, g.H);
             const float w = D > 0 ? rcp_approx((float)D) : __int_as_float(0x7f800000);
             tile[i] = make_int2(D, __float_as_int(w));
+        }
+        __syncthreads();
+    }
+    if constexpr (VAR == 5) {
+        // ST edges folded into the tile: 1/D = +inf for every pixel that stops
+        // a ray (invalid, or |depth Laplacian| > t; the outer ring, which no
+        // ray reaches, too).  Only the .y words change, the edge tests read .x.
+        for (int i = tid; i < n; i += NT) {
+            const int ly = i / TWR, lx = i - ly * TWR;
+            bool e = true;
+            if (lx > 0 && lx < TWR - 1 && ly > 0 && ly < THR - 1)
+                e = st_edge(g, tile[i].x, tile[i - 1].x, tile[i + 1].x, tile[i - TWR].x, tile[i + TWR].x);
+            if (e) tile[i].y = 0x7f800000;
         }
         __syncthreads();
     }
@@ -1125,6 +1146,9 @@ cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const voi
                        : launch_var<2, 10, 0>(g, t, disp, dp, o, none, s);
     else if (g.support == SN_SUPPORT_STARFILL_CD)
         e = launch_var<1, 0, 0>(g, t, disp, dp, o, none, s);
+    else if (g.support == SN_SUPPORT_STARFILL_ST && star8)
+        e = g.r_d == 2 ? launch_var<5, 11, 2>(g, t, disp, dp, o, none, s)
+                       : launch_var<5, 11, 0>(g, t, disp, dp, o, none, s);
     else if (g.support == SN_SUPPORT_STARFILL_ST)
         e = launch_var<4, 0, 0>(g, t, disp, dp, o, none, s);
     else
