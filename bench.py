@@ -339,6 +339,9 @@ def run_ours(args):
         # star-fill with the depth-edge stop (ST s10 d8 t0.1, Table perf-disc)
         "st_s10_d8_f32": time_form(scenes, args, dict(support=2, st_t=0.1), lambda s: s.disp, FRAME_ALGO_BYTES,
                                    dist, world),
+        # fixed 9x9 affine window (the paper's n x n setting, n = 9)
+        "fixed_9x9_f32": time_form(scenes, args, dict(support=0, r_affine=4), lambda s: s.disp, FRAME_ALGO_BYTES,
+                                   dist, world),
     }
     for f in forms.values():
         f["vs_plain"] = f["value"] / value

@@ -232,13 +232,27 @@ __device__ __forceinline__ void star_table_st(const int2* c, const uint8_t* ec, 
     }
 }
 
+// Fixed (2R + 1)^2 window on the packed tile; RA > 0 fixes the radius (and
+// the row stride STRIDE) at compile time, so the window unrolls.
+template <int RA = 0, int STRIDE = 0>
 __device__ __forceinline__ void fixed_packed(const int2* c, int stride, int R, int Dc, AffSums& s) {
     aff_zero(s);
-    for (int ov = -R; ov <= R; ov++) {
-        const int2* row = c + ov * stride;
-        for (int ou = -R; ou <= R; ou++) {
-            const int Di = row[ou].x;
-            if (Di > 0 && (ou | ov) != 0) aff_add(s, ou, ov, Di - Dc);
+    if constexpr (RA > 0) {
+#pragma unroll
+        for (int ov = -RA; ov <= RA; ov++) {
+#pragma unroll
+            for (int ou = -RA; ou <= RA; ou++) {
+                const int Di = c[ov * STRIDE + ou].x;
+                if (Di > 0 && (ou | ov) != 0) aff_add(s, ou, ov, Di - Dc);
+            }
+        }
+    } else {
+        for (int ov = -R; ov <= R; ov++) {
+            const int2* row = c + ov * stride;
+            for (int ou = -R; ou <= R; ou++) {
+                const int Di = row[ou].x;
+                if (Di > 0 && (ou | ov) != 0) aff_add(s, ou, ov, Di - Dc);
+            }
         }
     }
 }
@@ -403,6 +417,8 @@ __device__ __forceinline__ void plain_pixel(const Geo& g, const StarTable& T, co
         star8<10, kTW + 2 * R>(c, Dc, __int_as_float(cc.y), make_thr(g, Dc), s);
     } else if constexpr (VAR == 1) {
         star_table(c, TWR, Dc, __int_as_float(cc.y), make_thr(g, Dc), T, g.dirs, g.steps, s);
+    } else if constexpr (R > 0) {
+        fixed_packed<R, kTW + 2 * R>(c, TWR, R, Dc, s);  // compile-time 9x9 (R = r_a = 4 >= r_d)
     } else {
         fixed_packed(c, TWR, g.r_a, Dc, s);
     }
@@ -614,7 +630,7 @@ __device__ __forceinline__ void stage_tile(int2* tile, unsigned char* raw, const
     }
     __syncthreads();
 }
-constexpr bool frame_tma(int VAR, int R) { return R > 0 && (VAR == 2 || VAR == 3 || VAR == 5); }
+constexpr bool frame_tma(int VAR, int R) { return R > 0 && (VAR == 0 || VAR == 2 || VAR == 3 || VAR == 5); }
 constexpr size_t align128z(size_t b) { return (b + 127) & ~(size_t)127; }
 // Offset and size of the raw box (then its 8-byte mbarrier) after the
 // variant's other shared memory.
@@ -1151,6 +1167,8 @@ cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const voi
                        : launch_var<5, 11, 0>(g, t, disp, dp, o, none, s);
     else if (g.support == SN_SUPPORT_STARFILL_ST)
         e = launch_var<4, 0, 0>(g, t, disp, dp, o, none, s);
+    else if (g.r_a == 4 && g.r_d == 2)
+        e = launch_var<0, 4, 2>(g, t, disp, dp, o, none, s);  // the 9x9 window with the 5x5 denoise
     else
         e = launch_var<0, 0, 0>(g, t, disp, dp, o, none, s);
     mk.after(s);
