@@ -603,12 +603,14 @@ __device__ __forceinline__ void stage_tile(int2* tile, unsigned char* raw, const
     uint64_t* sbar = reinterpret_cast<uint64_t*>(raw + kRawBytes);
     const int tid = threadIdx.y * kTW + threadIdx.x;  // blocks are kTW wide, NT threads
     const bool tma = use_tma && (umma::smem_addr(raw) & 127u) == 0;
-    if (tma && tid == 0) {
-        umma::mbar_init(sbar, 1);
-        umma::mbar_expect_tx(sbar, kRawBytes);
-        umma::tma_load_2d(raw, dmap, x0 - tma_xpad<IN, R>(), y0 - R, sbar);
+    if (tma) {
+        if (tid == 0) {
+            umma::mbar_init(sbar, 1);
+            umma::mbar_expect_tx(sbar, kRawBytes);
+            umma::tma_load_2d(raw, dmap, x0 - tma_xpad<IN, R>(), y0 - R, sbar);
+        }
+        __syncthreads();  // no thread polls the barrier before it is initialised
     }
-    __syncthreads();  // no thread polls the barrier before it is initialised
     const bool ok = tma && umma::mbar_wait(sbar, 0, 1 << 22);
     if (tma && !ok && tid == 0) atomicOr(g.err, kErrMmaWait);
     for (int i = tid; i < N; i += NT) {
