@@ -1030,12 +1030,16 @@ constexpr int kSTH = 8;
 template <int IN>
 __global__ void __launch_bounds__(kTW* kSTH, 4)
     k_denoise5(const Geo g, const char* __restrict__ disp, size_t dp, float* __restrict__ den, size_t denp,
-               uint8_t* __restrict__ mask, size_t mp, const __grid_constant__ CUtensorMap dmap, int use_tma) {
-    constexpr int R = 2, TW = kTW + 2 * R;
-    __shared__ int2 tile[TW * (kSTH + 2 * R)];
-    __shared__ __align__(128) unsigned char raw[tma_bw<IN, R, TW>() * (kSTH + 2 * R) * tma_esize<IN>() + 16];
+               uint8_t* __restrict__ mask, size_t mp) {
+    // plain loads: for the 2-pixel halo a TMA box measured slower
+    constexpr int R = 2, TW = kTW + 2 * R, N = TW * (kSTH + 2 * R);
+    __shared__ int2 tile[N];
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kSTH;
-    stage_tile<IN, R, kSTH, kTW * kSTH>(tile, raw, &dmap, use_tma, disp, dp, x0, y0, g, false);
+    for (int i = threadIdx.y * kTW + threadIdx.x; i < N; i += kTW * kSTH) {
+        const int ly = i / TW, lx = i - ly * TW;
+        tile[i] = make_int2(load_code<IN>(disp, dp, x0 - R + lx, y0 - R + ly, g.W, g.H), 0);
+    }
+    __syncthreads();
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     if (x >= g.W || y >= g.H) return;
     const int2* c = tile + (threadIdx.y + R) * TW + threadIdx.x + R;
@@ -1187,15 +1191,12 @@ int stage_map(const Geo& g, const void* disp, size_t dp, CUtensorMap* m) {
 
 cudaError_t launch_denoise5(const Geo& g, const void* disp, size_t dp, float* den, size_t denp, uint8_t* mask,
                             size_t mp, cudaStream_t s) {
-    // plain loads: for the 2-pixel halo the TMA box measured slower (32.2 vs
-    // 31.2 us per 2048 x 1024 frame)
     const dim3 grid((g.W + kTW - 1) / kTW, (g.H + kSTH - 1) / kSTH), block(kTW, kSTH);
     const char* d = static_cast<const char*>(disp);
-    const CUtensorMap m{};
     switch (g.in_dtype) {
-        case SN_IN_F32: k_denoise5<SN_IN_F32><<<grid, block, 0, s>>>(g, d, dp, den, denp, mask, mp, m, 0); break;
-        case SN_IN_F16: k_denoise5<SN_IN_F16><<<grid, block, 0, s>>>(g, d, dp, den, denp, mask, mp, m, 0); break;
-        default: k_denoise5<SN_IN_U16X256><<<grid, block, 0, s>>>(g, d, dp, den, denp, mask, mp, m, 0); break;
+        case SN_IN_F32: k_denoise5<SN_IN_F32><<<grid, block, 0, s>>>(g, d, dp, den, denp, mask, mp); break;
+        case SN_IN_F16: k_denoise5<SN_IN_F16><<<grid, block, 0, s>>>(g, d, dp, den, denp, mask, mp); break;
+        default: k_denoise5<SN_IN_U16X256><<<grid, block, 0, s>>>(g, d, dp, den, denp, mask, mp); break;
     }
     return cudaGetLastError();
 }

@@ -110,3 +110,21 @@ def test_learned_ragged(P, H, W):
     clear = np.abs(qmin - TAU) >= 5e-3
     assert not ((gpu_gate != og) & clear).any()
     compare_frame(g, oracle.run_frame(disp, cam, gate=gpu_gate))
+
+
+def test_learned_u16_matches_f32(P):
+    # the learned kernel's TMA box for 16-bit input (16-byte aligned start
+    # x0 - 16): uint16 codes and FP32 disparities on the same 1/256-px grid
+    # give the same integer codes, hence identical outputs
+    s = make_scene("driving_2048x1024", frame=6)
+    same_codes = (s.disp_u16.astype(np.float64) / 256.0).astype(np.float32)
+    out = []
+    for arr, params in ((same_codes, {}), (s.disp_u16, dict(in_dtype=P.sn.SN_IN_U16X256))):
+        pipe = P.Pipeline(s.camera, s.W, s.H, learned=1, **params)
+        try:
+            out.append(run_gpu(pipe, arr))
+        finally:
+            pipe.close()
+    assert ((out[0]["mask"] & oracle.M_LEARNED) > 0).mean() > 0.5
+    for k in ("normals", "points", "labels", "mask"):
+        assert np.array_equal(out[0][k], out[1][k]), k

@@ -95,10 +95,10 @@ def test_st_threshold_at_the_laplacian(P):
         assert 0 < E[1:-1, 1:-1].mean() < 1
 
 
-@pytest.mark.parametrize("support", [1, 2])
+@pytest.mark.parametrize("support", [0, 1, 2])
 def test_driving_u16_and_f16_inputs(P, support):
-    # 16-bit inputs through the 16-byte aligned TMA boxes of both the
-    # covered-depth and the ST star
+    # 16-bit inputs through the 16-byte aligned TMA boxes of the 9x9 window,
+    # the covered-depth and the ST star
     s = make_scene("driving_2048x1024", frame=1)
     for arr, dt in ((s.disp_u16, P.sn.SN_IN_U16X256), (s.disp_f16, P.sn.SN_IN_F16)):
         g, ref = chain(P, arr, s.camera, in_dtype=dt, support=support, st_t=0.1)
