@@ -1,5 +1,6 @@
 // C ABI of the surface-normal library: argument checks, context and
 // workspace management, and the stage entry points declared in sn.h.
+#include <vector>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -48,6 +49,7 @@ struct sn_ctx {
     sn::GateDev gate;    // learned gate weights (learned contexts)
     float* gate_theta;   // their FP32 source on the device
     void* net_img;       // the weights as the frame kernel's shared memory holds them
+    int* star_pm;        // prefix moments of the star's rays (device)
     bool gate_loaded;
     bool prof;
     cudaEvent_t* ev;  // kProfFrames x (kStages + 1)
@@ -371,6 +373,12 @@ sn_status sn_create(const sn_camera* cam, int W, int H, const sn_params* pin, sn
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork_ev[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming);
     }
+    if (e == cudaSuccess) {
+        std::vector<int> pm((size_t)p.dirs * (p.steps + 1) * 6);
+        sn::star_prefix_moments(c->star, p.dirs, p.steps, pm.data());
+        e = cudaMalloc((void**)&c->star_pm, sizeof(int) * pm.size());
+        if (e == cudaSuccess) e = cudaMemcpy(c->star_pm, pm.data(), sizeof(int) * pm.size(), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess && p.learned) {
         e = sn::gate_alloc(c->gate);
         if (e == cudaSuccess) e = cudaMalloc(&c->gate_theta, sizeof(float) * sn::kGateParams);
@@ -382,6 +390,7 @@ sn_status sn_create(const sn_camera* cam, int W, int H, const sn_params* pin, sn
         return SN_ENOMEM;
     }
     g.err = c->ws.err;
+    g.star_pm = c->star_pm;
     snprintf(c->msg, sizeof(c->msg), "ok");
     *out = c;
     return SN_OK;
@@ -404,6 +413,7 @@ sn_status sn_destroy(sn_ctx* c) {
     if (c->gate.W1g) sn::gate_free(c->gate);
     if (c->gate_theta) cudaFree(c->gate_theta);
     if (c->net_img) cudaFree(c->net_img);
+    if (c->star_pm) cudaFree(c->star_pm);
     delete c;
     return SN_OK;
 }

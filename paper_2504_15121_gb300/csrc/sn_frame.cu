@@ -167,14 +167,18 @@ __device__ __forceinline__ void star8(const int2* c, int Dc, float wc, const Thr
     ray8<1, -1, LD, STRIDE>(c, Dc, wc, th, s);
 }
 
-// Any star table (union of rays, see StarTable), on the packed tile.
+// Any star table (union of rays, see StarTable), on the packed tile.  With
+// the rays' prefix moments (pm, see Geo::star_pm) a step accumulates only the
+// data sums, and each ray adds the moments of the prefix it took.
 __device__ __forceinline__ void star_table(const int2* c, int stride, int Dc, float wc, const Thr& th,
-                                           const StarTable& T, int dirs, int steps, AffSums& s) {
+                                           const StarTable& T, int dirs, int steps, const int* __restrict__ pm,
+                                           AffSums& s) {
     aff_zero(s);
     unsigned long long bits = 0ull;
     for (int j = 0; j < dirs; j++) {
         float wlo = wc, whi = wc;
         const int e0 = j * steps;
+        int kend = steps;  // the ray takes steps 0 .. kend - 1
         for (int k = 0; k < steps; k++) {
             const int e = e0 + k;
             const int cls = T.cls[e];
@@ -184,14 +188,32 @@ __device__ __forceinline__ void star_table(const int2* c, int stride, int Dc, fl
             const float w = __int_as_float(v.y);
             const float lo = fminf(wlo, w), hi = fmaxf(whi, w);
             const float diff = hi - lo;
-            if (diff > th.hi) break;
-            if (diff >= th.lo && cd_stop_from_w(lo, hi, Dc, th.K)) break;
+            if (diff > th.hi || (diff >= th.lo && cd_stop_from_w(lo, hi, Dc, th.K))) {
+                kend = k;
+                break;
+            }
             wlo = lo;
             whi = hi;
-            if (cls == 1)
-                aff_add(s, ou, ov, v.x - Dc);
-            else
+            if (cls == 1) {
+                if (pm) {
+                    const int dd = v.x - Dc;
+                    s.Bu += ou * dd;
+                    s.Bv += ov * dd;
+                } else {
+                    aff_add(s, ou, ov, v.x - Dc);
+                }
+            } else {
                 bits |= 1ull << T.bit[e];
+            }
+        }
+        if (pm) {
+            const int* q = pm + (j * (steps + 1) + kend) * 6;
+            s.N += __ldg(q);
+            s.Su += __ldg(q + 1);
+            s.Sv += __ldg(q + 2);
+            s.Suu += __ldg(q + 3);
+            s.Suv += __ldg(q + 4);
+            s.Svv += __ldg(q + 5);
         }
     }
     for (int b = 0; b < T.nshared; b++) {
@@ -416,7 +438,7 @@ __device__ __forceinline__ void plain_pixel(const Geo& g, const StarTable& T, co
         static_assert(R == 10, "the M = 8, s = 10 star needs a halo of 10");
         star8<10, kTW + 2 * R>(c, Dc, __int_as_float(cc.y), make_thr(g, Dc), s);
     } else if constexpr (VAR == 1) {
-        star_table(c, TWR, Dc, __int_as_float(cc.y), make_thr(g, Dc), T, g.dirs, g.steps, s);
+        star_table(c, TWR, Dc, __int_as_float(cc.y), make_thr(g, Dc), T, g.dirs, g.steps, g.star_pm, s);
     } else if constexpr (R > 0) {
         fixed_packed<R, kTW + 2 * R>(c, TWR, R, Dc, s);  // compile-time 9x9 (R = r_a = 4 >= r_d)
     } else {
@@ -1131,6 +1153,26 @@ cudaError_t encode_disp_map(CUtensorMap* m, const void* disp, size_t pitch, int 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+
+void star_prefix_moments(const StarTable& t, int dirs, int steps, int* pm) {
+    for (int j = 0; j < dirs; j++) {
+        int acc[6] = {0, 0, 0, 0, 0, 0};
+        for (int k = 0; k <= steps; k++) {
+            int* q = pm + (j * (steps + 1) + k) * 6;
+            for (int i = 0; i < 6; i++) q[i] = acc[i];
+            if (k == steps) break;
+            const int e = j * steps + k;
+            if (t.cls[e] != 1) continue;
+            const int u = t.ou[e], v = t.ov[e];
+            acc[0] += 1;
+            acc[1] += u;
+            acc[2] += v;
+            acc[3] += u * u;
+            acc[4] += u * v;
+            acc[5] += v * v;
+        }
+    }
+}
 
 bool star_is_m8(const StarTable& t, int dirs, int steps) {
     if (dirs != 8 || steps != 10) return false;

@@ -40,6 +40,10 @@ struct Geo {
     double st_F, st_t;
     float st_Ff, st_tf;
     int walk_limit;  // parent steps of one union-find walk in the component passes
+    // Moments of each star ray's prefixes (device, may be null): entry
+    // (j (steps + 1) + k) 6 + q holds, over the entries of ray j before step
+    // k that only this ray reaches, the sum of 1, u, v, u^2, u v, v^2 (q = 0..5)
+    const int* star_pm;
     int* err;        // device error word
 };
 
@@ -154,6 +158,9 @@ cudaError_t launch_net_image(const GateView& gv, void* img, cudaStream_t s);
 cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const void* disp, size_t dp,
                          const FrameOut& o, const GateView* gv, cudaStream_t s, Marks& mk);
 bool star_is_m8(const StarTable& t, int dirs, int steps);
+// Host: the prefix moments of the table's rays (dirs (steps + 1) 6 ints; see
+// Geo::star_pm).
+void star_prefix_moments(const StarTable& t, int dirs, int steps, int* pm);
 // Tensor map of a disparity image (the context's input type) for TMA tile
 // loads: W x H elements, rows `pitch` bytes apart (16-byte aligned base and
 // pitch), box bw x bh elements, zero outside the image.
