@@ -355,11 +355,21 @@ __device__ __forceinline__ bool denoise_exact(const int2* c, int stride, int rd_
             }
         }
     }
-    const long long M00 = (long long)Suu * Svv - (long long)Suv * Suv;
-    const long long M10 = (long long)Su * Svv - (long long)Sv * Suv;
-    const long long M20 = (long long)Su * Suv - (long long)Sv * Suu;
-    det = n * M00 - Su * M10 + Sv * M20;
-    num = b0 * M00 - b1 * M10 + b2 * M20;
+    if constexpr (RD == 2) {
+        // 5x5: |Su|, |Sv| <= 30, Suu, Svv <= 50, |Suv| <= 36, so the cofactors
+        // (<= 2580) and det (<= 217,300) fit in 32 bits; num needs 64
+        const int M00 = Suu * Svv - Suv * Suv;
+        const int M10 = Su * Svv - Sv * Suv;
+        const int M20 = Su * Suv - Sv * Suu;
+        det = n * M00 - Su * M10 + Sv * M20;
+        num = (long long)b0 * M00 - (long long)b1 * M10 + (long long)b2 * M20;
+    } else {
+        const long long M00 = (long long)Suu * Svv - (long long)Suv * Suv;
+        const long long M10 = (long long)Su * Svv - (long long)Sv * Suv;
+        const long long M20 = (long long)Su * Suv - (long long)Sv * Suu;
+        det = n * M00 - Su * M10 + Sv * M20;
+        num = b0 * M00 - b1 * M10 + b2 * M20;
+    }
     return det > 0 && (long long)Dc * det + num > 0;
 }
 
