@@ -274,29 +274,55 @@ static __device__ __noinline__ void solve_normal_f64(long long nu_i, long long n
 // anchor_f64() in FP64 when the conditioning flag trips, both in code units)
 // enters through the first moments only.  dtil is the denoised disparity in
 // pixels.  Returns false if the support does not determine the gradient.
-template <class AnchorF64>
+// STAR8: the support lies in the compile-time M = 8, s = 10 star, so
+// |Su|, |Sv| <= 222, Suu, Svv <= 1330 and |Suv| <= 560: det <= 1,768,900,
+// 1024 det, alpha gamma and the first-moment cofactors fit in 32 bits (the
+// data cofactors nu, nv still need 64).
+template <bool STAR8 = false, class AnchorF64>
 __device__ __forceinline__ bool solve_normal_dc(const AffSums& s, int Dc, float dcf, AnchorF64 anchor_f64,
                                                 float dtil, int x, int y, const Geo& g, float n[3],
                                                 bool& fp64) {
     fp64 = false;
     if (s.N < 3) return false;
-    const long long a = s.Suu, b = s.Suv, gm = s.Svv;
-    const long long det = a * gm - b * b;
-    if (det <= 0) return false;
-    fp64 = 1024ll * det < a * gm;
-    // exact parts of gamma b_u - beta b_v and alpha b_v - beta b_u
-    const long long nu_i = gm * s.Bu - b * s.Bv;
-    const long long nv_i = a * s.Bv - b * s.Bu;
-    const long long cu = gm * s.Su - b * s.Sv;
-    const long long cv = a * s.Sv - b * s.Su;
+    long long det, nu_i, nv_i, cu, cv;
+    float fdet, fcu, fcv;
+    if constexpr (STAR8) {
+        const int a = s.Suu, b = s.Suv, gm = s.Svv;
+        const int d32 = a * gm - b * b;
+        if (d32 <= 0) return false;
+        fp64 = 1024 * d32 < a * gm;
+        // exact parts of gamma b_u - beta b_v and alpha b_v - beta b_u
+        nu_i = (long long)gm * s.Bu - (long long)b * s.Bv;
+        nv_i = (long long)a * s.Bv - (long long)b * s.Bu;
+        const int cu32 = gm * s.Su - b * s.Sv, cv32 = a * s.Sv - b * s.Su;
+        det = d32;
+        cu = cu32;
+        cv = cv32;
+        fdet = (float)d32;  // exact: below 2^24
+        fcu = (float)cu32;
+        fcv = (float)cv32;
+    } else {
+        const long long a = s.Suu, b = s.Suv, gm = s.Svv;
+        det = a * gm - b * b;
+        if (det <= 0) return false;
+        fp64 = 1024ll * det < a * gm;
+        // exact parts of gamma b_u - beta b_v and alpha b_v - beta b_u
+        nu_i = gm * s.Bu - b * s.Bv;
+        nv_i = a * s.Bv - b * s.Bu;
+        cu = gm * s.Su - b * s.Sv;
+        cv = a * s.Sv - b * s.Su;
+        fdet = i64_to_f32(det);
+        fcu = i64_to_f32(cu);
+        fcv = i64_to_f32(cv);
+    }
     if (fp64) {
         solve_normal_f64(nu_i, nv_i, cu, cv, det, Dc, anchor_f64(), x, y, g, n);
         return true;
     }
     {
-        const float inv = 1.0f / (256.0f * i64_to_f32(det));
-        const float gu = fmaf(-dcf, i64_to_f32(cu), i64_to_f32(nu_i)) * inv;
-        const float gv = fmaf(-dcf, i64_to_f32(cv), i64_to_f32(nv_i)) * inv;
+        const float inv = 1.0f / (256.0f * fdet);
+        const float gu = fmaf(-dcf, fcu, i64_to_f32(nu_i)) * inv;
+        const float gv = fmaf(-dcf, fcv, i64_to_f32(nv_i)) * inv;
         const float mx = gu;
         const float my = gv * g.fy_over_fx;
         const float mz = (dtil - gu * ((float)x - g.cx) - gv * ((float)y - g.cy)) / g.fx;
@@ -309,10 +335,11 @@ __device__ __forceinline__ bool solve_normal_dc(const AffSums& s, int Dc, float 
 }
 
 // Same, with the anchor taken from a denoised disparity dtil (pixels).
+template <bool STAR8 = false>
 __device__ __forceinline__ bool solve_normal(const AffSums& s, int Dc, float dtil, int x, int y,
                                              const Geo& g, float n[3], bool& fp64) {
     const float dcf = dtil * 256.0f - (float)Dc;
-    return solve_normal_dc(
+    return solve_normal_dc<STAR8>(
         s, Dc, dcf, [=] { return (double)dtil * 256.0 - (double)Dc; }, dtil, x, y, g, n, fp64);
 }
 

@@ -431,7 +431,8 @@ __device__ __forceinline__ void plain_pixel(const Geo& g, const StarTable& T, co
     r.m = SN_MASK_VALID;
     long long num, det;
     const bool fit = denoise_exact<RD>(c, TWR, g.r_d, Dc, g.K_range, num, det);
-    const float dcf = fit ? i64_to_f32(num) / i64_to_f32(det) : 0.0f;
+    // a 5x5 det is below 2^24 (exact in FP32)
+    const float dcf = fit ? i64_to_f32(num) / (RD == 2 ? (float)(int)det : i64_to_f32(det)) : 0.0f;
     if (fit) r.m |= SN_MASK_DENOISED;
     r.dtil = ((float)Dc + dcf) * (1.0f / 256.0f);
     AffSums s;
@@ -455,8 +456,8 @@ __device__ __forceinline__ void plain_pixel(const Geo& g, const StarTable& T, co
         fixed_packed(c, TWR, g.r_a, Dc, s);
     }
     bool fp64;
-    if (solve_normal_dc(s, Dc, dcf, [=] { return fit ? (double)num / (double)det : 0.0; }, r.dtil, x, y, g, r.n,
-                        fp64))
+    if (solve_normal_dc<VAR == 2 || VAR == 3 || VAR == 5>(
+            s, Dc, dcf, [=] { return fit ? (double)num / (double)det : 0.0; }, r.dtil, x, y, g, r.n, fp64))
         r.m |= SN_MASK_NORMAL | (fp64 ? SN_MASK_FP64 : 0);
     pix_points(g, x, y, r);
 }
@@ -1112,7 +1113,7 @@ __global__ void __launch_bounds__(kTW* kSTH, 4)
         AffSums s;
         star8<10, TW>(c, Dc, __int_as_float(c[0].y), make_thr(g, Dc), s);
         bool fp64;
-        if (solve_normal(s, Dc, dtil, x, y, g, n, fp64)) m |= SN_MASK_NORMAL | (fp64 ? SN_MASK_FP64 : 0);
+        if (solve_normal<true>(s, Dc, dtil, x, y, g, n, fp64)) m |= SN_MASK_NORMAL | (fp64 ? SN_MASK_FP64 : 0);
     }
     if (g.normal_fmt == SN_NORMALS_F32X3) {
         const size_t plane = (size_t)g.H * np;
