@@ -325,7 +325,7 @@ __device__ __forceinline__ bool solve_normal_dc(const AffSums& s, int Dc, float 
         const float gv = fmaf(-dcf, fcv, i64_to_f32(nv_i)) * inv;
         const float mx = gu;
         const float my = gv * g.fy_over_fx;
-        const float mz = (dtil - gu * ((float)x - g.cx) - gv * ((float)y - g.cy)) / g.fx;
+        const float mz = (dtil - gu * ((float)x - g.cx) - gv * ((float)y - g.cy)) * g.inv_fx;
         const float r = rsqrtf(fmaf(mx, mx, fmaf(my, my, mz * mz)));
         n[0] = -mx * r;
         n[1] = -my * r;

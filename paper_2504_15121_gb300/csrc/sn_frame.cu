@@ -476,14 +476,16 @@ __device__ __forceinline__ void fast_pixel(const Geo& g, int Dc, const WinSums& 
                                            PixOut& r) {
     pix_zero(r);
     r.m = SN_MASK_VALID | SN_MASK_LEARNED;
+    // the 5x5 window bounds the moments (as in denoise_exact<2>): the
+    // cofactors and det fit in 32 bits, det below 2^24
     const int b0 = w2.SD - w2.n * Dc, b1 = w2.SuD - w2.Su * Dc, b2 = w2.SvD - w2.Sv * Dc;
-    const long long M00 = (long long)w2.Suu * w2.Svv - (long long)w2.Suv * w2.Suv;
-    const long long M10 = (long long)w2.Su * w2.Svv - (long long)w2.Sv * w2.Suv;
-    const long long M20 = (long long)w2.Su * w2.Suv - (long long)w2.Sv * w2.Suu;
-    const long long det = w2.n * M00 - w2.Su * M10 + w2.Sv * M20;
-    const long long num = b0 * M00 - b1 * M10 + b2 * M20;
+    const int M00 = w2.Suu * w2.Svv - w2.Suv * w2.Suv;
+    const int M10 = w2.Su * w2.Svv - w2.Sv * w2.Suv;
+    const int M20 = w2.Su * w2.Suv - w2.Sv * w2.Suu;
+    const int det = w2.n * M00 - w2.Su * M10 + w2.Sv * M20;
+    const long long num = (long long)b0 * M00 - (long long)b1 * M10 + (long long)b2 * M20;
     const bool fit = det > 0 && (long long)Dc * det + num > 0;
-    const float dcf = fit ? i64_to_f32(num) / i64_to_f32(det) : 0.0f;
+    const float dcf = fit ? i64_to_f32(num) / (float)det : 0.0f;
     if (fit) r.m |= SN_MASK_DENOISED;
     r.dtil = ((float)Dc + dcf) * (1.0f / 256.0f);
     AffSums s;
@@ -1082,7 +1084,7 @@ __global__ void __launch_bounds__(kTW* kSTH, 4)
     if (Dc > 0) {
         long long num, det;
         const bool fit = denoise_exact<2>(c, TW, 2, Dc, g.K_range, num, det);
-        const float dcf = fit ? i64_to_f32(num) / i64_to_f32(det) : 0.0f;
+        const float dcf = fit ? i64_to_f32(num) / (float)(int)det : 0.0f;  // 5x5: det below 2^24
         out = ((float)Dc + dcf) * (1.0f / 256.0f);
         m = SN_MASK_VALID | (fit ? SN_MASK_DENOISED : 0);
     }
