@@ -80,3 +80,42 @@ def test_frozen_extremes_walk():
         assert (n1, A1) == (n2, A2)
         if n1 < L:  # the exact tail only ever looks at the failing step's spread
             assert f1 == f2
+
+
+def test_denoise_5x5_cofactors_fit_32_bits():
+    # every subset of the 5x5 window (the centre always passes its own range
+    # gate): the 3x3 cofactors and the determinant of the denoise solve stay
+    # far inside 32 bits and below 2^24 (exact in FP32), as the kernels assume
+    ou = np.array([u for v in range(-2, 3) for u in range(-2, 3) if (u, v) != (0, 0)], np.int64)
+    ov = np.array([v for v in range(-2, 3) for u in range(-2, 3) if (u, v) != (0, 0)], np.int64)
+    worst = np.zeros(4, np.int64)
+    for lo in range(0, 1 << 24, 1 << 20):
+        m = np.arange(lo, lo + (1 << 20), dtype=np.int64)
+        bits = ((m[:, None] >> np.arange(24)) & 1).astype(np.int64)
+        n = bits.sum(1) + 1
+        Su, Sv = bits @ ou, bits @ ov
+        Suu, Svv, Suv = bits @ (ou * ou), bits @ (ov * ov), bits @ (ou * ov)
+        M00 = Suu * Svv - Suv * Suv
+        M10 = Su * Svv - Sv * Suv
+        M20 = Su * Suv - Sv * Suu
+        det = n * M00 - Su * M10 + Sv * M20
+        worst = np.maximum(worst, [np.abs(a).max() for a in (M00, M10, M20, det)])
+    assert worst[:3].max() <= 2580 and worst[3] <= 217_300 < 1 << 24, worst
+
+
+def test_star8_moments_fit_32_bits():
+    # the compile-time M = 8, s = 10 star: distinct offsets of each ray
+    # (rounding half away from zero); the largest support bounds every sum
+    import math
+    pts = set()
+    for j in range(8):
+        th = 2 * math.pi * j / 8
+        for k in range(1, 11):
+            u, v = math.cos(th) * k, math.sin(th) * k
+            pts.add((int(math.copysign(math.floor(abs(u) + 0.5), u)), int(math.copysign(math.floor(abs(v) + 0.5), v))))
+    pts.discard((0, 0))
+    Su = sum(abs(u) for u, v in pts)
+    Suu = sum(u * u for u, v in pts)
+    Suv = sum(abs(u * v) for u, v in pts)
+    assert len(pts) == 68 and Su == 222 and Suu == 1330 and Suv == 560
+    assert 1024 * Suu * Suu < 1 << 31  # 1024 det <= 1024 Suu Svv
