@@ -282,6 +282,17 @@ sn_status sn_normals_noalloc(const sn_camera *cam, const sn_params *p, int W, in
                              size_t disp_pitch, void *normals, size_t normals_pitch, uint8_t *mask,
                              size_t mask_pitch, sn_stream stream);
 
+/* Error status of the allocation-free path (no counterpart in the paper).
+ * The kernels of sn_normals_noalloc bound every wait for an asynchronous
+ * tile copy; one that gives up sets a bit in a static device error word of
+ * the library (its frame's outputs are then undefined, and the call that
+ * enqueued it has already returned SN_OK).  This call waits for `stream`,
+ * reads that word on the current device and clears it: SN_OK if no wait gave
+ * up since the previous check, SN_ETIMEOUT if one did, SN_ECUDA on a CUDA
+ * error.  It allocates nothing (two synchronous copies between the word and
+ * a host variable). */
+sn_status sn_noalloc_check_device(sn_stream stream);
+
 /* Loads the learned gate's weights (format version, BF16 weights, FP32
  * biases; see the package's gate module).  Copies synchronously. */
 sn_status sn_load_gate_weights(sn_ctx *ctx, const void *blob, size_t bytes);

@@ -647,7 +647,16 @@ __device__ __forceinline__ void stage_tile(int2* tile, unsigned char* raw, const
         __syncthreads();  // no thread polls the barrier before it is initialised
     }
     const bool ok = tma && umma::mbar_wait(sbar, 0, 1 << 22);
-    if (tma && !ok && tid == 0) atomicOr(g.err, kErrMmaWait);
+    if (tma && !ok) {
+        // Gave up: every thread that did reports it (the polls of different
+        // threads may end on either side of a late completion), converts no
+        // box entry (its tile entries become invalid codes) and waits once
+        // more, again bounded, for the copy still in flight, so that this
+        // CTA's shared memory is not handed to another CTA while the copy may
+        // still write it.  The frame's outputs are undefined after this.
+        atomicOr(g.err, kErrMmaWait);
+        umma::mbar_wait(sbar, 0, 1 << 24);
+    }
     for (int i = tid; i < N; i += NT) {
         const int ly = i / TW, lx = i - ly * TW;
         const int b = ly * BW + lx + tma_xpad<IN, R>() - R;

@@ -155,7 +155,12 @@ __global__ void __launch_bounds__(kCclTile * 8)
         __syncthreads();  // no thread polls the barrier before it is initialised
     }
     const bool ok = tma && umma::mbar_wait(&sbar, 0, 1 << 22);
-    if (tma && !ok && tid == 0) atomicOr(g.err, kErrMmaWait);
+    if (tma && !ok) {
+        // gave up: report, use no box entry, and wait once more (bounded) for
+        // the copy in flight before the CTA can exit (as in stage_tile)
+        atomicOr(g.err, kErrMmaWait);
+        umma::mbar_wait(&sbar, 0, 1 << 24);
+    }
 #pragma unroll
     for (int k = 0; k < kRows; k++) {
         const int r = threadIdx.y + 8 * k, i = r * kCclTile + lane;

@@ -20,7 +20,8 @@
 // until the process exits.  Every call overwrites the elements it reads
 // before reading them, so nothing needs clearing between calls.
 static __device__ __align__(256) float g_noalloc_den[SN_NOALLOC_MAX_ELEMS];
-// Error word handed to the kernels (they only set bits on failed bounded waits).
+// Error word handed to the kernels (they only set bits on failed bounded
+// waits); sn_noalloc_check_device reads and clears it.
 static __device__ __align__(256) int g_noalloc_err[4];
 
 namespace {
@@ -95,4 +96,21 @@ extern "C" sn_status sn_normals_noalloc(const sn_camera* cam, const sn_params* p
         e = sn::launch_affine(g, t, disp, disp_pitch, s->den, den_pitch_elems * 4, normals, normals_pitch, mask,
                               mask_pitch, false, stream, mk);
     return e == cudaSuccess ? SN_OK : SN_ECUDA;
+}
+
+// The kernels behind sn_normals_noalloc report a bounded wait that gave up
+// by setting bits of g_noalloc_err (they never clear it).  This reads and
+// clears the word of the current device after `stream` has finished, with
+// two synchronous copies between the symbol and a host variable (nothing is
+// allocated).
+extern "C" sn_status sn_noalloc_check_device(sn_stream stream) {
+    DeviceScratch* s = nullptr;
+    if (scratch_for_device(&s) != cudaSuccess) return SN_ECUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return SN_ECUDA;
+    int err = 0;
+    if (cudaMemcpyFromSymbol(&err, g_noalloc_err, sizeof(int)) != cudaSuccess) return SN_ECUDA;
+    if (err == 0) return SN_OK;
+    const int zero = 0;
+    if (cudaMemcpyToSymbol(g_noalloc_err, &zero, sizeof(int)) != cudaSuccess) return SN_ECUDA;
+    return SN_ETIMEOUT;
 }

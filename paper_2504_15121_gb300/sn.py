@@ -93,6 +93,7 @@ def _load():
         "sn_launch_count": ([vp], C.c_uint64),
         "sn_normals_noalloc": ([C.POINTER(sn_camera), C.POINTER(sn_params), i, i, vp, sz, vp, sz, vp,
                                 sz, vp], i),
+        "sn_noalloc_check_device": ([vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -108,7 +109,7 @@ EXPORTS = ("sn_version", "sn_default_params", "sn_create", "sn_destroy", "sn_den
            "sn_affine_normals", "sn_components", "sn_pointcloud", "sn_run_frame",
            "sn_load_gate_weights", "sn_star_offsets", "sn_check_device", "sn_status_string",
            "sn_last_error", "sn_set_profiling", "sn_stage_count", "sn_stage_name",
-           "sn_stage_times", "sn_launch_count", "sn_normals_noalloc", "sn_cross_normals",
+           "sn_stage_times", "sn_launch_count", "sn_normals_noalloc", "sn_noalloc_check_device", "sn_cross_normals",
            "sn_pca_normals", "sn_set_walk_limit", "sn_run_frame_host")
 
 
@@ -327,3 +328,9 @@ def sn_normals_noalloc(cam, params, disp, normals, mask, stream=None):
     st = lib.sn_normals_noalloc(C.byref(c), C.byref(params) if params is not None else None, W, H,
                                 d, dp, n, np_, m, mp, _stream(stream))
     _check(None, st)
+
+
+def sn_noalloc_check_device(stream=None):
+    """Reads and clears the allocation-free path's device error word after
+    `stream` completes; raises SnError(SN_ETIMEOUT) if a bounded wait gave up."""
+    _check(None, lib.sn_noalloc_check_device(_stream(stream)))

@@ -142,6 +142,72 @@ def test_ragged_random(P, H, W, support):
     compare_frame(g, ref)
 
 
+def _fallback_frame(rng, H=96, W=160):
+    """Integer codes with the denoise fallback's windows placed on purpose:
+    isolated pixels, one-row and one-column strips, diagonals (singular
+    normal matrices), and centres of 100 between a column of 1s and a column
+    of 200s (with k_range = 1 a determined fit with intercept < 0), over a
+    sparse random background."""
+    D = np.where(rng.random((H, W)) < 0.15, rng.integers(3000, 60000, (H, W)), 0).astype(np.int32)
+    for _ in range(12):
+        v, u = int(rng.integers(3, H - 3)), int(rng.integers(3, W - 12))
+        D[v - 2:v + 3, u - 2:u + 3] = 0
+        D[v, u] = int(rng.integers(100, 90000))                    # isolated
+    for _ in range(6):
+        v, u = int(rng.integers(3, H - 3)), int(rng.integers(3, W - 14))
+        D[v - 2:v + 3, u - 2:u + 12] = 0
+        D[v, u:u + 10] = 5000 + 17 * np.arange(10)               # one row
+        v, u = int(rng.integers(3, H - 14)), int(rng.integers(3, W - 3))
+        D[v - 2:v + 12, u - 2:u + 3] = 0
+        D[v:v + 10, u] = 8000 + 11 * np.arange(10)               # one column
+        v, u = int(rng.integers(3, H - 10)), int(rng.integers(3, W - 10))
+        D[v - 2:v + 9, u - 2:u + 9] = 0
+        for k in range(7):
+            D[v + k, u + k] = 4000 + 3 * k                        # diagonal
+    for _ in range(10):
+        v, u = int(rng.integers(3, H - 3)), int(rng.integers(3, W - 4))
+        D[v - 2:v + 3, u - 2:u + 3] = 0
+        D[v, u] = 100
+        D[v - 2:v + 3, u + 1] = 1
+        D[v - 2:v + 3, u + 2] = 200                               # intercept < 0 at (u, v)
+    return D
+
+
+@pytest.mark.parametrize("k_range", [0.05, 1.0])
+def test_denoise_fallback_windows(P, k_range):
+    # the denoise fallback (singular window, or intercept <= 0 with k_range =
+    # 1) on purpose, through the fused chain and the stage entry point: den =
+    # D / 256 and DENOISED clear exactly where the oracle falls back
+    rng = np.random.default_rng(int(k_range * 100) + 5)
+    D = _fallback_frame(rng)
+    disp = codes_to_f32(D)
+    H, W = D.shape
+    g, ref = chain(P, disp, CAM, k_range=k_range)
+    compare_frame(g, ref)
+    fb = (ref.mask & oracle.M_VALID > 0) & (ref.mask & oracle.M_DENOISED == 0)
+    assert fb.sum() >= 40, fb.sum()
+    assert (g["den"][fb] == D[fb] / 256.0).all()
+    if k_range == 1.0:
+        # some fallbacks are determined fits (rank 3) with intercept <= 0
+        den_o, fit = oracle.denoise(D, oracle.Params(k_range=1.0))
+        centres = (D == 100) & (fit == 0)
+        assert centres.sum() >= 5
+    pipe = P.Pipeline(CAM, W, H, k_range=k_range)
+    try:
+        sn = P.sn
+        d = pipe.upload(disp)
+        den = sn.empty_image(H, W, torch.float32)
+        m1 = sn.empty_image(H, W, torch.uint8)
+        sn.sn_denoise(pipe.ctx, d, den, m1)
+        torch.cuda.synchronize()
+        sn.sn_check_device(pipe.ctx)
+        assert np.array_equal(m1.cpu().numpy(), ref.mask & (oracle.M_VALID | oracle.M_DENOISED))
+        err = np.abs(den.cpu().numpy().astype(np.float64) - ref.den)
+        assert (err <= 1e-6 * ref.den).all()
+    finally:
+        pipe.close()
+
+
 def test_all_invalid(P):
     disp = np.zeros((37, 45), np.float32)
     disp[3, 4] = np.nan

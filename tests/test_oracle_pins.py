@@ -151,6 +151,69 @@ def test_denoise_gate_is_inclusive():
     assert den[2, 2] == 65536 / 256.0
 
 
+def _lstsq_intercept(D, u, v, r, K):
+    """Intercept of the least-squares plane over the range-gated window,
+    by numpy's lstsq on the explicit design matrix, and its rank."""
+    H, W = D.shape
+    Dc = int(D[v, u])
+    rows, ys = [], []
+    for ov in range(-r, r + 1):
+        for ou in range(-r, r + 1):
+            uu, vv = u + ou, v + ov
+            if 0 <= uu < W and 0 <= vv < H and D[vv, uu] > 0 and abs(int(D[vv, uu]) - Dc) * 65536 <= K * Dc:
+                rows.append([1.0, ou, ov])
+                ys.append(D[vv, uu] / 256.0)
+    A = np.array(rows, np.float64)
+    return np.linalg.lstsq(A, np.array(ys), rcond=None)[0][0], np.linalg.matrix_rank(A)
+
+
+def test_denoise_fallback_on_singular_windows():
+    # Reading: where the 3x3 normal matrix of the gated window is singular
+    # (the passing samples lie on one line) the denoised value is the raw
+    # centre code / 256 and DENOISED stays clear.  Hand-built cases: an
+    # isolated pixel, a one-row strip, a one-column strip, a diagonal, and a
+    # centre whose neighbours are all gated out but one.
+    D = np.zeros((12, 30), np.int32)
+    D[2, 2] = 5000                                   # isolated
+    D[6, 4:14] = 7000 + 13 * np.arange(10)           # one row
+    D[1:11, 20] = 9000 + 7 * np.arange(10)           # one column
+    for k in range(6):
+        D[5 + k % 6, 23 + k] = 4000 + 5 * k          # a diagonal
+    D[9:12, 1:4] = 30000                             # 3x3 block ...
+    D[10, 2] = 20000                                 # ... whose centre gates all but one out
+    D[9, 1] = 20100
+    den, ok = oracle.denoise(D, Params(k_range=0.05))
+    K = round(0.05 * 65536)
+    cases = [(2, 2), (6, 8), (6, 13), (4, 20), (10, 20), (7, 25), (10, 2)]
+    for v, u in cases:
+        c, rank = _lstsq_intercept(D, u, v, 2, K)
+        assert rank < 3, (u, v)
+        assert den[v, u] == D[v, u] / 256.0 and ok[v, u] == 0, (u, v, den[v, u])
+
+
+def test_denoise_fallback_on_nonpositive_intercept():
+    # Reading: a determined fit whose intercept c is <= 0 also falls back to
+    # the raw centre code / 256 with DENOISED clear.  With k_range = 1 the gate
+    # admits codes in [1, 2 Dc]; a centre of 100 between a column of 1s and
+    # a column of 200s tilts the plane so that numpy's lstsq gives c < 0.
+    D = np.zeros((9, 9), np.int32)
+    D[4, 4] = 100
+    D[2:7, 5] = 1
+    D[2:7, 6] = 200
+    K = 65536
+    c, rank = _lstsq_intercept(D, 4, 4, 2, K)
+    assert rank == 3 and c < 0, c
+    den, ok = oracle.denoise(D, Params(k_range=1.0))
+    assert den[4, 4] == 100 / 256.0 and ok[4, 4] == 0
+    # control: the same window with the 200s lowered to 60 has c > 0 and
+    # takes the fit
+    D[2:7, 6] = 60
+    c, rank = _lstsq_intercept(D, 4, 4, 2, K)
+    assert rank == 3 and c > 0, c
+    den, ok = oracle.denoise(D, Params(k_range=1.0))
+    assert ok[4, 4] == 1 and abs(den[4, 4] - c) < 1e-9
+
+
 def test_denoise_exact_on_plane():
     D = int_plane(30, 20, 20000, 37, -23)
     den, ok = oracle.denoise(D)
