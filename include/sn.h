@@ -96,9 +96,11 @@ enum {
  *             needs the default star (support, dirs 8, steps 10, r_denoise 2,
  *             r_affine 4), else SN_ENOTSUP.  A small network gives each pixel
  *             the probability q that the 5x5 patch centred there shows one
- *             surface; a valid pixel whose q values over the
- *             (2 SN_LEARNED_RADIUS - 3)^2 neighbourhood (pixels outside the
- *             image included) are all >= tau is certified (SN_MASK_LEARNED):
+ *             surface; a valid pixel whose q values at the lattice points
+ *             (pixels with both coordinates even, outside the image
+ *             included) within SN_LEARNED_RADIUS - 1 of it are all >= tau is
+ *             certified (SN_MASK_LEARNED; the 5x5 patches centred there cover
+ *             its full window):
  *             its denoise fit takes every valid sample of the 5x5 window (no
  *             range gate) and its affine fit every valid sample of the
  *             (2 SN_LEARNED_RADIUS + 1)^2 window but the centre (no
@@ -242,6 +244,28 @@ typedef struct {
  * CUDA stream capture (the fork and join become graph edges).  While
  * profiling is on (sn_set_profiling), all four launches stay on `stream`. */
 sn_status sn_run_frame(sn_ctx *ctx, const sn_frame_in *in, sn_frame_out *out, sn_stream stream);
+
+/* The learned gate's probability map (no counterpart in the paper: the
+ * gate is this library's own addition, see `learned` above).  For every
+ * pixel p, q[p] = sigmoid(z . W3 + b3) of the gate network: features of the
+ * codes (the FP32 differences of the FP32 log2 of the codes of p's right and
+ * lower neighbours and of p, 0 where either is invalid; p's validity), two
+ * 3x3 convolutions with ReLU in BF16 with FP32 accumulation, a 1x1 head.
+ * The gate reads q only at the lattice points (pixels with both
+ * coordinates even), and this call evaluates it there: q[p] at pixels with
+ * both coordinates even, NaN at the others.  Needs a learned context with
+ * weights loaded (else SN_EINVAL).
+ *   disp  [H][disp_pitch] input in the context's in_dtype
+ *   q     [H][q_pitch] float output */
+sn_status sn_gate_q(sn_ctx *ctx, const void *disp, size_t disp_pitch, float *q, size_t q_pitch, sn_stream stream);
+
+/* The table of log2 D for every disparity code D = 0..131071 that the gate's
+ * features read (FP32, the correctly rounded FP32 value of log2 D; NaN for
+ * D = 0, the invalid code), copied to HOST memory `out` (n >= 131072
+ * floats), for inspection and tests.  Fills the table on the current device
+ * first if no learned context did (a one-time kernel and a synchronisation).
+ * SN_EINVAL for a NULL pointer or n < 131072, SN_ECUDA on a CUDA error. */
+sn_status sn_gate_log2_table(float *out, int n);
 
 /* sn_run_frame on HOST buffers: copies the disparity (in->disp, host) to
  * the device, runs sn_run_frame, and copies normals, points, labels, mask

@@ -8,18 +8,21 @@ Network (frozen definition; the paper has no learned part -- it notes that
 the method is differentiable apart from the adaptive support, Sec. I-C):
 
   features f(p), 8 channels, from the integer disparity codes D (0 = invalid,
-  pixels outside the image invalid), L = log2 D:
+  pixels outside the image invalid), L = log2 D rounded to FP32:
       f0 = L(p + e_u) - L(p)   if p and p + e_u are valid, else 0
       f1 = L(p + e_v) - L(p)   if p and p + e_v are valid, else 0
+      (both differences in FP32 arithmetic)
       f2 = 1 if p is valid, else 0
       f3..f7 = 0
   h1 = relu(conv3x3(f) W1 + b1)          16 channels
   z  = relu(conv3x3(h1) W2 + b2)         16 channels
   q  = sigmoid(z . W3 + b3)              P(the 5x5 patch at p is one valid surface)
   conv3x3: out(p) = sum over o in {-1,0,1}^2 of W[(o_v+1)*3 + (o_u+1)] in(p + o).
-  gate(p) = (min over |o|_inf <= r - 2 of q(p + o) >= tau) and p is valid,
-  r the radius of the full window a certified pixel fits (the union of the
-  5x5 patches centred within r - 2 of p is that window).
+  gate(p) = (min of q(c) over the lattice points c (both coordinates even)
+  with |c - p|_inf <= r - 1 is >= tau) and p is valid, r the radius of the
+  full window a certified pixel fits: the 5x5 patches centred at those
+  lattice points cover p's (2r + 1)^2 window whatever the parity of p
+  (pixels outside the image count, as invalid pixels).
   Label of a patch: at least 13 of its 25 pixels are valid (pixels outside
   the image are invalid) and all its valid pixels show one primitive.
 
@@ -78,16 +81,18 @@ def features(D):
     """f for every pixel of an integer-code image (any shape [..., H, W])."""
     D = np.asarray(D)
     valid = D > 0
-    L = np.where(valid, np.log2(np.where(valid, D, 1).astype(np.float64)), 0.0)
+    # L = log2 D rounded to FP32, and the steps are FP32 differences of
+    # those values (the definition the kernel computes exactly)
+    L = np.where(valid, np.log2(np.where(valid, D, 1).astype(np.float64)), 0.0).astype(np.float32)
     f = np.zeros(D.shape + (N_IN,))
     vr = np.zeros_like(valid)
     vr[..., :, :-1] = valid[..., :, :-1] & valid[..., :, 1:]
     vd = np.zeros_like(valid)
     vd[..., :-1, :] = valid[..., :-1, :] & valid[..., 1:, :]
     dr = np.zeros(D.shape)
-    dr[..., :, :-1] = L[..., :, 1:] - L[..., :, :-1]
+    dr[..., :, :-1] = (L[..., :, 1:] - L[..., :, :-1]).astype(np.float64)
     dd = np.zeros(D.shape)
-    dd[..., :-1, :] = L[..., 1:, :] - L[..., :-1, :]
+    dd[..., :-1, :] = (L[..., 1:, :] - L[..., :-1, :]).astype(np.float64)
     f[..., 0] = np.where(vr, dr, 0.0)
     f[..., 1] = np.where(vd, dd, 0.0)
     f[..., 2] = valid.astype(np.float64)
@@ -128,18 +133,106 @@ def forward_image(D, theta, round_bf16=True, margin=0):
     return q[m:m + H + 2 * margin, m:m + W + 2 * margin] if m > 0 else q
 
 
-def gate_image(D, theta, tau, radius, round_bf16=True):
-    """(gate bits, q, min q over the (2 radius - 3)^2 neighbourhood) of an
-    image for a full window of the given radius; the minimum includes the q
-    of pixels outside the image (which are invalid pixels)."""
-    H, W = D.shape
-    m = radius - 2
-    qe = forward_image(D, theta, round_bf16, margin=m)
-    qmin = np.full((H, W), np.inf)
+def _lattice_min(qe, H, W, m):
+    """Minimum over the lattice points (even coordinates) within m of every
+    pixel; qe covers the image and m pixels around it (origin at -m)."""
+    ys, xs = np.mgrid[-m:H + m, -m:W + m]
+    qlat = np.where((ys % 2 == 0) & (xs % 2 == 0), qe, np.inf)
+    out = np.full((H, W), np.inf)
     for oy in range(2 * m + 1):
         for ox in range(2 * m + 1):
-            qmin = np.minimum(qmin, qe[oy:oy + H, ox:ox + W])
+            out = np.minimum(out, qlat[oy:oy + H, ox:ox + W])
+    return out
+
+
+def gate_image(D, theta, tau, radius, round_bf16=True):
+    """(gate bits, q, minimum of q over each pixel's lattice points) of an
+    image for a full window of the given radius; the minimum includes the q
+    of lattice points outside the image (which are invalid pixels)."""
+    H, W = D.shape
+    m = radius - 1
+    qe = forward_image(D, theta, round_bf16, margin=m)
+    qmin = _lattice_min(qe, H, W, m)
     return (qmin >= tau) & (D > 0), qe[m:m + H, m:m + W], qmin
+
+
+# ---------------------------------------------------------------- bounds of a kernel's q
+U_ACC = 2.0 ** -23       # unit error of one FP32 addition, rounding to nearest or towards zero
+SIGMOID_ABS = 2e-6       # absolute error allowed to the kernel's FP32 sigmoid
+
+
+def _gamma(n):
+    return n * U_ACC / (1.0 - n * U_ACC)
+
+
+def _conv3x3_pos_neg(lo, hi, W):
+    """Range of a valid 3x3 cross-correlation (no bias) over inputs known to
+    lie in [lo, hi] elementwise: each weight takes the end of the interval
+    that minimises (maximises) its product."""
+    Wp, Wn = np.maximum(W, 0.0), np.minimum(W, 0.0)
+    return (_conv3x3(lo, Wp, 0.0) + _conv3x3(hi, Wn, 0.0),
+            _conv3x3(hi, Wp, 0.0) + _conv3x3(lo, Wn, 0.0))
+
+
+def q_bounds(D, theta, margin=0):
+    """[q_lo, q_hi] for every pixel of an image and `margin` pixels around it:
+    the values a kernel may produce that computes the features exactly as
+    defined above, rounds weights, features and layer-1 activations to BF16
+    (nearest even), accumulates each convolution and the head in FP32 in any
+    order (each addition rounding to nearest or towards zero), and evaluates
+    the sigmoid within SIGMOID_ABS.  Bound per sum of n terms t_i (the bias
+    counted as a term): |fl(sum) - sum| <= gamma_n sum |t_i|,
+    gamma_n = n u / (1 - n u), u = 2^-23.  Where a layer-1 activation lies
+    within that bound of a BF16 rounding boundary both roundings are allowed;
+    the ranges then pass through layer 2, the ReLUs, the head and the sigmoid
+    by interval arithmetic (every step is monotone or linear)."""
+    w = unflatten(theta)
+    w = {k: (bf16(v) if k.startswith("W") else v) for k, v in w.items()}
+    H, W = D.shape
+    P = max(4, margin + 2)
+    Dp = np.zeros((H + 2 * P + 1, W + 2 * P + 1), D.dtype)
+    Dp[P:P + H, P:P + W] = D
+    f = bf16(features(Dp)[:-1, :-1])
+    # layer 1: 72 products (9 taps x 8 channels) and the bias
+    a1 = _conv3x3(f, w["W1"], w["b1"])
+    mag1 = _conv3x3(np.abs(f), np.abs(w["W1"]), np.abs(w["b1"]))
+    e1 = _gamma(9 * N_IN + 1) * mag1
+    h1_lo = bf16(np.maximum(a1 - e1, 0.0))
+    h1_hi = bf16(np.maximum(a1 + e1, 0.0))
+    # layer 2: 144 products and the bias
+    a2_lo, a2_hi = _conv3x3_pos_neg(h1_lo, h1_hi, w["W2"])
+    mag2 = _conv3x3(np.maximum(np.abs(h1_lo), np.abs(h1_hi)), np.abs(w["W2"]), np.abs(w["b2"]))
+    e2 = _gamma(9 * N_HID + 1) * mag2
+    a2_lo, a2_hi = a2_lo + w["b2"] - e2, a2_hi + w["b2"] + e2
+    z_lo, z_hi = np.maximum(a2_lo, 0.0), np.maximum(a2_hi, 0.0)
+    # head: 16 products and the bias, allowing the bias of layer 2 to be
+    # folded into it (sums over |W3| (|a2| + |b2|))
+    W3p, W3n = np.maximum(w["W3"], 0.0), np.minimum(w["W3"], 0.0)
+    l_lo = z_lo @ W3p + z_hi @ W3n + w["b3"][0]
+    l_hi = z_hi @ W3p + z_lo @ W3n + w["b3"][0]
+    mag3 = (np.maximum(np.abs(a2_lo), np.abs(a2_hi)) + np.abs(w["b2"])) @ np.abs(w["W3"]) + abs(w["b3"][0])
+    e3 = _gamma(2 * N_HID + 2) * mag3
+    q_lo = 1.0 / (1.0 + np.exp(-(l_lo - e3))) - SIGMOID_ABS
+    q_hi = 1.0 / (1.0 + np.exp(-(l_hi + e3))) + SIGMOID_ABS
+    m = P - 2 - margin
+    if m > 0:
+        q_lo = q_lo[m:m + H + 2 * margin, m:m + W + 2 * margin]
+        q_hi = q_hi[m:m + H + 2 * margin, m:m + W + 2 * margin]
+    return q_lo, q_hi
+
+
+def gate_bounds(D, theta, tau, radius):
+    """(surely certified, surely not certified, q_lo, q_hi) of every pixel:
+    the minimum of q over the pixel's lattice points (pixels outside the
+    image included) is >= tau for every q in the bounds, or < tau for every q
+    in them.  Pixels in neither set are undecided by the bounds."""
+    H, W = D.shape
+    m = radius - 1
+    lo, hi = q_bounds(D, theta, margin=m)
+    mlo = _lattice_min(lo, H, W, m)
+    mhi = _lattice_min(hi, H, W, m)
+    valid = D > 0
+    return (mlo >= tau) & valid, (mhi < tau) | ~valid, lo[m:m + H, m:m + W], hi[m:m + H, m:m + W]
 
 
 # ---------------------------------------------------------------- patches (training)

@@ -63,7 +63,8 @@ enum {
 };
 
 /* Radius of the full window that a pixel certified by the learned gate fits
- * (the gate certifies the union of 5x5 patches centred within radius - 2). */
+ * (the gate certifies the union of the 5x5 patches centred at the lattice
+ * points, both coordinates even, within radius - 1 of the pixel). */
 #define ORC_LEARNED_RADIUS 6
 
 int orc_learned_radius(void) { return ORC_LEARNED_RADIUS; }

@@ -48,7 +48,8 @@ struct sn_ctx {
     bool star8;  // the star table is the compile-time M = 8, s = 10 ray set
     sn::GateDev gate;    // learned gate weights (learned contexts)
     float* gate_theta;   // their FP32 source on the device
-    void* net_img;       // the weights as the frame kernel's shared memory holds them
+    void* net_img;       // the weights as the learned kernel's shared memory holds them
+    const float* log2tab;  // the library's table of log2 of every code (learned contexts)
     int* star_pm;        // prefix moments of the star's rays (device)
     bool gate_loaded;
     bool prof;
@@ -383,6 +384,7 @@ sn_status sn_create(const sn_camera* cam, int W, int H, const sn_params* pin, sn
         e = sn::gate_alloc(c->gate);
         if (e == cudaSuccess) e = cudaMalloc(&c->gate_theta, sizeof(float) * sn::kGateParams);
         if (e == cudaSuccess) e = cudaMalloc(&c->net_img, sn::kNetImageBytes);
+        if (e == cudaSuccess) e = sn::log2_table(&c->log2tab);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -541,7 +543,7 @@ sn_status sn_run_frame(sn_ctx* c, const sn_frame_in* in, sn_frame_out* out, sn_s
     if (c->p.learned) {
         if (!c->gate_loaded) return fail(c, SN_EINVAL, "learned context: gate weights not loaded");
         gv = sn::GateView{c->gate.W1g, c->gate.W2g, c->gate.b1, c->gate.b2, c->gate.W3, c->gate.b3, c->p.tau,
-                          c->net_img};
+                          c->net_img, c->log2tab};
     }
     const sn::GateView* g = c->p.learned ? &gv : nullptr;
     cudaError_t e;
@@ -564,6 +566,21 @@ sn_status sn_run_frame(sn_ctx* c, const sn_frame_in* in, sn_frame_out* out, sn_s
     }
     c->launches += mk.launches;
     return e == cudaSuccess ? SN_OK : cuda_fail(c, e, "sn_run_frame");
+}
+
+sn_status sn_gate_q(sn_ctx* c, const void* disp, size_t dpitch, float* q, size_t qp, sn_stream stream) {
+    if (!c) return SN_EINVAL;
+    if (!c->p.learned) return fail(c, SN_EINVAL, "sn_gate_q: context was not created with learned = 1");
+    if (!c->gate_loaded) return fail(c, SN_EINVAL, "sn_gate_q: gate weights not loaded");
+    sn_status st;
+    if ((st = check_buf(c, disp, dpitch, in_elem(c->p.in_dtype), "disp")) != SN_OK) return st;
+    if ((st = check_buf(c, q, qp, 4, "q")) != SN_OK) return st;
+    const sn::GateView gv{c->gate.W1g, c->gate.W2g, c->gate.b1, c->gate.b2, c->gate.W3, c->gate.b3, c->p.tau,
+                          c->net_img, c->log2tab};
+    const sn::FrameOut none{};
+    cudaError_t e = sn::launch_learned(c->geo, disp, dpitch, none, gv, q, qp, stream);
+    if (e == cudaSuccess) c->launches++;
+    return e == cudaSuccess ? SN_OK : cuda_fail(c, e, "sn_gate_q");
 }
 
 namespace {
@@ -665,7 +682,7 @@ sn_status sn_load_gate_weights(sn_ctx* c, const void* blob, size_t bytes) {
     if (e == cudaSuccess) e = sn::gate_layout(c->gate_theta, c->gate, nullptr);
     if (e == cudaSuccess) {
         const sn::GateView gv{c->gate.W1g, c->gate.W2g, c->gate.b1, c->gate.b2, c->gate.W3, c->gate.b3, c->p.tau,
-                              nullptr};
+                              nullptr, c->log2tab};
         e = sn::launch_net_image(gv, c->net_img, nullptr);
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -367,16 +367,15 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
 }
 
 // ---------------------------------------------------------------- learned gate
-// log2 of an integer disparity code (FP32)
-__device__ __forceinline__ float log2_code(int D) { return __log2f((float)D); }
-
-// Gate features of one pixel from its code and its right / lower
-// neighbours': log2 steps (0 where either pixel is invalid) and validity.
-// Training and inference both use this function.
-__device__ __forceinline__ void gate_feature(int Dc, int Dr, int Dd, float f[3]) {
-    const float Lc = Dc > 0 ? log2_code(Dc) : 0.0f;
-    f[0] = (Dc > 0 && Dr > 0) ? log2_code(Dr) - Lc : 0.0f;
-    f[1] = (Dc > 0 && Dd > 0) ? log2_code(Dd) - Lc : 0.0f;
+// Gate features of one pixel from the log2 of its own and its right / lower
+// neighbours' codes, read from `tab` (FP32 log2 of every code, NaN for code
+// 0): the FP32 differences (0 where either code is invalid) and the
+// validity.  The training kernels use this function; the inference kernel
+// computes the same values from a staged tile.
+__device__ __forceinline__ void gate_feature(const float* __restrict__ tab, int Dc, int Dr, int Dd, float f[3]) {
+    const float Lc = __ldg(tab + Dc);
+    f[0] = (Dc > 0 && Dr > 0) ? __ldg(tab + Dr) - Lc : 0.0f;
+    f[1] = (Dc > 0 && Dd > 0) ? __ldg(tab + Dd) - Lc : 0.0f;
     f[2] = Dc > 0 ? 1.0f : 0.0f;
 }
 

@@ -2,7 +2,8 @@
 // Adam) and the trainer entry points of include/sn_gate.h.
 //
 // Network (per pixel p, see include/sn_gate.h): features f(p) (8 channels:
-// log2-disparity steps to the right and down, validity, 5 zeros), a 3x3
+// FP32 steps of the FP32 log2 of the codes to the right and down, validity,
+// 5 zeros), a 3x3
 // convolution 8 -> 16 with ReLU, a 3x3 convolution 16 -> 16 with ReLU, a
 // 1x1 layer 16 -> 1 and a sigmoid.  Training works on 6x6 patches of
 // integer disparity codes (centre at [2][2]).  Every contraction is a BF16
@@ -82,13 +83,14 @@ cudaError_t gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, long long sam
 namespace {
 
 // Dp [B][36] -> F [B][25][8] (bf16): features at the 5x5 patch positions.
-__global__ void k_features(int B, const int* __restrict__ Dp, __nv_bfloat16* __restrict__ F) {
+__global__ void k_features(int B, const int* __restrict__ Dp, const float* __restrict__ tab,
+                           __nv_bfloat16* __restrict__ F) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)B * 25) return;
     const int b = (int)(i / 25), pos = (int)(i % 25), r = pos / 5, c = pos % 5;
     const int* d = Dp + (long long)b * 36;
     float f[3];
-    gate_feature(d[r * 6 + c], d[r * 6 + c + 1], d[(r + 1) * 6 + c], f);
+    gate_feature(tab, d[r * 6 + c], d[r * 6 + c + 1], d[(r + 1) * 6 + c], f);
     __nv_bfloat16* o = F + i * 8;
     o[0] = __float2bfloat16(f[0]);
     o[1] = __float2bfloat16(f[1]);
@@ -223,6 +225,7 @@ struct sn_gate_trainer {
     sn::GateDev w{};
     __nv_bfloat16 *F = nullptr, *A1 = nullptr, *A2 = nullptr, *dZ = nullptr, *dH1 = nullptr;
     float *C1 = nullptr, *C2 = nullptr, *dA2 = nullptr, *dW1g = nullptr, *dW2g = nullptr;
+    const float* log2tab = nullptr;  // FP32 log2 of every code (the library's table)
 };
 
 namespace {
@@ -233,7 +236,7 @@ unsigned blocks(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); 
 cudaError_t gate_pass(sn_gate_trainer* t, const int* Dp, const float* y, int B, float* q_out, cudaStream_t s) {
     using namespace sn;
     cudaError_t e;
-    k_features<<<blocks((long long)B * 25), 256, 0, s>>>(B, Dp, t->F);
+    k_features<<<blocks((long long)B * 25), 256, 0, s>>>(B, Dp, t->log2tab, t->F);
     k_im2col1<<<blocks((long long)B * 9 * 80), 256, 0, s>>>(B, t->F, t->A1);
     // C1 [B*9][16] = A1 [B*9][80] x W1g^T
     if ((e = gemm_bf16(B * 9, 16, 80, t->A1, 80, 1, t->w.W1g, 1, 80, t->C1, 16, s)) != cudaSuccess) return e;
@@ -279,6 +282,7 @@ sn_status sn_gate_trainer_create(int max_batch, const float* theta0, sn_gate_tra
     const size_t B = max_batch;
     cudaError_t e = cudaSuccess;
     const int P = sn::kGateParams;
+    if (e == cudaSuccess) e = sn::log2_table(&t->log2tab);
     if (e == cudaSuccess) e = alloc(&t->theta, P);
     if (e == cudaSuccess) e = alloc(&t->m, P);
     if (e == cudaSuccess) e = alloc(&t->v, P);

@@ -143,18 +143,31 @@ struct GateView {
     const float* W3;
     const float* b3;
     float tau;
-    // The same weights as the frame kernel's shared memory holds them
-    // (kNetImageBytes, written by launch_net_image): b1, b2, W3, b3 (FP32,
-    // padded to 208 bytes), then the B operands of the two convolutions in
-    // tcgen05 core-matrix layout (3 and 9 K-steps of 512 bytes).
+    // The same weights as the gate kernel's shared memory holds them
+    // (kNetImageBytes, written by launch_net_image): b1, -b2, W3 and
+    // b3 + W3 . b2 (FP32, padded to 208 bytes), then the B operands of the
+    // two convolutions in tcgen05 core-matrix layout (3 and 9 K-steps of 512
+    // bytes).
     const void* net;
+    const float* log2tab;  // log2_table()
 };
 constexpr int kNetImageBytes = 208 + 3 * 512 + 9 * 512;
 // Builds the image `net` from the other GateView fields.
 cudaError_t launch_net_image(const GateView& gv, void* img, cudaStream_t s);
+// Device address of the table of log2 of every disparity code (FP32,
+// correctly rounded; NaN for code 0) on the current device, filled by the
+// first call on that device (synchronously; not under stream capture).
+cudaError_t log2_table(const float** out);
+// The learned form: the gate kernel (network on the tensor cores, gate bits
+// into o.mask), then the chain kernel (certified pixels on the full window,
+// the others on the plain chain).  q != nullptr: only the gate kernel,
+// writing q at the pixels with both coordinates even and NaN at the others
+// (W x H floats, rows qp bytes apart).
+cudaError_t launch_learned(const Geo& g, const void* disp, size_t dp, const FrameOut& o, const GateView& gv, float* q,
+                           size_t qp, cudaStream_t s);
 // The fused frame kernel alone (denoise, support, fit, normal, point, mask;
 // not the labels).  gv == nullptr: plain chain; otherwise the learned
-// variant (star M = 8, s = 10, r_d = 2).
+// kernel (star M = 8, s = 10, r_d = 2).
 cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const void* disp, size_t dp,
                          const FrameOut& o, const GateView* gv, cudaStream_t s, Marks& mk);
 bool star_is_m8(const StarTable& t, int dirs, int steps);

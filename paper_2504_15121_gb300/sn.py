@@ -94,6 +94,8 @@ def _load():
         "sn_normals_noalloc": ([C.POINTER(sn_camera), C.POINTER(sn_params), i, i, vp, sz, vp, sz, vp,
                                 sz, vp], i),
         "sn_noalloc_check_device": ([vp], i),
+        "sn_gate_q": ([vp, vp, sz, vp, sz, vp], i),
+        "sn_gate_log2_table": ([vp, i], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -110,7 +112,7 @@ EXPORTS = ("sn_version", "sn_default_params", "sn_create", "sn_destroy", "sn_den
            "sn_load_gate_weights", "sn_star_offsets", "sn_check_device", "sn_status_string",
            "sn_last_error", "sn_set_profiling", "sn_stage_count", "sn_stage_name",
            "sn_stage_times", "sn_launch_count", "sn_normals_noalloc", "sn_noalloc_check_device", "sn_cross_normals",
-           "sn_pca_normals", "sn_set_walk_limit", "sn_run_frame_host")
+           "sn_pca_normals", "sn_set_walk_limit", "sn_run_frame_host", "sn_gate_q", "sn_gate_log2_table")
 
 
 # ---------------------------------------------------------------- helpers
@@ -328,6 +330,22 @@ def sn_normals_noalloc(cam, params, disp, normals, mask, stream=None):
     st = lib.sn_normals_noalloc(C.byref(c), C.byref(params) if params is not None else None, W, H,
                                 d, dp, n, np_, m, mp, _stream(stream))
     _check(None, st)
+
+
+def sn_gate_q(ctx, disp, q, stream=None):
+    """The learned gate's probability map q [H, W] (float32) of a learned
+    context with weights loaded."""
+    d, dp = _img(disp)
+    qq, qp = _img(q)
+    _check(ctx, lib.sn_gate_q(ctx, d, dp, qq, qp, _stream(stream)))
+
+
+def sn_gate_log2_table():
+    """The device table of FP32 log2 of every code (numpy float32 [131072])."""
+    import numpy as np
+    out = np.empty(131072, np.float32)
+    _check(None, lib.sn_gate_log2_table(out.ctypes.data_as(C.c_void_p), out.size))
+    return out
 
 
 def sn_noalloc_check_device(stream=None):

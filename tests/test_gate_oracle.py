@@ -105,7 +105,8 @@ def test_patch_labels_by_hand():
 @pytest.mark.parametrize("radius", [3, 6])
 def test_gate_image_is_min_of_patch_q(radius):
     # the image form's gate equals, pixel by pixel, the minimum of the patch
-    # form's q over the (2 radius - 3)^2 neighbourhood of the zero-padded image
+    # form's q over the lattice points (even coordinates) within radius - 1 of
+    # the pixel in the zero-padded image
     rng = np.random.default_rng(4)
     H, W = 11, 13
     D = rng.integers(4000, 4300, (H, W))
@@ -117,13 +118,84 @@ def test_gate_image_is_min_of_patch_q(radius):
     k = len(qs) // 2
     tau = float(0.5 * (qs[k - 1] + qs[k]))     # splits the image, far from every qmin
     g, q, qmin = gate.gate_image(D, theta, tau, radius, round_bf16=False)
-    m, P = radius - 2, radius + 2
+    m, P = radius - 1, radius + 2
     Dp = np.pad(D, P)
     for v in range(H):
         for u in range(W):
             patches = np.stack([Dp[v + oy + P - 2:v + oy + P + 4, u + ox + P - 2:u + ox + P + 4]
-                                for oy in range(-m, m + 1) for ox in range(-m, m + 1)])
+                                for oy in range(-m, m + 1) for ox in range(-m, m + 1)
+                                if (v + oy) % 2 == 0 and (u + ox) % 2 == 0])
             qm = gate.forward_patches(patches, theta).min()
             assert abs(qm - qmin[v, u]) < 1e-12
             assert g[v, u] == ((qm >= tau) and D[v, u] > 0)
     assert 0 < g.sum() < (D > 0).sum()
+
+
+def test_lattice_patches_cover_the_window():
+    # the 5x5 patches centred at the lattice points (even coordinates) within
+    # r - 1 of a pixel cover its (2r + 1)^2 window for either parity
+    for r in (3, 6):
+        for px in (0, 1):
+            covered = set()
+            for c in range(px - (r - 1), px + r):
+                if c % 2 == 0:
+                    covered.update(range(c - 2, c + 3))
+            assert set(range(px - r, px + r + 1)) <= covered, (r, px)
+
+
+def _fp32_network(D, theta, rng, margin):
+    """The network as a kernel computes it: exact FP32 features, BF16 weights,
+    features and layer-1 activations, every sum accumulated in FP32 in a
+    random order (each addition rounded to nearest), sigmoid in FP32."""
+    w = gate.unflatten(theta)
+    w = {k: (gate.bf16(v) if k.startswith("W") else v) for k, v in w.items()}
+    H, W = D.shape
+    P = max(4, margin + 2)
+    Dp = np.zeros((H + 2 * P + 1, W + 2 * P + 1), D.dtype)
+    Dp[P:P + H, P:P + W] = D
+    f = gate.bf16(gate.features(Dp)[:-1, :-1]).astype(np.float32)
+
+    def conv(x, Wt, b):
+        Ho, Wo = x.shape[0] - 2, x.shape[1] - 2
+        terms = []
+        for oy in range(3):
+            for ox in range(3):
+                for c in range(x.shape[2]):
+                    terms.append(x[oy:oy + Ho, ox:ox + Wo, c, None] * Wt[None, None, :, oy * 3 + ox, c].astype(np.float32))
+        terms.append(np.broadcast_to(np.asarray(b, np.float32), (Ho, Wo, Wt.shape[0])))
+        order = rng.permutation(len(terms))
+        acc = np.zeros((Ho, Wo, Wt.shape[0]), np.float32)
+        for k in order:
+            acc = (acc + terms[k]).astype(np.float32)
+        return acc
+    h1 = gate.bf16(np.maximum(conv(f, w["W1"], w["b1"]), 0)).astype(np.float32)
+    z = np.maximum(conv(h1, w["W2"], w["b2"]), 0)
+    logit = np.float32(w["b3"][0])
+    for c in rng.permutation(16):
+        logit = (logit + z[..., c] * np.float32(w["W3"][c])).astype(np.float32)
+    q = (1.0 / (1.0 + np.exp(-logit.astype(np.float64)))).astype(np.float32)
+    m = P - 2 - margin
+    return q[m:m + H + 2 * margin, m:m + W + 2 * margin].astype(np.float64)
+
+
+def test_q_bounds_contain_fp32_evaluations():
+    # the bounds of q (oracle.gate.q_bounds) contain the FP64 network and
+    # FP32 evaluations in random accumulation orders, and they are tight:
+    # most widths are at the FP32 noise level, a few are wider where a
+    # layer-1 activation sits at a BF16 rounding boundary
+    from paper_2504_15121_gb300 import gate as G
+    theta = G.load_weights().astype(np.float64)
+    rng = np.random.default_rng(11)
+    H, W = 28, 36
+    base = rng.integers(6000, 9000, (H, W))
+    blocks = rng.integers(0, 2, (H // 7 + 1, W // 7 + 1)).repeat(7, 0).repeat(7, 1)[:H, :W]
+    D = (base * (1 + 0.4 * blocks) + rng.integers(-40, 40, (H, W))).astype(np.int32)
+    D[rng.random((H, W)) < 0.06] = 0
+    lo, hi = gate.q_bounds(D, theta, margin=2)
+    q64 = gate.forward_image(D, theta, margin=2)
+    assert ((lo <= q64) & (q64 <= hi)).all()
+    for _ in range(3):
+        q32 = _fp32_network(D, theta, rng, margin=2)
+        assert ((lo <= q32) & (q32 <= hi)).all(), np.abs(np.clip(q32, lo, hi) - q32).max()
+    width = hi - lo
+    assert np.median(width) < 1e-4 and (width < 1e-3).mean() > 0.9, (np.median(width), (width < 1e-3).mean())
