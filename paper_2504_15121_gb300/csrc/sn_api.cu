@@ -50,6 +50,7 @@ struct sn_ctx {
     float* gate_theta;   // their FP32 source on the device
     void* net_img;       // the weights as the learned kernel's shared memory holds them
     const float* log2tab;  // the library's table of log2 of every code (learned contexts)
+    sn::GateView gv;       // what the learned kernels read (set by sn_load_gate_weights)
     int* star_pm;        // prefix moments of the star's rays (device)
     bool gate_loaded;
     bool prof;
@@ -542,8 +543,7 @@ sn_status sn_run_frame(sn_ctx* c, const sn_frame_in* in, sn_frame_out* out, sn_s
     sn::GateView gv{};
     if (c->p.learned) {
         if (!c->gate_loaded) return fail(c, SN_EINVAL, "learned context: gate weights not loaded");
-        gv = sn::GateView{c->gate.W1g, c->gate.W2g, c->gate.b1, c->gate.b2, c->gate.W3, c->gate.b3, c->p.tau,
-                          c->net_img, c->log2tab};
+        gv = c->gv;
     }
     const sn::GateView* g = c->p.learned ? &gv : nullptr;
     cudaError_t e;
@@ -575,8 +575,7 @@ sn_status sn_gate_q(sn_ctx* c, const void* disp, size_t dpitch, float* q, size_t
     sn_status st;
     if ((st = check_buf(c, disp, dpitch, in_elem(c->p.in_dtype), "disp")) != SN_OK) return st;
     if ((st = check_buf(c, q, qp, 4, "q")) != SN_OK) return st;
-    const sn::GateView gv{c->gate.W1g, c->gate.W2g, c->gate.b1, c->gate.b2, c->gate.W3, c->gate.b3, c->p.tau,
-                          c->net_img, c->log2tab};
+    const sn::GateView gv = c->gv;
     const sn::FrameOut none{};
     cudaError_t e = sn::launch_learned(c->geo, disp, dpitch, none, gv, q, qp, stream);
     if (e == cudaSuccess) c->launches++;
@@ -681,9 +680,21 @@ sn_status sn_load_gate_weights(sn_ctx* c, const void* blob, size_t bytes) {
     cudaError_t e = cudaMemcpy(c->gate_theta, b + 12, sizeof(float) * sn::kGateParams, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = sn::gate_layout(c->gate_theta, c->gate, nullptr);
     if (e == cudaSuccess) {
-        const sn::GateView gv{c->gate.W1g, c->gate.W2g, c->gate.b1, c->gate.b2, c->gate.W3, c->gate.b3, c->p.tau,
-                              nullptr, c->log2tab};
+        sn::GateView gv{};
+        gv.W1g = c->gate.W1g;
+        gv.W2g = c->gate.W2g;
+        gv.b1 = c->gate.b1;
+        gv.b2 = c->gate.b2;
+        gv.W3 = c->gate.W3;
+        gv.b3 = c->gate.b3;
+        gv.tau = c->p.tau;
+        gv.net = c->net_img;
+        gv.log2tab = c->log2tab;
+        float theta[sn::kGateParams];
+        memcpy(theta, b + 12, sizeof(theta));
+        sn::gate_constants(theta, &gv);
         e = sn::launch_net_image(gv, c->net_img, nullptr);
+        if (e == cudaSuccess) c->gv = gv;
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(c, e, "sn_load_gate_weights");

@@ -210,6 +210,27 @@ __global__ void k_gate_layout(const float* __restrict__ theta, GateDev w) {
     if (i == 0) w.b3[0] = theta[kOffB3];
 }
 
+// BF16 rounding (to nearest, ties to even) of a finite float, as a float
+static float bf16_round(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+void gate_constants(const float* theta, GateView* gv) {
+    float c3 = theta[kOffB3];
+    for (int c = 0; c < 16; c++) {
+        gv->k.b1[c] = theta[kOffB1 + c];
+        gv->k.nb2[c] = -theta[kOffB2 + c];
+        gv->k.w3[c] = bf16_round(theta[kOffW3 + c]);
+        c3 = fmaf(gv->k.w3[c], theta[kOffB2 + c], c3);
+    }
+    gv->k.c3 = c3;
+}
+
 cudaError_t gate_layout(const float* theta, const GateDev& w, cudaStream_t s) {
     k_gate_layout<<<(16 * 144 + 255) / 256, 256, 0, s>>>(theta, w);
     return cudaGetLastError();

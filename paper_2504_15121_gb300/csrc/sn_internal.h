@@ -143,15 +143,22 @@ struct GateView {
     const float* W3;
     const float* b3;
     float tau;
-    // The same weights as the gate kernel's shared memory holds them
-    // (kNetImageBytes, written by launch_net_image): b1, -b2, W3 and
-    // b3 + W3 . b2 (FP32, padded to 208 bytes), then the B operands of the
-    // two convolutions in tcgen05 core-matrix layout (3 and 9 K-steps of 512
-    // bytes).
+    // The B operands of the two convolutions as the gate kernel's shared
+    // memory holds them (kNetImageBytes, written by launch_net_image), in
+    // tcgen05 core-matrix layout: 3 and 9 K-steps of 512 bytes.
     const void* net;
     const float* log2tab;  // log2_table()
+    // The epilogue constants (kernel parameters, read from the constant
+    // bank): b1, -b2, W3 rounded to BF16 as every weight of the network, and
+    // c3 = b3 + sum W3 b2 (FP32 multiply-adds in channel order), so that
+    // W3 . relu(acc + b2) + b3 = W3 . max(acc, -b2) + c3.
+    struct {
+        float b1[16], nb2[16], w3[16], c3;
+    } k;
 };
-constexpr int kNetImageBytes = 208 + 3 * 512 + 9 * 512;
+constexpr int kNetImageBytes = 3 * 512 + 9 * 512;
+// Fills gv->k from the FP32 parameter vector (host).
+void gate_constants(const float* theta, GateView* gv);
 // Builds the image `net` from the other GateView fields.
 cudaError_t launch_net_image(const GateView& gv, void* img, cudaStream_t s);
 // Device address of the table of log2 of every disparity code (FP32,

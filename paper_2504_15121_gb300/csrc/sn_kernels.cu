@@ -146,21 +146,25 @@ __global__ void __launch_bounds__(kCclTile * 8)
     const int lane = threadIdx.x, tid = threadIdx.y * kCclTile + lane;
     if (count && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) *count = 0;
     const bool tma = use_tma && (umma::smem_addr(raw) & 127u) == 0;
+    // one thread issues the copy and waits for it (sleeping between polls);
+    // the block barrier publishes the copy and the outcome (as in stage_tile)
+    bool ok = true;
     if (tma) {
         if (tid == 0) {
             umma::mbar_init(&sbar, 1);
             umma::mbar_expect_tx(&sbar, sizeof(raw));
             umma::tma_load_2d(raw, &dmap, x0, y0, &sbar);
+            ok = umma::mbar_wait_sleep(&sbar, 0, 1 << 16, 20000);
+            if (!ok) {
+                // gave up: report, use no box entry, and wait once more
+                // (bounded) for the copy in flight before the CTA can exit
+                atomicOr(g.err, kErrMmaWait);
+                umma::mbar_wait_sleep(&sbar, 0, 1 << 16, 20000);
+            }
         }
-        __syncthreads();  // no thread polls the barrier before it is initialised
+        ok = __syncthreads_and(ok);
     }
-    const bool ok = tma && umma::mbar_wait(&sbar, 0, 1 << 22);
-    if (tma && !ok) {
-        // gave up: report, use no box entry, and wait once more (bounded) for
-        // the copy in flight before the CTA can exit (as in stage_tile)
-        atomicOr(g.err, kErrMmaWait);
-        umma::mbar_wait(&sbar, 0, 1 << 24);
-    }
+    ok = tma && ok;
 #pragma unroll
     for (int k = 0; k < kRows; k++) {
         const int r = threadIdx.y + 8 * k, i = r * kCclTile + lane;

@@ -73,11 +73,10 @@ constexpr int kFeatN = kFW * kFH;
 constexpr int kFeatPos = (kMT1 * 128 + 2 * kP1 + 2 + 7) & ~7;
 constexpr int kPlanePos = (kMT2 * 128 + kPJ + 1 + 7) & ~7;
 static_assert(kLatO >= 2 && kLatO % 2 == 0 && kLatO <= kLatM, "lattice origin");
-static_assert(16 * kMT1 <= 256 && kMT2 <= kMT1, "a TMEM buffer holds layer 1's accumulators, then layer 2's");
 static_assert(kMT2 <= kThreads / 128, "one layer-2 tile per warp group in the head");
 static_assert(((kH1H + 1) / 2 - 1) * kPJ + (kH1W + 1) / 2 - 1 < kPlanePos, "the layer-1 map fits its planes");
 constexpr uint32_t kNetIdesc = umma::idesc_bf16<128, 16>();
-constexpr int kSpin = 1 << 22;  // polls of a completion wait before giving up
+constexpr int kSleepPolls = 1 << 16;  // polls (each may sleep ~20 us) of a completion wait before giving up
 
 // The TMA box of one tile: columns x0 - kGX .. x0 - kGX + kGBW - 1 (x0 - kGX
 // a multiple of 8 elements, a 16-byte boundary for 4- and 2-byte input),
@@ -85,21 +84,26 @@ constexpr int kSpin = 1 << 22;  // polls of a completion wait before giving up
 // lx + kGX - kLatO - 2.
 constexpr int kGX = 8, kGBW = 48, kGBH = kLH;
 static_assert(kGX >= kLatO + 2 && kGX - kLatO - 2 + kLW <= kGBW && kGBW % 8 == 0, "box covers the codes");
-constexpr int kLPerThread = (kLN + kThreads - 1) / kThreads;
+constexpr int kLPerThread = (kLH + kThreads / kLW - 1) / (kThreads / kLW);  // code rows per thread
 constexpr size_t kGRawBytes = (size_t)kGBW * kGBH * 4;  // FP32 input; 16-bit input uses half
-constexpr size_t kGLStride = align128z(sizeof(float) * kLN);
-constexpr size_t kGFeatStride = align128z(16 * (size_t)kFeatPos);
-constexpr size_t kGH1Stride = align128z(8 * 16 * (size_t)kPlanePos);  // 4 parity planes x 2 channel halves
+// One buffer of each map suffices: the features of tile i + 1 are written
+// after layer 1 of tile i has completed, its layer-1 map after layer 2 of tile
+// i has completed, its codes' log2 after the features of tile i are made.
+// TMEM: layer 1's accumulators in columns [0, 16 kMT1), layer 2's in
+// [kT2Col, kT2Col + 16 kMT2), so that layer 1 of tile i + 1 runs while the
+// head of tile i reads layer 2's.
+constexpr uint32_t kT2Col = 16 * kMT1;
+static_assert(kT2Col + 16 * kMT2 <= 256, "both layers' accumulators in 256 TMEM columns");
 constexpr size_t kGOffRaw = 0;
-constexpr size_t kGOffL = kGOffRaw + align128z(kGRawBytes);  // 2 log2 regions
-constexpr size_t kGOffFeat = kGOffL + 2 * kGLStride;          // 2 feature maps
-constexpr size_t kGOffH1 = kGOffFeat + 2 * kGFeatStride;      // 2 layer-1 maps
-constexpr size_t kGOffQ = kGOffH1 + 2 * kGH1Stride;
+constexpr size_t kGOffL = kGOffRaw + align128z(kGRawBytes);
+constexpr size_t kGOffFeat = kGOffL + align128z(sizeof(float) * kLN);
+constexpr size_t kGOffH1 = kGOffFeat + align128z(16 * (size_t)kFeatPos);  // 4 parity planes x 2 channel halves
+constexpr size_t kGOffQ = kGOffH1 + align128z(8 * 16 * (size_t)kPlanePos);
 constexpr size_t kGOffQRow = kGOffQ + align128z(sizeof(float) * kLatW * kLatH);
 constexpr size_t kGOffPar = kGOffQRow + align128z(sizeof(float) * kLatH * kTW);
-constexpr size_t kGOffBar = align16z(kGOffPar + kNetImageBytes);  // wbar, tbar, l1[2], l2[2], TMEM slot
+constexpr size_t kGOffBar = align16z(kGOffPar + kNetImageBytes);  // wbar, tbar, l1, l2, TMEM slot
 constexpr size_t kGSmem = align128z(kGOffBar + 8 * 8);
-static_assert(kGSmem + 1024 <= 228 * 1024, "one gate CTA per SM");
+static_assert(2 * (kGSmem + 1024) <= 228 * 1024, "two gate CTAs per SM");
 static_assert(kNetImageBytes % 16 == 0 && kGOffPar % 16 == 0, "bulk copy of the weights image");
 
 // ---------------------------------------------------------------- chain kernel layout
@@ -131,30 +135,6 @@ __global__ void k_log2tab() {
 }
 
 // ---------------------------------------------------------------- small helpers
-__device__ __forceinline__ float min3f(float a, float b, float c) {
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-
-// (a0 + b0, a1 + b1) as one packed FP32 instruction
-__device__ __forceinline__ void add2(float& a0, float& a1, float b0, float b1) {
-    unsigned long long p, q;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(p) : "f"(a0), "f"(a1));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(q) : "f"(b0), "f"(b1));
-    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(p) : "l"(q));
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a0), "=f"(a1) : "l"(p));
-}
-
-// (s0 + a0 b0, s1 + a1 b1) as one packed FP32 instruction
-__device__ __forceinline__ void fma2(float& s0, float& s1, float a0, float a1, float b0, float b1) {
-    unsigned long long p, q, r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(p) : "f"(a0), "f"(a1));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(q) : "f"(b0), "f"(b1));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(s0), "f"(s1));
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(r) : "l"(p), "l"(q));
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(s0), "=f"(s1) : "l"(r));
-}
 
 // BF16 pair (lo = relu(a), hi = relu(b)), rounded to nearest even
 __device__ __forceinline__ unsigned relu_bf16x2(float a, float b) {
@@ -184,33 +164,16 @@ __device__ __forceinline__ int box_code(const unsigned char* raw, int i) {
 }
 
 // ---------------------------------------------------------------- the weights image
-// b1, -b2, W3 (rounded to BF16, as every weight of the network) and
-// c3 = b3 + sum W3 b2 (FP32, padded to 208 bytes), then the B operands:
-// element (n, k) of K-step s at s 512 + (k / 8) 256 + (n / 8) 128 +
-// (n % 8) 16 + (k % 8) 2 bytes (16 x 16 BF16 in 8 x 16-byte core matrices).
-// Layer 1, K-step dy: k 0-7 weigh the feature row of position dx = 0 (its
-// channels 0-3) and its right neighbour dx = 1 (4-7), k 8-15 positions
-// dx = 2 and dx = 3 (zero); channel 3 of a position is zero.  Layer 2,
-// K-step tap: k = channel of the layer-1 map.
+// The B operands: element (n, k) of K-step s at s 512 + (k / 8) 256 +
+// (n / 8) 128 + (n % 8) 16 + (k % 8) 2 bytes (16 x 16 BF16 in 8 x 16-byte
+// core matrices).  Layer 1, K-step dy: k 0-7 weigh the feature row of
+// position dx = 0 (its channels 0-3) and its right neighbour dx = 1 (4-7),
+// k 8-15 positions dx = 2 and dx = 3 (zero); channel 3 of a position is
+// zero.  Layer 2, K-step tap: k = channel of the layer-1 map.
 __global__ void k_net_image(const GateView gv, unsigned char* __restrict__ img) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    float* par = reinterpret_cast<float*>(img);
-    unsigned char* W1s = img + 208;
-    unsigned char* W2s = img + 208 + 3 * 512;
-    if (i < 52) {
-        float v = 0.0f;
-        if (i < 16) {
-            v = gv.b1[i];
-        } else if (i < 32) {
-            v = -gv.b2[i - 16];
-        } else if (i < 48) {
-            v = __bfloat162float(__float2bfloat16_rn(gv.W3[i - 32]));  // every weight is BF16
-        } else if (i == 48) {
-            v = gv.b3[0];
-            for (int c = 0; c < 16; c++) v = fmaf(__bfloat162float(__float2bfloat16_rn(gv.W3[c])), gv.b2[c], v);
-        }
-        par[i] = v;
-    }
+    unsigned char* W1s = img;
+    unsigned char* W2s = img + 3 * 512;
     if (i < 16 * 48) {
         // W1g is [16][80] with k = tap * 8 + channel (tap = 3 dy + dx)
         const int nn = i / 48, k = i % 48;
@@ -231,19 +194,18 @@ __global__ void k_net_image(const GateView gv, unsigned char* __restrict__ img) 
 // QMAP: write q at the pixels with both coordinates even (NaN at the others)
 // to qout; otherwise the gate bit into o.mask.
 template <int IN, bool QMAP>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     k_gate(const Geo g, const FrameOut o, const GateView gv, float* __restrict__ qout, size_t qp,
            const __grid_constant__ CUtensorMap dmap) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const float* par = reinterpret_cast<const float*>(smem + kGOffPar);
-    const unsigned char* W1s = smem + kGOffPar + 208;
+    const unsigned char* W1s = smem + kGOffPar;
     const unsigned char* W2s = W1s + 3 * 512;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kGOffBar);
     uint64_t* wbar = bars;       // the weights copy
     uint64_t* tbar = bars + 1;   // the TMA box (one per tile, in order)
-    uint64_t* l1bar = bars + 2;  // [2]: layer-1 MMAs of buffer b
-    uint64_t* l2bar = bars + 4;  // [2]: layer-2 MMAs of buffer b
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 6);
+    uint64_t* l1bar = bars + 2;  // layer-1 MMAs (one phase per tile)
+    uint64_t* l2bar = bars + 3;  // layer-2 MMAs (one phase per tile)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
     unsigned char* raw = smem + kGOffRaw;
     float* qs = reinterpret_cast<float*>(smem + kGOffQ);
     float* qrow = reinterpret_cast<float*>(smem + kGOffQRow);
@@ -253,12 +215,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int ntiles = tilesX * tilesY;
     const int n = ((int)blockIdx.x < ntiles) ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
     constexpr uint32_t kRawBytes = (uint32_t)kGBW * kGBH * (IN == SN_IN_F32 ? 4 : 2);
-    auto Lbuf = [&](int r) { return reinterpret_cast<float*>(smem + kGOffL + (size_t)r * kGLStride); };
-    auto feat = [&](int b) { return reinterpret_cast<uint4*>(smem + kGOffFeat + (size_t)b * kGFeatStride); };
-    // plane (py, px), channel half h of buffer b: kPlanePos positions
-    auto plane = [&](int b, int p, int h) {
-        return reinterpret_cast<uint4*>(smem + kGOffH1 + (size_t)b * kGH1Stride) + (size_t)(2 * p + h) * kPlanePos;
-    };
+    float* L = reinterpret_cast<float*>(smem + kGOffL);
+    uint4* feat = reinterpret_cast<uint4*>(smem + kGOffFeat);
+    // parity plane p = 2 (row parity) + column parity, channel half h: kPlanePos positions
+    auto plane = [&](int p, int h) { return reinterpret_cast<uint4*>(smem + kGOffH1) + (size_t)(2 * p + h) * kPlanePos; };
     auto tile_xy = [&](int i, int& x0, int& y0) {
         const int k = (int)blockIdx.x + i * (int)gridDim.x;
         x0 = (k % tilesX) * kTW;
@@ -270,17 +230,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         umma::mbar_expect_tx(tbar, kRawBytes);
         umma::tma_load_2d(raw, &dmap, x0 - kGX, y0 - kLatO - 2, tbar);
     };
-    // counts of what the issuing thread has put in flight (for the drain)
-    int nt = 0, n1[2] = {0, 0}, n2[2] = {0, 0};
+    // counts of what has been put in flight (for the drain; tid 0's view)
+    int nt = 0, n1 = 0, n2 = 0;
 
-    if (warp == 0) umma::tmem_alloc(tslot, 512);
+    if (warp == 0) umma::tmem_alloc(tslot, 256);
     if (tid == 0) {
         umma::mbar_init(wbar, 1);
         umma::mbar_init(tbar, 1);
-        for (int r = 0; r < 2; r++) {
-            umma::mbar_init(l1bar + r, 1);
-            umma::mbar_init(l2bar + r, 1);
-        }
+        umma::mbar_init(l1bar, kMT1);  // one commit per issuing warp
+        umma::mbar_init(l2bar, kMT2);
         umma::mbar_expect_tx(wbar, kNetImageBytes);
         umma::bulk_g2s(smem + kGOffPar, gv.net, kNetImageBytes, wbar);
         if (n > 0) {
@@ -289,56 +247,60 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     }
     // map positions that no output reads stay zero (they feed dropped GEMM rows)
-    for (int b = 0; b < 2; b++) {
-        for (int i = kFeatN + tid; i < kFeatPos; i += kThreads) feat(b)[i] = make_uint4(0u, 0u, 0u, 0u);
-        uint4* H = plane(b, 0, 0);
-        for (int i = tid; i < 8 * kPlanePos; i += kThreads) H[i] = make_uint4(0u, 0u, 0u, 0u);
-    }
+    for (int i = kFeatN + tid; i < kFeatPos; i += kThreads) feat[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = tid; i < 8 * kPlanePos; i += kThreads) plane(0, 0)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();  // barriers initialised, TMEM address written
     const uint32_t tmem = *tslot;
     const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;  // the TMEM lanes this warp may read
-    bool ok = umma::mbar_wait(wbar, 0, kSpin);
+    // One thread waits for an asynchronous step (sleeping between polls);
+    // the block barrier that follows publishes it and the outcome.
+    auto wait1 = [&](uint64_t* bar, int parity) {
+        return tid != 0 || umma::mbar_wait_sleep(bar, parity, kSleepPolls, 20000);
+    };
+    bool ok = wait1(wbar, 0);
 
     // codes and their log2 of tile i's box into L buffer i & 1 (this
     // thread's entries in registers first, so that the table reads overlap)
+    constexpr int kLRowsPerPass = kThreads / kLW;
+    static_assert(kLPerThread * kLRowsPerPass >= kLH, "the code region in kLPerThread passes");
+    const int lx = tid % kLW, ly0 = tid / kLW;
+    const bool lthread = tid < kLRowsPerPass * kLW;
     float Lreg[kLPerThread];
-    auto load_L = [&](int i) {
-        ok = umma::mbar_wait(tbar, i & 1, kSpin) && ok;
+    auto load_L = [&](int i) {  // after the block barrier that follows wait1(tbar, i & 1)
 #pragma unroll
         for (int k = 0; k < kLPerThread; k++) {
-            const int e = tid + k * kThreads;
-            if (e < kLN) {
-                const int D = ok ? box_code<IN>(raw, (e / kLW) * kGBW + e % kLW + kGX - kLatO - 2) : 0;
+            const int ly = ly0 + k * kLRowsPerPass;
+            if (lthread && ly < kLH) {
+                const int D = ok ? box_code<IN>(raw, ly * kGBW + lx + kGX - kLatO - 2) : 0;
                 Lreg[k] = __ldg(gv.log2tab + D);
             }
         }
     };
-    auto store_L = [&](int i) {
-        float* L = Lbuf(i & 1);
+    auto store_L = [&]() {
 #pragma unroll
         for (int k = 0; k < kLPerThread; k++) {
-            const int e = tid + k * kThreads;
-            if (e < kLN) L[e] = Lreg[k];
+            const int ly = ly0 + k * kLRowsPerPass;
+            if (lthread && ly < kLH) L[ly * kLW + lx] = Lreg[k];
         }
     };
-    // head of the tile in buffer i & 1 (lattice rows), then the output
+    // head of tile i (layer 2's accumulators, lattice rows), then the output
     auto head = [&](int i) {
-        const int b = i & 1;
-        ok = __all_sync(0xffffffffu, ok && umma::mbar_wait(l2bar + b, (i >> 1) & 1, kSpin));  // warp-uniform
+        ok = __syncthreads_and(ok && wait1(l2bar, i & 1));
         umma::fence_after();
         const int t = warp >> 2;
         if (ok && t < kMT2) {
             uint32_t r[16];
-            umma::ld16(tmem + 256 * b + tlane + 16 * t, r);
+            umma::ld16(tmem + kT2Col + tlane + 16 * t, r);
             umma::wait_ld();
-            // W3 . relu(acc + b2) = W3 . max(acc, -b2) + W3 . b2 (folded into par[48])
-            float s0 = 0.0f, s1 = 0.0f;
+            // W3 . relu(acc + b2) + b3 = W3 . max(acc, -b2) + c3 (constants from the kernel parameters)
+            float s0 = gv.k.c3, s1 = 0.0f;
 #pragma unroll
-            for (int c = 0; c < 8; c++)
-                fma2(s0, s1, par[32 + 2 * c], par[33 + 2 * c], fmaxf(__uint_as_float(r[2 * c]), par[16 + 2 * c]),
-                     fmaxf(__uint_as_float(r[2 * c + 1]), par[17 + 2 * c]));
+            for (int c = 0; c < 8; c++) {
+                s0 = fmaf(gv.k.w3[2 * c], fmaxf(__uint_as_float(r[2 * c]), gv.k.nb2[2 * c]), s0);
+                s1 = fmaf(gv.k.w3[2 * c + 1], fmaxf(__uint_as_float(r[2 * c + 1]), gv.k.nb2[2 * c + 1]), s1);
+            }
             const int j = 128 * t + (warp & 3) * 32 + lane, a = j / kPJ, bb = j - a * kPJ;
-            if (a < kLatH && bb < kLatW) qs[a * kLatW + bb] = __fdividef(1.0f, 1.0f + __expf(-((s0 + s1) + par[48])));
+            if (a < kLatH && bb < kLatW) qs[a * kLatW + bb] = __fdividef(1.0f, 1.0f + __expf(-(s0 + s1)));
         }
         umma::fence_before();
         __syncthreads();
@@ -372,9 +334,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     };
 
+    ok = __syncthreads_and(ok && (n == 0 || wait1(tbar, 0)));
     if (n > 0) {
         load_L(0);
-        store_L(0);
+        store_L();
     }
     ok = __syncthreads_and(ok);  // the box of tile 0 is read: it may be overwritten
     if (ok && n > 1 && tid == 0) {
@@ -383,26 +346,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     int i = 0;
     for (; ok && i < n; i++) {
-        const int b = i & 1;
         // ---- features of tile i: each map row holds a position's channels
         // (f0, f1, f2, 0) and its right neighbour's
         {
-            const float* L = Lbuf(b);
-            uint4* F = feat(b);
-            for (int p = tid; p < kFeatN; p += kThreads) {
-                const int fy = p / kFW, fx = p - fy * kFW;
-                const int e = fy * kLW + fx;
-                const float Lc = L[e], Lr = L[e + 1];
-                uint4 v;
-                v.x = bf16x2(nan_to_zero(Lr - Lc), nan_to_zero(L[e + kLW] - Lc));
-                v.y = Lc == Lc ? 0x3F80u : 0u;  // BF16 1.0 where the code is valid
-                v.z = 0u;
-                v.w = 0u;
-                if (fx + 1 < kFW) {
-                    v.z = bf16x2(nan_to_zero(L[e + 2] - Lr), nan_to_zero(L[e + kLW + 1] - Lr));
-                    v.w = Lr == Lr ? 0x3F80u : 0u;
+            uint4* F = feat;
+            constexpr int kRowsPerPass = kThreads / kFW;
+            const int fx = tid % kFW;
+            if (tid < kRowsPerPass * kFW) {
+                for (int fy = tid / kFW; fy < kFH; fy += kRowsPerPass) {
+                    const int e = fy * kLW + fx;
+                    const float Lc = L[e], Lr = L[e + 1];
+                    uint4 v;
+                    v.x = bf16x2(nan_to_zero(Lr - Lc), nan_to_zero(L[e + kLW] - Lc));
+                    v.y = Lc == Lc ? 0x3F80u : 0u;  // BF16 1.0 where the code is valid
+                    v.z = 0u;
+                    v.w = 0u;
+                    if (fx + 1 < kFW) {
+                        v.z = bf16x2(nan_to_zero(L[e + 2] - Lr), nan_to_zero(L[e + kLW + 1] - Lr));
+                        v.w = Lr == Lr ? 0x3F80u : 0u;
+                    }
+                    F[fy * kFW + fx] = v;
                 }
-                F[p] = v;
             }
         }
         umma::fence_proxy_async();
@@ -410,66 +374,64 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = __syncthreads_and(ok);
         if (!ok) break;
         umma::fence_after();
-        // ---- layer-1 MMAs of tile i (async), then the head of tile i - 1
-        if (tid == 0) {
+        // ---- layer-1 MMAs of tile i (async; lane 0 of warp t issues MMA
+        // tile t), then the head of tile i - 1
+        if (lane == 0 && warp < kMT1) {
             const uint64_t bd = umma::desc(umma::smem_addr(W1s), 256, 128);
-            for (int t = 0; t < kMT1; t++) {
-                const uint64_t a0 = umma::desc(umma::smem_addr(feat(b) + 128 * t), 32, 128);
+            const uint64_t a0 = umma::desc(umma::smem_addr(feat + 128 * warp), 32, 128);
 #pragma unroll
-                for (int dy = 0; dy < 3; dy++)
-                    umma::mma<kNetIdesc>(tmem + 256 * b + 16 * t, a0 + dy * kP1, bd + 32 * dy, dy > 0);
-            }
-            umma::commit(l1bar + b);
-            n1[b]++;
+            for (int dy = 0; dy < 3; dy++)
+                umma::mma<kNetIdesc>(tmem + 16 * warp, a0 + dy * kP1, bd + 32 * dy, dy > 0);
+            umma::commit(l1bar);
         }
+        if (tid == 0) n1++;
         if (i > 0) head(i - 1);
         // ---- codes and log2 of tile i + 1 (in registers), the layer-1
         // epilogue of tile i, then the log2 into their buffer
-        if (i + 1 < n) load_L(i + 1);
-        ok = __all_sync(0xffffffffu, ok && umma::mbar_wait(l1bar + b, (i >> 1) & 1, kSpin));  // warp-uniform
+        ok = __syncthreads_and(ok && (i + 1 >= n || wait1(tbar, (i + 1) & 1)) && wait1(l1bar, i & 1));
         umma::fence_after();
+        if (ok && i + 1 < n) load_L(i + 1);
         if (ok) {
             for (int t = warp >> 2; t < kMT1; t += kThreads / 128) {
                 uint32_t r[16];
-                umma::ld16(tmem + 256 * b + tlane + 16 * t, r);
+                umma::ld16(tmem + tlane + 16 * t, r);
                 umma::wait_ld();
                 const int j = 128 * t + (warp & 3) * 32 + lane, hy = j / kP1, hx = j - hy * kP1;
                 if (hy < kH1H && hx < kH1W) {
                     unsigned w[8];
 #pragma unroll
-                    for (int c = 0; c < 8; c++) {
-                        float a = __uint_as_float(r[2 * c]), e = __uint_as_float(r[2 * c + 1]);
-                        add2(a, e, par[2 * c], par[2 * c + 1]);
-                        w[c] = relu_bf16x2(a, e);
-                    }
+                    for (int c = 0; c < 8; c++)
+                        w[c] = relu_bf16x2(__uint_as_float(r[2 * c]) + gv.k.b1[2 * c],
+                                           __uint_as_float(r[2 * c + 1]) + gv.k.b1[2 * c + 1]);
                     const int p = 2 * (hy & 1) + (hx & 1), k = (hy >> 1) * kPJ + (hx >> 1);
-                    plane(b, p, 0)[k] = make_uint4(w[0], w[1], w[2], w[3]);
-                    plane(b, p, 1)[k] = make_uint4(w[4], w[5], w[6], w[7]);
+                    plane(p, 0)[k] = make_uint4(w[0], w[1], w[2], w[3]);
+                    plane(p, 1)[k] = make_uint4(w[4], w[5], w[6], w[7]);
                 }
             }
         }
-        if (i + 1 < n) store_L(i + 1);
+        if (i + 1 < n) store_L();
         umma::fence_proxy_async();
         umma::fence_before();
         ok = __syncthreads_and(ok);
         if (!ok) break;
         umma::fence_after();
-        // ---- layer-2 MMAs of tile i on its lattice points (async); the box
-        // of tile i + 2 (the one of tile i + 1 has been read)
-        if (tid == 0) {
+        // ---- layer-2 MMAs of tile i on its lattice points (async; lane 0 of
+        // warp t issues MMA tile t); the box of tile i + 2 (the one of tile
+        // i + 1 has been read)
+        if (lane == 0 && warp < kMT2) {
             const uint64_t bd = umma::desc(umma::smem_addr(W2s), 256, 128);
-            for (int t = 0; t < kMT2; t++) {
 #pragma unroll
-                for (int tap = 0; tap < 9; tap++) {
-                    const int dy = tap / 3, dx = tap % 3;
-                    const uint64_t a = umma::desc(umma::smem_addr(plane(b, 2 * (dy & 1) + (dx & 1), 0) + 128 * t),
-                                                  16 * kPlanePos, 128) +
-                                       (dy >> 1) * kPJ + (dx >> 1);
-                    umma::mma<kNetIdesc>(tmem + 256 * b + 16 * t, a, bd + 32 * tap, tap > 0);
-                }
+            for (int tap = 0; tap < 9; tap++) {
+                const int dy = tap / 3, dx = tap % 3;
+                const uint64_t a = umma::desc(umma::smem_addr(plane(2 * (dy & 1) + (dx & 1), 0) + 128 * warp),
+                                              16 * kPlanePos, 128) +
+                                   (dy >> 1) * kPJ + (dx >> 1);
+                umma::mma<kNetIdesc>(tmem + kT2Col + 16 * warp, a, bd + 32 * tap, tap > 0);
             }
-            umma::commit(l2bar + b);
-            n2[b]++;
+            umma::commit(l2bar);
+        }
+        if (tid == 0) {
+            n2++;
             if (i + 2 < n) {
                 issue_tma(i + 2);
                 nt++;
@@ -483,19 +445,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         // flight drain (bounded) before the TMEM is freed and the CTA exits.
         if (tid == 0) {
             atomicOr(g.err, kErrMmaWait);
-            if (nt) umma::mbar_wait(tbar, (nt - 1) & 1, kSpin);
-            for (int r = 0; r < 2; r++) {
-                if (n1[r]) umma::mbar_wait(l1bar + r, (n1[r] - 1) & 1, kSpin);
-                if (n2[r]) umma::mbar_wait(l2bar + r, (n2[r] - 1) & 1, kSpin);
-            }
-            umma::mbar_wait(wbar, 0, kSpin);
+            if (nt) umma::mbar_wait_sleep(tbar, (nt - 1) & 1, kSleepPolls, 20000);
+            if (n1) umma::mbar_wait_sleep(l1bar, (n1 - 1) & 1, kSleepPolls, 20000);
+            if (n2) umma::mbar_wait_sleep(l2bar, (n2 - 1) & 1, kSleepPolls, 20000);
+            umma::mbar_wait_sleep(wbar, 0, kSleepPolls, 20000);
         }
     }
     umma::fence_before();
     __syncthreads();
     if (warp == 0) {
         umma::fence_after();
-        umma::tmem_dealloc(tmem, 512);
+        umma::tmem_dealloc(tmem, 256);
     }
 }
 
@@ -660,7 +620,7 @@ cudaError_t launch_gate(const Geo& g, const void* disp, size_t dp, const FrameOu
     const cudaError_t e = smem_once(k_gate<IN, QMAP>, kGSmem, done);
     if (e != cudaSuccess) return e;
     const int ntiles = ((g.W + kTW - 1) / kTW) * ((g.H + kTH - 1) / kTH);
-    const int grid = ntiles < sm_count() ? ntiles : sm_count();
+    const int grid = ntiles < 2 * sm_count() ? ntiles : 2 * sm_count();  // two resident CTAs per SM
     k_gate<IN, QMAP><<<grid, dim3(kTW, kTH), kGSmem, s>>>(g, o, gv, q, qp, dmap);
     return cudaGetLastError();
 }

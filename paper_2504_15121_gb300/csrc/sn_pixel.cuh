@@ -526,25 +526,29 @@ __device__ __forceinline__ void stage_tile(int2* tile, unsigned char* raw, const
     uint64_t* sbar = reinterpret_cast<uint64_t*>(raw + kRawBytes);
     const int tid = threadIdx.y * kTW + threadIdx.x;  // blocks are kTW wide, NT threads
     const bool tma = use_tma && (umma::smem_addr(raw) & 127u) == 0;
+    // One thread issues the copy and waits for it (sleeping between polls,
+    // so that the copy's latency costs the SM no issue slots); the block
+    // barrier then publishes the copy and the outcome to every thread.
+    bool ok = true;
     if (tma) {
         if (tid == 0) {
             umma::mbar_init(sbar, 1);
             umma::mbar_expect_tx(sbar, kRawBytes);
             umma::tma_load_2d(raw, dmap, x0 - tma_xpad<IN, R>(), y0 - R, sbar);
+            ok = umma::mbar_wait_sleep(sbar, 0, 1 << 16, 20000);
+            if (!ok) {
+                // Gave up: report it, and wait once more (bounded) for the
+                // copy still in flight, so that this CTA's shared memory is
+                // not handed to another CTA while the copy may still write
+                // it.  No box entry is converted (the tile's codes become
+                // invalid); the frame's outputs are undefined after this.
+                atomicOr(g.err, kErrMmaWait);
+                umma::mbar_wait_sleep(sbar, 0, 1 << 16, 20000);
+            }
         }
-        __syncthreads();  // no thread polls the barrier before it is initialised
+        ok = __syncthreads_and(ok);
     }
-    const bool ok = tma && umma::mbar_wait(sbar, 0, 1 << 22);
-    if (tma && !ok) {
-        // Gave up: every thread that did reports it (the polls of different
-        // threads may end on either side of a late completion), converts no
-        // box entry (its tile entries become invalid codes) and waits once
-        // more, again bounded, for the copy still in flight, so that this
-        // CTA's shared memory is not handed to another CTA while the copy may
-        // still write it.  The frame's outputs are undefined after this.
-        atomicOr(g.err, kErrMmaWait);
-        umma::mbar_wait(sbar, 0, 1 << 24);
-    }
+    ok = tma && ok;
     for (int i = tid; i < N; i += NT) {
         const int ly = i / TW, lx = i - ly * TW;
         const int b = ly * BW + lx + tma_xpad<IN, R>() - R;

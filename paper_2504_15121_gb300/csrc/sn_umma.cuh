@@ -100,6 +100,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int l
     return false;
 }
 
+// The same wait with a suspend hint: between polls the thread may sleep in
+// hardware until the phase completes or about `hint_ns` nanoseconds pass, so
+// a long wait costs almost no issue slots.  At most `limit` polls.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* mbar, uint32_t parity, int limit, uint32_t hint_ns) {
+    const uint32_t a = smem_addr(mbar);
+    for (int it = 0; it < limit; it++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity), "r"(hint_ns)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // Warp-wide: allocates `ncols` TMEM columns (a power of two >= 32) and writes
 // their address to *slot; then gives up the CTA's right to allocate more.
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
