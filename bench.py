@@ -355,6 +355,8 @@ def run_ours(args):
         comparators = {"cross": time_comparator(scenes, args, "cross", 0, world),
                        "pca_9x9": time_comparator(scenes, args, "pca", 4, world)}
     stage_calls = time_stage_calls(scenes, args) if world == 1 else None
+    # every method's ground-truth error on the box-and-curve scene (1482x994)
+    errors_mixed = scene_errors("mixed_1482x994") if world == 1 else None
     # mixed-resolution batch of 64 frames, one graph launch per step
     mixed = run_mixed_batch(args) if world == 1 and not args.no_mixed else None
 
@@ -415,6 +417,7 @@ def run_ours(args):
             "forms": forms,
             "comparators": comparators,
             "stage_calls": stage_calls,
+            "gt_error_by_method_mixed_1482x994": errors_mixed,
             "mixed_batch": mixed,
             "clocks": clk,
             "e2e": e2e,
@@ -577,6 +580,58 @@ def time_comparator(scenes, args, which, r, world):
         sn.sn_destroy(ctx)
     return {"value": world * steps * F * s0.W * s0.H / (ms / 1e3) / 1e6, "unit": "MPix/s",
             "what": "normals + mask only", "gt_error_deg": gt}
+
+
+def scene_errors(scene_name, n_frames=4):
+    """Mean angular error against the generator's ground truth of every
+    method on frames of one scene (Table scene-errors of the paper compares
+    the adaptive, fixed-window, PCA and Cross estimators on box scenes):
+    star-fill CD s10 d8 and s30 d16, ST s10 d8, the fixed 9x9 window, the
+    learned form, PCA 9x9 and Cross; each frame run once on the GPU."""
+    import torch
+    from scenes import make_scene
+    from paper_2504_15121_gb300 import Pipeline, sn
+    scenes = [make_scene(scene_name, frame=200 + i) for i in range(n_frames)]
+    s0 = scenes[0]
+    out = {"scene": scene_name, "frames": n_frames}
+    chains = {"cd_s10_d8": {}, "cd_s30_d16": dict(dirs=16, steps=30), "st_s10_d8": dict(support=2, st_t=0.1),
+              "fixed_9x9": dict(support=0, r_affine=4), "learned": dict(learned=1)}
+    for name, params in chains.items():
+        pipe = Pipeline(s0.camera, s0.W, s0.H, **params)
+        try:
+            bufs = []
+            for s in scenes:
+                b = pipe.buffers()
+                pipe.run_frame(pipe.upload(s.disp), b)
+                bufs.append(b)
+            torch.cuda.synchronize()
+            sn.sn_check_device(pipe.ctx)
+            out[name] = gt_error_deg(bufs, scenes)
+        finally:
+            pipe.close()
+    ctx = sn.sn_create(s0.camera, s0.W, s0.H, sn.default_params())
+    try:
+        for name in ("pca_9x9", "cross"):
+            bufs = []
+            for s in scenes:
+                d = sn.empty_image(s0.H, s0.W, torch.float32)
+                d.copy_(torch.from_numpy(s.disp))
+
+                class _O:
+                    pass
+                o = _O()
+                o.normals, o.mask = sn.empty_planes(3, s0.H, s0.W), sn.empty_image(s0.H, s0.W, torch.uint8)
+                if name == "cross":
+                    sn.sn_cross_normals(ctx, d, o.normals, o.mask)
+                else:
+                    sn.sn_pca_normals(ctx, d, 4, o.normals, o.mask)
+                bufs.append(o)
+            torch.cuda.synchronize()
+            out[name] = gt_error_deg(bufs, scenes)
+        sn.sn_check_device(ctx)
+    finally:
+        sn.sn_destroy(ctx)
+    return out
 
 
 MIXED_SIZES = ("planes_320x240", "planes_640x480", "mixed_1482x994", "driving_2048x1024")
@@ -744,7 +799,8 @@ def run_serving(args):
     4x 1482x994 at 30 Hz, 2x 2048x1024 at 30 Hz), Poisson arrivals, one
     CUDA graph per request slot, 4 streams; latency from arrival to result
     ready on the device.  Offered rate x1 for --serve-seconds, then a rate
-    sweep; plain FP32 chain and FP16 in / snorm16 out chain."""
+    sweep; plain FP32 chain, FP16 in / snorm16 out chain, and the learned
+    chain with FP16 in / snorm16 out."""
     import numpy as np
     import torch
     from paper_2504_15121_gb300 import serve, sn
@@ -757,6 +813,9 @@ def run_serving(args):
     for form, params, pick in (
             ("plain_f32", {}, lambda s: s.disp),
             ("f16_snorm16", dict(in_dtype=sn.SN_IN_F16, normal_fmt=sn.SN_NORMALS_SNORM16X4),
+             lambda s: s.disp.astype(np.float16)),
+            # the learned + FP16 chain of the serving workload
+            ("learned_f16_snorm16", dict(learned=1, in_dtype=sn.SN_IN_F16, normal_fmt=sn.SN_NORMALS_SNORM16X4),
              lambda s: s.disp.astype(np.float16))):
         cams, pools = [], []
         for name, rate in SERVING_CAMERAS:

@@ -43,8 +43,13 @@ typedef struct sn_server sn_server;
 typedef struct {
     int W, H;
     sn_camera cam;
-    sn_params params;  /* in_dtype and normal_fmt select the form per camera */
+    sn_params params;  /* in_dtype, normal_fmt and learned select the form per camera */
     double rate_hz;    /* mean frame rate for sn_server_simulate */
+    /* params.learned = 1: the gate weights (the blob sn_load_gate_weights
+     * takes, HOST memory, read during sn_server_create only); ignored
+     * otherwise.  A learned camera without weights fails with SN_EINVAL. */
+    const void *gate_weights;
+    size_t gate_weights_bytes;
 } sn_server_camera;
 
 typedef struct {

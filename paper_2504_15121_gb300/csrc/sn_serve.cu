@@ -302,6 +302,12 @@ sn_status sn_server_create(const sn_server_config* cfg, sn_server** out) {
         c.in_elem = c.cfg.params.in_dtype == SN_IN_F32 ? 4 : 2;
         c.nrm_bytes_px = c.cfg.params.normal_fmt == SN_NORMALS_F32X3 ? 12 : 8;
         st = sn_create(&c.cfg.cam, c.cfg.W, c.cfg.H, &c.cfg.params, &c.ctx);
+        if (st == SN_OK && c.cfg.params.learned) {
+            // the weights go in before the slots' graphs capture the chain
+            st = c.cfg.gate_weights ? sn_load_gate_weights(c.ctx, c.cfg.gate_weights, c.cfg.gate_weights_bytes)
+                                    : SN_EINVAL;
+            c.cfg.gate_weights = nullptr;  // the caller's buffer is not kept
+        }
     }
     if (st != SN_OK) {
         sn_server_destroy(s);

@@ -12,7 +12,7 @@ from .sn import SnError, lib, sn_camera, sn_params, default_params, SN_OK
 
 class sn_server_camera(C.Structure):
     _fields_ = [("W", C.c_int), ("H", C.c_int), ("cam", sn_camera), ("params", sn_params),
-                ("rate_hz", C.c_double)]
+                ("rate_hz", C.c_double), ("gate_weights", C.c_void_p), ("gate_weights_bytes", C.c_size_t)]
 
 
 class sn_server_config(C.Structure):
@@ -63,9 +63,22 @@ def _check(st, what):
         raise SnError(st, what)
 
 
-def camera(W, H, cam, rate_hz=0.0, **params) -> sn_server_camera:
-    return sn_server_camera(W, H, sn_camera(cam.fx, cam.fy, cam.cx, cam.cy, cam.baseline),
-                            default_params(**params), rate_hz)
+_weight_buffers = []   # gate-weight blobs handed to servers (kept alive for the process)
+
+
+def camera(W, H, cam, rate_hz=0.0, gate_weights=None, **params) -> sn_server_camera:
+    """One camera of a server.  learned=1 attaches the gate weights
+    (gate_weights: path or bytes; default: the packaged trained weights)."""
+    p = default_params(**params)
+    ptr, size = None, 0
+    if p.learned:
+        from . import gate
+        blob = gate_weights if isinstance(gate_weights, (bytes, bytearray)) else \
+            open(gate_weights or gate.DEFAULT_WEIGHTS, "rb").read()
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        _weight_buffers.append(buf)
+        ptr, size = C.cast(buf, C.c_void_p), len(blob)
+    return sn_server_camera(W, H, sn_camera(cam.fx, cam.fy, cam.cx, cam.cy, cam.baseline), p, rate_hz, ptr, size)
 
 
 class Server:

@@ -1,6 +1,7 @@
 """Serving runtime (include/sn_serve.h) on the GPU.
 
-* every result computed in a mix of cameras and resolutions, with several
+* every result computed in a mix of cameras and resolutions (plain FP32,
+  uint16 in / snorm16 out, and the learned FP16 chain), with several
   requests in flight on several streams, is bit-identical to the same frame
   run alone through sn_run_frame;
 * admission: a camera whose slots are all held queues its requests and
@@ -60,7 +61,8 @@ def wait_results(srv, n, timeout=60.0):
 def test_results_alone_equal_mixed(P):
     from paper_2504_15121_gb300 import serve
     specs = [("planes_640x480", {}), ("mixed_1482x994", {}),
-             ("driving_2048x1024", dict(in_dtype=P.sn.SN_IN_U16X256, normal_fmt=P.sn.SN_NORMALS_SNORM16X4))]
+             ("driving_2048x1024", dict(in_dtype=P.sn.SN_IN_U16X256, normal_fmt=P.sn.SN_NORMALS_SNORM16X4)),
+             ("mixed_1482x994", dict(learned=1, in_dtype=P.sn.SN_IN_F16, normal_fmt=P.sn.SN_NORMALS_SNORM16X4))]
     frames = {}
     cams = []
     for ci, (name, params) in enumerate(specs):
@@ -75,7 +77,8 @@ def test_results_alone_equal_mixed(P):
         for k in range(2):
             for ci, (name, params) in enumerate(specs):
                 s = frames[ci][k]
-                arr = s.disp_u16 if params.get("in_dtype") == P.sn.SN_IN_U16X256 else s.disp
+                arr = s.disp_u16 if params.get("in_dtype") == P.sn.SN_IN_U16X256 else \
+                    s.disp.astype(np.float16) if params.get("in_dtype") == P.sn.SN_IN_F16 else s.disp
                 host[tag] = (ci, s, arr, params)
                 assert srv.submit(ci, pinned(arr), tag) == P.sn.SN_OK
                 tag += 1
@@ -137,6 +140,17 @@ def serving_cameras(P, serve, **params):
             else (lambda s: s.disp.astype(np.float16)) if f16 else (lambda s: s.disp)
         pools.append([pinned(pick(s)) for s in ss])
     return cams, pools
+
+
+def test_learned_camera_needs_weights(P):
+    from paper_2504_15121_gb300 import serve
+    s = make_scene("planes_320x240", frame=0)
+    cam = serve.camera(s.W, s.H, s.camera, learned=1)
+    cam.gate_weights = None
+    cam.gate_weights_bytes = 0
+    with pytest.raises(P.sn.SnError) as ei:
+        serve.Server([cam], memory_budget=1 << 30, max_slots_per_camera=1, n_streams=1)
+    assert ei.value.status == P.sn.SN_EINVAL
 
 
 def test_simulated_camera_set(P):
