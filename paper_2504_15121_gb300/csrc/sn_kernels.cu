@@ -154,12 +154,12 @@ __global__ void __launch_bounds__(kCclTile * 8)
             umma::mbar_init(&sbar, 1);
             umma::mbar_expect_tx(&sbar, sizeof(raw));
             umma::tma_load_2d(raw, &dmap, x0, y0, &sbar);
-            ok = umma::mbar_wait_sleep(&sbar, 0, 1 << 16, 20000);
+            ok = umma::mbar_wait_ns(&sbar, 0, umma::kWaitNs);
             if (!ok) {
                 // gave up: report, use no box entry, and wait once more
                 // (bounded) for the copy in flight before the CTA can exit
                 atomicOr(g.err, kErrMmaWait);
-                umma::mbar_wait_sleep(&sbar, 0, 1 << 16, 20000);
+                umma::mbar_wait_ns(&sbar, 0, umma::kDrainNs);
             }
         }
         ok = __syncthreads_and(ok);

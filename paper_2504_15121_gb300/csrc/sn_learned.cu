@@ -76,7 +76,6 @@ static_assert(kLatO >= 2 && kLatO % 2 == 0 && kLatO <= kLatM, "lattice origin");
 static_assert(kMT2 <= kThreads / 128, "one layer-2 tile per warp group in the head");
 static_assert(((kH1H + 1) / 2 - 1) * kPJ + (kH1W + 1) / 2 - 1 < kPlanePos, "the layer-1 map fits its planes");
 constexpr uint32_t kNetIdesc = umma::idesc_bf16<128, 16>();
-constexpr int kSleepPolls = 1 << 16;  // polls (each may sleep ~20 us) of a completion wait before giving up
 
 // The TMA box of one tile: columns x0 - kGX .. x0 - kGX + kGBW - 1 (x0 - kGX
 // a multiple of 8 elements, a 16-byte boundary for 4- and 2-byte input),
@@ -255,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     // One thread waits for an asynchronous step (sleeping between polls);
     // the block barrier that follows publishes it and the outcome.
     auto wait1 = [&](uint64_t* bar, int parity) {
-        return tid != 0 || umma::mbar_wait_sleep(bar, parity, kSleepPolls, 20000);
+        return tid != 0 || umma::mbar_wait_ns(bar, parity, umma::kWaitNs);
     };
     bool ok = wait1(wbar, 0);
 
@@ -445,10 +444,10 @@ __global__ void __launch_bounds__(kThreads, 2)
         // flight drain (bounded) before the TMEM is freed and the CTA exits.
         if (tid == 0) {
             atomicOr(g.err, kErrMmaWait);
-            if (nt) umma::mbar_wait_sleep(tbar, (nt - 1) & 1, kSleepPolls, 20000);
-            if (n1) umma::mbar_wait_sleep(l1bar, (n1 - 1) & 1, kSleepPolls, 20000);
-            if (n2) umma::mbar_wait_sleep(l2bar, (n2 - 1) & 1, kSleepPolls, 20000);
-            umma::mbar_wait_sleep(wbar, 0, kSleepPolls, 20000);
+            if (nt) umma::mbar_wait_ns(tbar, (nt - 1) & 1, umma::kDrainNs);
+            if (n1) umma::mbar_wait_ns(l1bar, (n1 - 1) & 1, umma::kDrainNs);
+            if (n2) umma::mbar_wait_ns(l2bar, (n2 - 1) & 1, umma::kDrainNs);
+            umma::mbar_wait_ns(wbar, 0, umma::kDrainNs);
         }
     }
     umma::fence_before();

@@ -535,7 +535,7 @@ __device__ __forceinline__ void stage_tile(int2* tile, unsigned char* raw, const
             umma::mbar_init(sbar, 1);
             umma::mbar_expect_tx(sbar, kRawBytes);
             umma::tma_load_2d(raw, dmap, x0 - tma_xpad<IN, R>(), y0 - R, sbar);
-            ok = umma::mbar_wait_sleep(sbar, 0, 1 << 16, 20000);
+            ok = umma::mbar_wait_ns(sbar, 0, umma::kWaitNs);
             if (!ok) {
                 // Gave up: report it, and wait once more (bounded) for the
                 // copy still in flight, so that this CTA's shared memory is
@@ -543,7 +543,7 @@ __device__ __forceinline__ void stage_tile(int2* tile, unsigned char* raw, const
                 // it.  No box entry is converted (the tile's codes become
                 // invalid); the frame's outputs are undefined after this.
                 atomicOr(g.err, kErrMmaWait);
-                umma::mbar_wait_sleep(sbar, 0, 1 << 16, 20000);
+                umma::mbar_wait_ns(sbar, 0, umma::kDrainNs);
             }
         }
         ok = __syncthreads_and(ok);

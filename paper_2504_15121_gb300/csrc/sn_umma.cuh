@@ -83,40 +83,40 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, 
         : "memory");
 }
 
-// Waits for the phase with the given parity to complete, for at most
-// `limit` polls; returns false if it did not.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int limit) {
-    const uint32_t a = smem_addr(mbar);
-    for (int it = 0; it < limit; it++) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-// The same wait with a suspend hint: between polls the thread may sleep in
-// hardware until the phase completes or about `hint_ns` nanoseconds pass, so
-// a long wait costs almost no issue slots.  At most `limit` polls.
-__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* mbar, uint32_t parity, int limit, uint32_t hint_ns) {
+// Waits for the phase with the given parity to complete.  Between polls the
+// thread may sleep in hardware until the phase completes or about 20 us
+// pass, so a long wait costs almost no issue slots.  Gives up (returns
+// false) once `timeout_ns` nanoseconds of the global timer have passed since
+// the call, or after 2^24 polls should that timer not advance.
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t* mbar, uint32_t parity, uint64_t timeout_ns) {
     const uint32_t a = smem_addr(mbar);
-    for (int it = 0; it < limit; it++) {
+    const uint64_t t0 = global_ns();
+    for (int it = 0; it < (1 << 24); it++) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
-            : "r"(a), "r"(parity), "r"(hint_ns)
+            : "r"(a), "r"(parity), "r"(20000u)
             : "memory");
         if (done) return true;
+        if (global_ns() - t0 > timeout_ns) return false;
     }
     return false;
 }
+
+// Bounds of the waits above.  A tile's copy or a tile's MMAs complete in
+// microseconds; a wait that runs out of kWaitNs reports a device error, and
+// the wait that then drains what is still in flight gets kDrainNs more
+// before the CTA frees its TMEM and shared memory.
+constexpr uint64_t kWaitNs = 500000000ull;    // 0.5 s
+constexpr uint64_t kDrainNs = 2000000000ull;  // 2 s
 
 // Warp-wide: allocates `ncols` TMEM columns (a power of two >= 32) and writes
 // their address to *slot; then gives up the CTA's right to allocate more.
