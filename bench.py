@@ -333,19 +333,19 @@ def run_ours(args):
     # precision form's I/O
     u16 = dict(in_dtype=sn.SN_IN_U16X256, normal_fmt=sn.SN_NORMALS_SNORM16X4)
     forms = {
-        "precision_u16_snorm16": time_form(scenes, args, u16, lambda s: s.disp_u16, 27, dist, world),
-        "learned_f32": time_form(scenes, args, dict(learned=1), lambda s: s.disp, FRAME_ALGO_BYTES, dist, world),
+        "precision_u16_snorm16": time_form(scenes, args, u16, lambda s: s.disp_u16, 27, dist, world, hbm_peak),
+        "learned_f32": time_form(scenes, args, dict(learned=1), lambda s: s.disp, FRAME_ALGO_BYTES, dist, world, hbm_peak),
         "learned_u16_snorm16": time_form(scenes, args, dict(u16, learned=1), lambda s: s.disp_u16, 27, dist,
-                                         world),
+                                         world, hbm_peak),
         # the paper's larger adaptive setting (Table perf-disc2): star-fill CD with 16 directions, 30 steps
         "cd_s30_d16_f32": time_form(scenes, args, dict(dirs=16, steps=30), lambda s: s.disp, FRAME_ALGO_BYTES,
-                                    dist, world),
+                                    dist, world, hbm_peak),
         # star-fill with the depth-edge stop (ST s10 d8 t0.1, Table perf-disc)
         "st_s10_d8_f32": time_form(scenes, args, dict(support=2, st_t=0.1), lambda s: s.disp, FRAME_ALGO_BYTES,
-                                   dist, world),
+                                   dist, world, hbm_peak),
         # fixed 9x9 affine window (the paper's n x n setting, n = 9)
         "fixed_9x9_f32": time_form(scenes, args, dict(support=0, r_affine=4), lambda s: s.disp, FRAME_ALGO_BYTES,
-                                   dist, world),
+                                   dist, world, hbm_peak),
     }
     for f in forms.values():
         f["vs_plain"] = f["value"] / value
@@ -483,7 +483,7 @@ def latency_pass(pipe, disp, outs, n):
     return sorted(a.elapsed_time(b) for a, b in ev)
 
 
-def time_form(scenes, args, params, pick, bytes_per_px, dist, world):
+def time_form(scenes, args, params, pick, bytes_per_px, dist, world, hbm_peak=None):
     """Device throughput and per-frame times of another form of the chain on
     the same scenes (same frames per step and step count)."""
     import torch
@@ -511,13 +511,20 @@ def time_form(scenes, args, params, pick, bytes_per_px, dist, world):
     sn.sn_check_device(pipe.ctx)
     fm = latency_pass(pipe, disp, outs, max(1, steps // 4) * F)
     sn.sn_check_device(pipe.ctx)
+    # the form's frame kernel(s) alone: live event times on one stream,
+    # algorithmic bytes (the chain's less the labels) against the HBM peak
+    stage_ms, nframes, _ = profiled_pass(pipe, disp, outs, max(1, steps // 8))
     gt = gt_error_deg(outs, scenes)
     pipe.close()
     ms = max_over_ranks(ms, dist)
     W, H = s0.W, s0.H
+    kern_us = 1e3 * stage_ms.get("frame", 0.0) / max(nframes, 1)
+    kern_gbs = (bytes_per_px - 4) * W * H / (kern_us / 1e6) / 1e9 if kern_us > 0 else None
     return {"value": whole_job_mpix(world, steps * F * W * H, ms), "unit": "MPix/s", "steps": steps,
             "frame_ms_p50": fm[len(fm) // 2] if fm else None,
             "frame_ms_p99": fm[min(len(fm) - 1, int(0.99 * (len(fm) - 1) + 0.5))] if fm else None,
+            "frame_kernel_us": kern_us,
+            "frame_kernel_hbm_frac": kern_gbs / hbm_peak if kern_gbs and hbm_peak else None,
             "algo_bytes_per_px": bytes_per_px,
             "gt_error_deg": gt,
             "params": {k: (v if isinstance(v, float) else int(v)) for k, v in params.items()}}

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
     // ---- stage the tile and its halo: (D, 1/D)
     const int n = TWR * THR;
     if constexpr (frame_tma(VAR, R)) {
-        stage_tile<IN, R, TH, NT>(tile, smem + tma_raw_off<IN, VAR, R>(), &dmap, true, disp, dp, x0, y0, g, true);
+        stage_tile<IN, R, TH, NT>(tile, smem + tma_raw_off<IN, VAR, R>(), &dmap, true, disp, dp, x0, y0, g, kStageRcp);
     } else {
         for (int i = tid; i < n; i += NT) {
             const int ly = i / TWR;
@@ -106,22 +106,6 @@ __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR
         plain_pixel<VAR, R, RD>(g, &T, c, TWR, x, y, r, Est + (c - tile));
         emit(g, o, x, y, r);
     }
-}
-
-// Raises a kernel's dynamic shared-memory limit once per device, to the most
-// any parameter set of its variant can ask for (so no launch, and no launch
-// under stream capture, changes function attributes).  `done` is the
-// per-variant record of the devices already set.
-template <class Kernel>
-cudaError_t smem_limit_once(Kernel k, size_t bytes, std::atomic<unsigned long long>& done) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    const unsigned long long bit = 1ull << (dev & 63);
-    if (done.load() & bit) return cudaSuccess;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) done.fetch_or(bit);
-    return e;
 }
 
 template <int IN, int VAR, int R, int RD>
@@ -203,7 +187,7 @@ __global__ void __launch_bounds__(kTW* kSTH, 4)
     __shared__ int2 tile[TW * (kSTH + 2 * R)];
     __shared__ __align__(128) unsigned char raw[tma_bw<IN, R, TW>() * (kSTH + 2 * R) * tma_esize<IN>() + 16];
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kSTH;
-    stage_tile<IN, R, kSTH, kTW * kSTH>(tile, raw, &dmap, use_tma, disp, dp, x0, y0, g, true);
+    stage_tile<IN, R, kSTH, kTW * kSTH>(tile, raw, &dmap, use_tma, disp, dp, x0, y0, g, kStageRcp);
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     if (x >= g.W || y >= g.H) return;
     const int2* c = tile + (threadIdx.y + R) * TW + threadIdx.x + R;
@@ -324,7 +308,7 @@ cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const voi
     else if (g.support == SN_SUPPORT_STARFILL_ST)
         e = launch_var<4, 0, 0>(g, t, disp, dp, o, s);
     else if (g.r_a == 4 && g.r_d == 2)
-        e = launch_var<0, 4, 2>(g, t, disp, dp, o, s);  // the 9x9 window with the 5x5 denoise
+        e = launch_window(g, disp, dp, o, s);  // the 9x9 window with the 5x5 denoise, convolution form
     else
         e = launch_var<0, 0, 0>(g, t, disp, dp, o, s);
     mk.after(s);

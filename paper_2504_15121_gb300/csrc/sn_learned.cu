@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     // the gate bit the gate kernel left in the mask
     const bool cand = inside && (o.mask[(size_t)y * o.mp + x] & SN_MASK_LEARNED);
     if (tid == 0) *cnt = 0;
-    stage_tile<IN, kLR, kTH, kThreads>(tile, smem + kCOffRS, &dmap, true, disp, dp, x0, y0, g, true);
+    stage_tile<IN, kLR, kTH, kThreads>(tile, smem + kCOffRS, &dmap, true, disp, dp, x0, y0, g, kStageRcp);
     const int2* c = tile + (row + kLR) * kLTWR + lane + kLR;
     const int Dc = c[0].x;  // 0 outside the image
     const bool gated = cand && Dc > 0;
@@ -585,18 +585,6 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 }
 
-template <class Kernel>
-cudaError_t smem_once(Kernel k, size_t bytes, std::atomic<unsigned long long>& done) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    const unsigned long long bit = 1ull << (dev & 63);
-    if (done.load() & bit) return cudaSuccess;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) done.fetch_or(bit);
-    return e;
-}
-
 int sm_count() {
     static std::atomic<int> cached[64];
     int dev = 0;
@@ -616,7 +604,7 @@ cudaError_t launch_gate(const Geo& g, const void* disp, size_t dp, const FrameOu
     const cudaError_t me = encode_disp_map(&dmap, disp, dp, g.W, g.H, IN, kGBW, kGBH);
     if (me != cudaSuccess) return me;
     static std::atomic<unsigned long long> done{0};
-    const cudaError_t e = smem_once(k_gate<IN, QMAP>, kGSmem, done);
+    const cudaError_t e = smem_limit_once(k_gate<IN, QMAP>, kGSmem, done);
     if (e != cudaSuccess) return e;
     const int ntiles = ((g.W + kTW - 1) / kTW) * ((g.H + kTH - 1) / kTH);
     const int grid = ntiles < 2 * sm_count() ? ntiles : 2 * sm_count();  // two resident CTAs per SM
@@ -630,7 +618,7 @@ cudaError_t launch_chain(const Geo& g, const void* disp, size_t dp, const FrameO
     const cudaError_t me = encode_disp_map(&dmap, disp, dp, g.W, g.H, IN, tma_bw<IN, kLR, kLTWR>(), kLTHR);
     if (me != cudaSuccess) return me;
     static std::atomic<unsigned long long> done{0};
-    const cudaError_t e = smem_once(k_learned<IN>, kCSmem, done);
+    const cudaError_t e = smem_limit_once(k_learned<IN>, kCSmem, done);
     if (e != cudaSuccess) return e;
     const dim3 grid((g.W + kTW - 1) / kTW, (g.H + kTH - 1) / kTH), block(kTW, kTH);
     k_learned<IN><<<grid, block, kCSmem, s>>>(g, static_cast<const char*>(disp), dp, o, dmap);

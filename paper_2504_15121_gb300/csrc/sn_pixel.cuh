@@ -6,6 +6,8 @@
 // linkage.
 #pragma once
 
+#include <atomic>
+
 #include <cuda.h>  // CUtensorMap
 #include <cuda_bf16.h>
 
@@ -462,6 +464,22 @@ struct WinSums {
     int n, Su, Sv, Suu, Suv, Svv, SD, SuD, SvD;
 };
 
+// The denoise fit over the samples a 5x5 window's sums w2 cover (the same
+// integers as denoise_exact<2> over the same samples): intercept
+// Dc + num / det; false where det <= 0 or the intercept is not positive.
+// The 5x5 window bounds the moments: the cofactors and det fit in 32 bits,
+// det below 2^24.
+__device__ __forceinline__ bool denoise_from_sums(const WinSums& w2, int Dc, long long& num, long long& det) {
+    const int b0 = w2.SD - w2.n * Dc, b1 = w2.SuD - w2.Su * Dc, b2 = w2.SvD - w2.Sv * Dc;
+    const int M00 = w2.Suu * w2.Svv - w2.Suv * w2.Suv;
+    const int M10 = w2.Su * w2.Svv - w2.Sv * w2.Suv;
+    const int M20 = w2.Su * w2.Suv - w2.Sv * w2.Suu;
+    const int d = w2.n * M00 - w2.Su * M10 + w2.Sv * M20;
+    det = d;
+    num = (long long)b0 * M00 - (long long)b1 * M10 + (long long)b2 * M20;
+    return d > 0 && (long long)Dc * d + num > 0;
+}
+
 // The learned fast path of a certified pixel (its (2 kFastR + 1)^2 window
 // shows one surface): the denoise fit takes every valid sample of the 5x5
 // window (no range gate) and the affine fit every valid sample of the full
@@ -470,16 +488,9 @@ __device__ __forceinline__ void fast_pixel(const Geo& g, int Dc, const WinSums& 
                                            PixOut& r) {
     pix_zero(r);
     r.m = SN_MASK_VALID | SN_MASK_LEARNED;
-    // the 5x5 window bounds the moments (as in denoise_exact<2>): the
-    // cofactors and det fit in 32 bits, det below 2^24
-    const int b0 = w2.SD - w2.n * Dc, b1 = w2.SuD - w2.Su * Dc, b2 = w2.SvD - w2.Sv * Dc;
-    const int M00 = w2.Suu * w2.Svv - w2.Suv * w2.Suv;
-    const int M10 = w2.Su * w2.Svv - w2.Sv * w2.Suv;
-    const int M20 = w2.Su * w2.Suv - w2.Sv * w2.Suu;
-    const int det = w2.n * M00 - w2.Su * M10 + w2.Sv * M20;
-    const long long num = (long long)b0 * M00 - (long long)b1 * M10 + (long long)b2 * M20;
-    const bool fit = det > 0 && (long long)Dc * det + num > 0;
-    const float dcf = fit ? i64_to_f32(num) / (float)det : 0.0f;
+    long long num, det;
+    const bool fit = denoise_from_sums(w2, Dc, num, det);
+    const float dcf = fit ? i64_to_f32(num) / (float)(int)det : 0.0f;
     if (fit) r.m |= SN_MASK_DENOISED;
     r.dtil = ((float)Dc + dcf) * (1.0f / 256.0f);
     AffSums s;
@@ -512,14 +523,20 @@ template <int IN, int R, int TWR> constexpr int tma_bw() {
     return (tma_xpad<IN, R>() - R + TWR + 16 / tma_esize<IN>() - 1) / (16 / tma_esize<IN>()) * (16 / tma_esize<IN>());
 }
 
-// Stages the (32 + 2R) x (TH + 2R) tile around (x0, y0) as (D, 1/D) pairs
-// (1/D only if with_rcp): one TMA copy of the raw box into `raw` (128-byte
-// aligned, tma_bw x (TH + 2R) elements, then an 8-byte mbarrier), then a
-// conversion pass.  If `use_tma` is off or `raw` is not 128-byte aligned,
-// the tile is loaded with plain loads instead.  Ends with a block barrier.
+// What stage_tile writes beside each code D: nothing (0), 1/D (FP32
+// within 1 ulp; +inf for an invalid code) or D + 2^23 [D > 0] (the code and
+// its validity in one word, for window sums).
+enum StageY { kStageZero = 0, kStageRcp = 1, kStagePacked = 2 };
+
+// Stages the (32 + 2R) x (TH + 2R) tile around (x0, y0) as (D, y) pairs, y
+// as `ymode` (a StageY) says: one TMA copy of the raw box into `raw`
+// (128-byte aligned, tma_bw x (TH + 2R) elements, then an 8-byte mbarrier),
+// then a conversion pass.  If `use_tma` is off or `raw` is not 128-byte
+// aligned, the tile is loaded with plain loads instead.  Ends with a block
+// barrier.
 template <int IN, int R, int TH, int NT>
 __device__ __forceinline__ void stage_tile(int2* tile, unsigned char* raw, const CUtensorMap* dmap, bool use_tma,
-                                           const char* disp, size_t dp, int x0, int y0, const Geo& g, bool with_rcp) {
+                                           const char* disp, size_t dp, int x0, int y0, const Geo& g, int ymode) {
     constexpr int TW = kTW + 2 * R, N = TW * (TH + 2 * R), BW = tma_bw<IN, R, TW>();
     constexpr int kRawBytes = BW * (TH + 2 * R) * tma_esize<IN>();
     static_assert(kRawBytes % 16 == 0 && (BW * tma_esize<IN>()) % 16 == 0, "TMA box rows of whole 16-byte units");
@@ -563,13 +580,33 @@ __device__ __forceinline__ void stage_tile(int2* tile, unsigned char* raw, const
         } else if (!tma) {
             D = load_code<IN>(disp, dp, x0 - R + lx, y0 - R + ly, g.W, g.H);
         }
-        const float w = !with_rcp ? 0.0f : (D > 0 ? rcp_approx((float)D) : __int_as_float(0x7f800000));
-        tile[i] = make_int2(D, __float_as_int(w));
+        int y = 0;
+        if (ymode == kStageRcp)
+            y = __float_as_int(D > 0 ? rcp_approx((float)D) : __int_as_float(0x7f800000));
+        else if (ymode == kStagePacked)
+            y = D + (D > 0 ? 1 << 23 : 0);
+        tile[i] = make_int2(D, y);
     }
     __syncthreads();
 }
 constexpr size_t align16z(size_t b) { return (b + 15) & ~(size_t)15; }
 constexpr size_t align128z(size_t b) { return (b + 127) & ~(size_t)127; }
+
+// Raises a kernel's dynamic shared-memory limit once per device, to the most
+// any launch of it can ask for (so no launch, and no launch under stream
+// capture, changes function attributes).  `done` is the kernel's record of
+// the devices already set.
+template <class Kernel>
+cudaError_t smem_limit_once(Kernel k, size_t bytes, std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done.fetch_or(bit);
+    return e;
+}
 
 }  // namespace
 
