@@ -68,7 +68,25 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-resolution batch")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
-    return ap.parse_args()
+    ap.add_argument("--only-headline", action="store_true",
+                    help="time the headline chain only (no other forms, comparators, stage calls, scene errors, "
+                         "mixed batch, end to end, CPU baseline or serving): short runs for profilers")
+    ap.add_argument("--params", default="",
+                    help="sn_params overrides of the headline pipeline, e.g. support=0,r_affine=4 or learned=1 "
+                         "(for profiling another form; the line then names them in its config)")
+    args = ap.parse_args()
+    if args.only_headline:
+        args.no_mixed = args.no_e2e = args.no_cpu_baseline = args.no_serving = True
+    return args
+
+
+def parse_params(text):
+    """'k=v,k=v' -> dict of sn_params overrides (ints, or floats where the value has a '.')."""
+    out = {}
+    for item in filter(None, text.split(",")):
+        k, v = item.split("=")
+        out[k.strip()] = float(v) if "." in v else int(v)
+    return out
 
 
 # ---------------------------------------------------------------- clocks
@@ -266,8 +284,10 @@ def run_ours(args):
     scenes = make_inputs(args.distinct, rank)
     s0 = scenes[0]
     W, H, cam = s0.W, s0.H, s0.camera
-    pipe = Pipeline(cam, W, H)
-    disp = [pipe.upload(s.disp) for s in scenes]
+    overrides = parse_params(args.params)
+    pipe = Pipeline(cam, W, H, **overrides)
+    u16_in = overrides.get("in_dtype") == sn.SN_IN_U16X256
+    disp = [pipe.upload(s.disp_u16 if u16_in else s.disp) for s in scenes]
     F = args.frames
     outs = [pipe.buffers() for _ in range(F)]
     stream = torch.cuda.current_stream()
@@ -332,7 +352,7 @@ def run_ours(args):
     # normals out (precision form); the learned gate with FP32 and with the
     # precision form's I/O
     u16 = dict(in_dtype=sn.SN_IN_U16X256, normal_fmt=sn.SN_NORMALS_SNORM16X4)
-    forms = {
+    forms = None if args.only_headline else {
         "precision_u16_snorm16": time_form(scenes, args, u16, lambda s: s.disp_u16, 27, dist, world, hbm_peak),
         "learned_f32": time_form(scenes, args, dict(learned=1), lambda s: s.disp, FRAME_ALGO_BYTES, dist, world, hbm_peak),
         "learned_u16_snorm16": time_form(scenes, args, dict(u16, learned=1), lambda s: s.disp_u16, 27, dist,
@@ -347,16 +367,16 @@ def run_ours(args):
         "fixed_9x9_f32": time_form(scenes, args, dict(support=0, r_affine=4), lambda s: s.disp, FRAME_ALGO_BYTES,
                                    dist, world, hbm_peak),
     }
-    for f in forms.values():
+    for f in (forms or {}).values():
         f["vs_plain"] = f["value"] / value
     # the comparison estimators of Sec. IV on the same scenes (normals only)
     comparators = None
-    if world == 1:
+    if world == 1 and not args.only_headline:
         comparators = {"cross": time_comparator(scenes, args, "cross", 0, world),
                        "pca_9x9": time_comparator(scenes, args, "pca", 4, world)}
-    stage_calls = time_stage_calls(scenes, args) if world == 1 else None
+    stage_calls = time_stage_calls(scenes, args) if world == 1 and not args.only_headline else None
     # every method's ground-truth error on the box-and-curve scene (1482x994)
-    errors_mixed = scene_errors("mixed_1482x994") if world == 1 else None
+    errors_mixed = scene_errors("mixed_1482x994") if world == 1 and not args.only_headline else None
     # mixed-resolution batch of 64 frames, one graph launch per step
     mixed = run_mixed_batch(args) if world == 1 and not args.no_mixed else None
 
@@ -389,6 +409,7 @@ def run_ours(args):
                 "l2": "inputs+outputs per step "
                       f"{F * W * H * (4 + FRAME_ALGO_BYTES - 4) / 1e9:.2f} GB >> 129 MB L2 (no flush needed)",
                 "parallelism": f"replicas x{world}",
+                **({"params": overrides} if overrides else {}),
             },
             "frame_ms": {"p50": pct(0.5), "p99": pct(0.99), "max": fm[-1] if fm else None,
                          "source": "CUDA events around each sn_run_frame on one stream, frames back to back, "
@@ -848,7 +869,7 @@ def run_serving(args):
 
 # sources each kernel's build depends on (the traffic figure is void once
 # any of them has changed since the capture)
-KERNEL_SOURCES = {"frame": ("sn_frame.cu", "sn_device.cuh", "sn_umma.cuh", "sn_internal.h")}
+KERNEL_SOURCES = {"frame": ("sn_frame.cu", "sn_pixel.cuh", "sn_device.cuh", "sn_umma.cuh", "sn_internal.h")}
 
 
 def kernel_source_sha(kernel: str):
