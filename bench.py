@@ -369,6 +369,11 @@ def run_ours(args):
     }
     for f in (forms or {}).values():
         f["vs_plain"] = f["value"] / value
+    # accuracy against throughput: plain settings of the support (the paper's
+    # star-fill sizes and fixed windows) on the same scenes, and the learned
+    # form against the fastest of them that is at least as accurate
+    frontier = None if args.only_headline else accuracy_frontier(scenes, args, dist, world, hbm_peak, value,
+                                                                 gt_plain, forms)
     # the comparison estimators of Sec. IV on the same scenes (normals only)
     comparators = None
     if world == 1 and not args.only_headline:
@@ -436,6 +441,7 @@ def run_ours(args):
                                                 f"{sm_mhz:.0f} MHz (median sampled SM clock)"}},
             "gpu_launches": int(launches),
             "forms": forms,
+            "accuracy_frontier": frontier,
             "comparators": comparators,
             "stage_calls": stage_calls,
             "gt_error_by_method_mixed_1482x994": errors_mixed,
@@ -549,6 +555,45 @@ def time_form(scenes, args, params, pick, bytes_per_px, dist, world, hbm_peak=No
             "algo_bytes_per_px": bytes_per_px,
             "gt_error_deg": gt,
             "params": {k: (v if isinstance(v, float) else int(v)) for k, v in params.items()}}
+
+
+FRONTIER = {
+    "cd_s20_d8": dict(dirs=8, steps=20),
+    "cd_s30_d8": dict(dirs=8, steps=30),
+    "cd_s10_d16": dict(dirs=16, steps=10),
+    "cd_s20_d16": dict(dirs=16, steps=20),
+    "fixed_5x5": dict(support=0, r_affine=2),
+    "fixed_13x13": dict(support=0, r_affine=6),
+}
+
+
+def accuracy_frontier(scenes, args, dist, world, hbm_peak, plain_value, gt_plain, forms):
+    """MPix/s and mean ground-truth error of plain settings beside the default
+    (CD s10 d8) and the forms already timed (CD s30 d16, fixed 9x9), and the
+    learned forms' throughput against the fastest plain setting whose error
+    is no worse than theirs (the comparison at equal angular error)."""
+    pts = {"cd_s10_d8": {"value": plain_value, "gt_error_deg": gt_plain["mean"], "pixels": gt_plain["pixels"]}}
+    for k in ("cd_s30_d16_f32", "fixed_9x9_f32", "st_s10_d8_f32"):
+        pts[k[:-4]] = {"value": forms[k]["value"], "gt_error_deg": forms[k]["gt_error_deg"]["mean"],
+                       "pixels": forms[k]["gt_error_deg"]["pixels"]}
+    for name, params in FRONTIER.items():
+        f = time_form(scenes, args, params, lambda s: s.disp, FRAME_ALGO_BYTES, dist, world, hbm_peak)
+        pts[name] = {"value": f["value"], "gt_error_deg": f["gt_error_deg"]["mean"],
+                     "pixels": f["gt_error_deg"]["pixels"], "params": f["params"]}
+    out = {"plain": pts,
+           "rule": "a plain setting counts as at least as accurate when its mean error is no higher and it "
+                   "gives normals at no fewer than 99 % of the learned form's pixels (ST, which drops most "
+                   "pixels of the driving scene as edges, does not qualify)"}
+    for lk in ("learned_f32", "learned_u16_snorm16"):
+        e, v = forms[lk]["gt_error_deg"]["mean"], forms[lk]["value"]
+        npx = forms[lk]["gt_error_deg"]["pixels"]
+        ok = {k: p for k, p in pts.items() if p["gt_error_deg"] <= e and p["pixels"] >= 0.99 * npx}
+        best = max(ok, key=lambda k: ok[k]["value"]) if ok else None
+        out[lk] = {"value": v, "gt_error_deg": e,
+                   "fastest_plain_as_accurate": best,
+                   "vs_that_plain": v / ok[best]["value"] if best else None,
+                   "vs_default_plain": v / plain_value}
+    return out
 
 
 def time_comparator(scenes, args, which, r, world):
