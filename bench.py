@@ -563,7 +563,10 @@ FRONTIER = {
     "cd_s10_d16": dict(dirs=16, steps=10),
     "cd_s20_d16": dict(dirs=16, steps=20),
     "fixed_5x5": dict(support=0, r_affine=2),
+    "fixed_7x7": dict(support=0, r_affine=3),
+    "fixed_11x11": dict(support=0, r_affine=5),
     "fixed_13x13": dict(support=0, r_affine=6),
+    "fixed_15x15": dict(support=0, r_affine=7),
 }
 
 
@@ -668,7 +671,8 @@ def scene_errors(scene_name, n_frames=4):
     s0 = scenes[0]
     out = {"scene": scene_name, "frames": n_frames}
     chains = {"cd_s10_d8": {}, "cd_s30_d16": dict(dirs=16, steps=30), "st_s10_d8": dict(support=2, st_t=0.1),
-              "fixed_9x9": dict(support=0, r_affine=4), "learned": dict(learned=1)}
+              "fixed_9x9": dict(support=0, r_affine=4), "fixed_13x13": dict(support=0, r_affine=6),
+              "fixed_15x15": dict(support=0, r_affine=7), "learned": dict(learned=1)}
     for name, params in chains.items():
         pipe = Pipeline(s0.camera, s0.W, s0.H, **params)
         try:

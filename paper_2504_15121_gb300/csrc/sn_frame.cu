@@ -307,8 +307,8 @@ cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const voi
         e = g.r_d == 2 ? launch_var<5, 11, 2>(g, t, disp, dp, o, s) : launch_var<5, 11, 0>(g, t, disp, dp, o, s);
     else if (g.support == SN_SUPPORT_STARFILL_ST)
         e = launch_var<4, 0, 0>(g, t, disp, dp, o, s);
-    else if (g.r_a == 4 && g.r_d == 2)
-        e = launch_window(g, disp, dp, o, s);  // the 9x9 window with the 5x5 denoise, convolution form
+    else if (window_supported(g))
+        e = launch_window(g, disp, dp, o, s);  // fixed windows up to 15x15 with the 5x5 denoise, convolution form
     else
         e = launch_var<0, 0, 0>(g, t, disp, dp, o, s);
     mk.after(s);

@@ -177,8 +177,10 @@ cudaError_t launch_learned(const Geo& g, const void* disp, size_t dp, const Fram
 // kernel (star M = 8, s = 10, r_d = 2).
 cudaError_t launch_frame(const Geo& g, const StarTable& t, bool star8, const void* disp, size_t dp,
                          const FrameOut& o, const GateView* gv, cudaStream_t s, Marks& mk);
-// The fixed 9 x 9 window with the 5 x 5 denoise (r_a = 4, r_d = 2) in its
-// convolution form: one fused kernel like launch_frame's.
+// The fixed (2 r_a + 1)^2 window with the 5 x 5 denoise (2 <= r_a <= 7,
+// r_d = 2; window_supported) in its convolution form: one fused kernel like
+// launch_frame's.
+bool window_supported(const Geo& g);
 cudaError_t launch_window(const Geo& g, const void* disp, size_t dp, const FrameOut& o, cudaStream_t s);
 bool star_is_m8(const StarTable& t, int dirs, int steps);
 // Host: the prefix moments of the table's rays (dirs (steps + 1) 6 ints; see

@@ -524,7 +524,7 @@ template <int IN, int R, int TWR> constexpr int tma_bw() {
 }
 
 // What stage_tile writes beside each code D: nothing (0), 1/D (FP32
-// within 1 ulp; +inf for an invalid code) or D + 2^23 [D > 0] (the code and
+// within 1 ulp; +inf for an invalid code) or D + 2^24 [D > 0] (the code and
 // its validity in one word, for window sums).
 enum StageY { kStageZero = 0, kStageRcp = 1, kStagePacked = 2 };
 
@@ -584,7 +584,7 @@ __device__ __forceinline__ void stage_tile(int2* tile, unsigned char* raw, const
         if (ymode == kStageRcp)
             y = __float_as_int(D > 0 ? rcp_approx((float)D) : __int_as_float(0x7f800000));
         else if (ymode == kStagePacked)
-            y = D + (D > 0 ? 1 << 23 : 0);
+            y = D + (D > 0 ? 1 << 24 : 0);
         tile[i] = make_int2(D, y);
     }
     __syncthreads();

@@ -1,10 +1,10 @@
-// The fixed 9 x 9 window (r_a = 4) with the 5 x 5 range-gated denoise, in
-// the convolution form of Sec. III-C: every sum the two fits need over a
-// square window is a separable sum of per-sample terms (1, u, u^2, D, u D
-// along a row; then weights 1, v, v^2 along the column), so a row pass
-// over the staged tile and a column pass over the row sums give every
-// pixel's sums at a cost per pixel that no longer grows with the window's
-// area.
+// The fixed (2R + 1)^2 window (r_a = R, 2 <= R <= 7) with the 5 x 5
+// range-gated denoise, in the convolution form of Sec. III-C: every sum the
+// two fits need over a square window is a separable sum of per-sample terms
+// (1, u, u^2, D, u D along a row; then weights 1, v, v^2 along the column),
+// so a row pass over the staged tile and a column pass over the row sums
+// give every pixel's sums at a cost per pixel that grows with the window's
+// side, not its area.
 //
 // Denoise: where every valid sample of a pixel's 5 x 5 window passes the
 // range gate (the usual case: one surface), the gated fit takes exactly the
@@ -25,40 +25,52 @@ namespace sn {
 
 namespace {
 
-constexpr int kWR = 4;                     // the window's radius r_a
-constexpr int kWTH = 16;                   // tile rows; 32 x 8 threads, two pixels each (rows ty, ty + 8)
-constexpr int kWNT = kTW * 8;              // threads per CTA
-constexpr int kWTW = kTW + 2 * kWR;        // 40 staged columns
-constexpr int kWTHR = kWTH + 2 * kWR;      // 24 staged rows
-constexpr int kWRS = kWTHR * kTW;          // row sums: every staged row, the tile's 32 columns
-static_assert(kWRS % kWNT == 0, "whole row-pass rounds");
-constexpr size_t kWOffTile = 0;
-constexpr size_t kWOffRS9 = align128z(sizeof(int2) * kWTW * kWTHR);
-constexpr size_t kWOffRS5 = kWOffRS9 + sizeof(int4) * kWRS;
-constexpr size_t kWOffMM = kWOffRS5 + sizeof(int4) * kWRS;
-constexpr size_t kWOffList = kWOffMM + sizeof(int2) * kWRS;
-constexpr size_t kWOffCnt = kWOffList + sizeof(int) * kTW * kWTH;
-constexpr size_t kWSmem = align128z(kWOffCnt + 16);
-// the raw TMA box (and its mbarrier) lies where the 9-wide row sums go
-static_assert(tma_bw<SN_IN_F32, kWR, kWTW>() * kWTHR * 4 + 8 <= sizeof(int4) * kWRS, "raw box inside the row sums");
+constexpr int kWTH = 16;       // tile rows; 32 x 8 threads, two pixels each (rows ty, ty + 8)
+constexpr int kWNT = kTW * 8;  // threads per CTA
 
-// Row sums of one staged entry over |u| <= h, from the packed words
-// E = D + 2^23 [D > 0] (D < 2^17).  Over at most 9 samples with |u| <= 4:
-// sum E = sum D + 2^23 n with sum D < 9 * 2^17 < 2^23; sum u E = sum u D +
-// 2^23 sum u with |sum u D| <= 20 * 2^17 < 2^22; sum u^2 E = sum u^2 D +
-// 2^23 sum u^2 with sum u^2 D <= 60 * 2^17 < 2^23.  Unpacked into
+// Geometry and shared-memory layout of the kernel for window radius R.
+template <int R>
+struct Win {
+    static_assert(R >= 2 && R <= 7, "window radius 2..7");
+    static constexpr int HR = R;                  // halo (>= 2, the denoise's)
+    static constexpr int TW = kTW + 2 * HR;       // staged columns
+    static constexpr int THR = kWTH + 2 * HR;     // staged rows
+    static constexpr int RS = THR * kTW;          // row sums: every staged row, the tile's 32 columns
+    static constexpr int ROUNDS = (RS + kWNT - 1) / kWNT;
+    static constexpr size_t OFF_TILE = 0;
+    static constexpr size_t OFF_RSA = align128z(sizeof(int2) * TW * THR);  // the full window's row sums
+    static constexpr size_t OFF_RS5 = OFF_RSA + sizeof(int4) * RS;
+    static constexpr size_t OFF_MM = OFF_RS5 + sizeof(int4) * RS;
+    static constexpr size_t OFF_LIST = OFF_MM + sizeof(int2) * RS;
+    static constexpr size_t OFF_CNT = OFF_LIST + sizeof(int) * kTW * kWTH;
+    static constexpr size_t SMEM = align128z(OFF_CNT + 16);
+    // sums of u^2 E stay packed up to R = 5 (sum u^2 D <= 110 * 2^17 < 2^24)
+    static constexpr bool PACKED_UU = R <= 5;
+    // moments bounded as for the M = 8, s = 10 star (1024 alpha gamma < 2^31)
+    // up to R = 5: the 32-bit solve
+    static constexpr bool SOLVE32 = R <= 5;
+};
+static_assert(tma_bw<SN_IN_F32, 7, Win<7>::TW>() * Win<7>::THR * 4 + 8 <= sizeof(int4) * Win<7>::RS,
+              "raw box inside the row sums");
+static_assert(4 * (Win<7>::SMEM + 1024) <= 228 * 1024, "four CTAs per SM");
+
+// Row sums of one staged entry, from the packed words E = D + 2^24 [D > 0]
+// (D < 2^17) over |u| <= R <= 7 (at most 15 samples): sum E = sum D +
+// 2^24 n with sum D < 15 * 2^17 < 2^24; sum u E = sum u D + 2^24 sum u with
+// |sum u D| <= 56 * 2^17 < 2^23; sum u^2 E = sum u^2 D + 2^24 sum u^2 where
+// that packs (R <= 5), else sum u^2 directly.  Unpacked into
 // (n + 2^16 sum u, sum u^2, sum D, sum u D).
-__device__ __forceinline__ int4 unpack_row(int Q0, int Q1, int Q2) {
-    const int n = Q0 >> 23, SD = Q0 & 0x7FFFFF;
-    const int Su = (Q1 + (1 << 22)) >> 23;
-    const int SuD = Q1 - Su * (1 << 23);
-    return make_int4(n + Su * 65536, Q2 >> 23, SD, SuD);
+__device__ __forceinline__ int4 unpack_row(int Q0, int Q1, int Suu) {
+    const int n = Q0 >> 24, SD = Q0 & 0xFFFFFF;
+    const int Su = (Q1 + (1 << 23)) >> 24;
+    const int SuD = Q1 - Su * (1 << 24);
+    return make_int4(n + Su * 65536, Suu, SD, SuD);
 }
 
 // Column pass over rows j = -H .. H of the row sums (A = n + 2^16 sum u per
 // row, B = sum u^2, sum D, sum u D): sum A = n + 2^16 Su, sum j A = Sv +
 // 2^16 Suv, sum j^2 A = Svv + 2^16 (sum v^2 u), each low field within its
-// 16 bits (n <= 81, |Sv| <= 180, Svv <= 540).
+// 16 bits (n <= 225, |Sv| <= 840, Svv <= 4200 for H <= 7).
 template <int H>
 __device__ __forceinline__ WinSums column_sums(const int4* rs, int e0) {
     int SA = 0, SAv = 0, SAv2 = 0, SB = 0, SQ0 = 0, SQ0v = 0, SQ1 = 0;
@@ -86,11 +98,10 @@ __device__ __forceinline__ WinSums column_sums(const int4* rs, int e0) {
     return w;
 }
 
-// The affine fit over the 9 x 9 window's valid samples except the centre
-// (sums wa include the centre, which adds only to n and SD), anchored at
-// the denoised centre; normal, point and mask.  The window bounds the
-// moments like the M = 8, s = 10 star (alpha gamma <= 540^2), so the 32-bit
-// solve applies.
+// The affine fit over the window's valid samples except the centre (sums
+// wa include the centre, which adds only to n and SD), anchored at the
+// denoised centre; normal, point and mask.
+template <bool SOLVE32>
 __device__ __forceinline__ void window_affine(const Geo& g, int Dc, bool fit, long long num, long long det,
                                               const WinSums& wa, int x, int y, PixOut& r) {
     pix_zero(r);
@@ -108,37 +119,40 @@ __device__ __forceinline__ void window_affine(const Geo& g, int Dc, bool fit, lo
     s.Bu = wa.SuD - Dc * wa.Su;
     s.Bv = wa.SvD - Dc * wa.Sv;
     bool fp64;
-    if (solve_normal_dc<true>(s, Dc, dcf, [=] { return fit ? (double)num / (double)det : 0.0; }, r.dtil, x, y, g,
-                              r.n, fp64))
+    if (solve_normal_dc<SOLVE32>(s, Dc, dcf, [=] { return fit ? (double)num / (double)det : 0.0; }, r.dtil, x, y,
+                                 g, r.n, fp64))
         r.m |= SN_MASK_NORMAL | (fp64 ? SN_MASK_FP64 : 0);
     pix_points(g, x, y, r);
 }
 
-template <int IN>
+template <int IN, int R>
 __global__ void __launch_bounds__(kWNT, 4)
     k_window(const Geo g, const char* __restrict__ disp, size_t dp, const FrameOut o,
              const __grid_constant__ CUtensorMap dmap) {
+    using L = Win<R>;
     extern __shared__ __align__(128) unsigned char smem[];
-    int2* tile = reinterpret_cast<int2*>(smem + kWOffTile);
-    int4* rs9 = reinterpret_cast<int4*>(smem + kWOffRS9);
-    int4* rs5 = reinterpret_cast<int4*>(smem + kWOffRS5);
-    int2* mm5 = reinterpret_cast<int2*>(smem + kWOffMM);
-    int* list = reinterpret_cast<int*>(smem + kWOffList);
-    int* cnt = reinterpret_cast<int*>(smem + kWOffCnt);
+    int2* tile = reinterpret_cast<int2*>(smem + L::OFF_TILE);
+    int4* rsa = reinterpret_cast<int4*>(smem + L::OFF_RSA);
+    int4* rs5 = reinterpret_cast<int4*>(smem + L::OFF_RS5);
+    int2* mm5 = reinterpret_cast<int2*>(smem + L::OFF_MM);
+    int* list = reinterpret_cast<int*>(smem + L::OFF_LIST);
+    int* cnt = reinterpret_cast<int*>(smem + L::OFF_CNT);
     const int lane = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * kTW + lane;
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kWTH;
     if (tid == 0) *cnt = 0;
-    stage_tile<IN, kWR, kWTH, kWNT>(tile, smem + kWOffRS9, &dmap, true, disp, dp, x0, y0, g, kStagePacked);
+    // the raw TMA box (and its mbarrier) lies where the full window's row sums go
+    stage_tile<IN, L::HR, kWTH, kWNT>(tile, smem + L::OFF_RSA, &dmap, true, disp, dp, x0, y0, g, kStagePacked);
 
     // ---- row pass: every staged row, the tile's columns; |u| <= 2 first
     // (with the smallest valid code minus 1, as unsigned, and the largest
-    // code), then |u| <= 4
+    // code), then |u| <= R
 #pragma unroll
-    for (int k = 0; k < kWRS / kWNT; k++) {
+    for (int k = 0; k < L::ROUNDS; k++) {
         const int e = tid + k * kWNT;
-        const int2* p = tile + (e / kTW) * kWTW + e % kTW + kWR;
-        int Q0 = 0, Q1 = 0, Q2 = 0, mx = 0;
+        if (L::RS % kWNT != 0 && e >= L::RS) break;
+        const int2* p = tile + (e / kTW) * L::TW + e % kTW + L::HR;
+        int Q0 = 0, Q1 = 0, Q2 = 0, B = 0, mx = 0;
         unsigned mn = 0xFFFFFFFFu;
 #pragma unroll
         for (int u = -2; u <= 2; u++) {
@@ -149,20 +163,24 @@ __global__ void __launch_bounds__(kWNT, 4)
             mn = min(mn, (unsigned)(t.x - 1));
             mx = max(mx, t.x);
         }
-        rs5[e] = unpack_row(Q0, Q1, Q2);
+        rs5[e] = unpack_row(Q0, Q1, Q2 >> 24);
         mm5[e] = make_int2((int)mn, mx);
+        if constexpr (!L::PACKED_UU) B = Q2 >> 24;
 #pragma unroll
-        for (int a = 3; a <= kWR; a++) {
+        for (int a = 3; a <= R; a++) {
 #pragma unroll
             for (int sgn = -1; sgn <= 1; sgn += 2) {
                 const int u = sgn * a;
                 const int E = p[u].y;
                 Q0 += E;
                 Q1 += u * E;
-                Q2 += (u * u) * E;
+                if constexpr (L::PACKED_UU)
+                    Q2 += (u * u) * E;
+                else
+                    B += (u * u) * (E >> 24);
             }
         }
-        rs9[e] = unpack_row(Q0, Q1, Q2);
+        rsa[e] = unpack_row(Q0, Q1, L::PACKED_UU ? Q2 >> 24 : B);
     }
     __syncthreads();
 
@@ -172,8 +190,8 @@ __global__ void __launch_bounds__(kWNT, 4)
 #pragma unroll
     for (int k = 0; k < 2; k++) {
         const int row = ty + 8 * k, x = x0 + lane, y = y0 + row;
-        const int e0 = (row + kWR) * kTW + lane;
-        const int Dc = tile[(row + kWR) * kWTW + lane + kWR].x;  // 0 outside the image
+        const int e0 = (row + L::HR) * kTW + lane;
+        const int Dc = tile[(row + L::HR) * L::TW + lane + L::HR].x;  // 0 outside the image
         const bool inside = x < g.W && y < g.H;
         need[k] = false;
         if (!inside) continue;
@@ -202,7 +220,7 @@ __global__ void __launch_bounds__(kWNT, 4)
         const WinSums w2 = column_sums<2>(rs5, e0);
         long long num, det;
         const bool fit = denoise_from_sums(w2, Dc, num, det);
-        window_affine(g, Dc, fit, num, det, column_sums<kWR>(rs9, e0), x, y, r);
+        window_affine<L::SOLVE32>(g, Dc, fit, num, det, column_sums<R>(rsa, e0), x, y, r);
         emit(g, o, x, y, r);
     }
 
@@ -220,36 +238,55 @@ __global__ void __launch_bounds__(kWNT, 4)
     for (int i = tid; i < nl; i += kWNT) {
         const int p = list[i];
         const int px = p % kTW, py = p / kTW;
-        const int2* c = tile + (py + kWR) * kWTW + px + kWR;
+        const int2* c = tile + (py + L::HR) * L::TW + px + L::HR;
         const int Dc = c[0].x;
         long long num, det;
-        const bool fit = denoise_exact<2>(c, kWTW, 2, Dc, g.K_range, num, det);
+        const bool fit = denoise_exact<2>(c, L::TW, 2, Dc, g.K_range, num, det);
         PixOut r;
-        window_affine(g, Dc, fit, num, det, column_sums<kWR>(rs9, (py + kWR) * kTW + px), x0 + px, y0 + py, r);
+        window_affine<L::SOLVE32>(g, Dc, fit, num, det, column_sums<R>(rsa, (py + L::HR) * kTW + px), x0 + px,
+                                  y0 + py, r);
         emit(g, o, x0 + px, y0 + py, r);
     }
 }
 
-template <int IN>
+template <int IN, int R>
 cudaError_t launch_window_in(const Geo& g, const void* disp, size_t dp, const FrameOut& o, cudaStream_t s) {
+    using L = Win<R>;
     CUtensorMap dmap{};
-    const cudaError_t me = encode_disp_map(&dmap, disp, dp, g.W, g.H, IN, tma_bw<IN, kWR, kWTW>(), kWTHR);
+    const cudaError_t me = encode_disp_map(&dmap, disp, dp, g.W, g.H, IN, tma_bw<IN, L::HR, L::TW>(), L::THR);
     if (me != cudaSuccess) return me;
     static std::atomic<unsigned long long> done{0};
-    const cudaError_t e = smem_limit_once(k_window<IN>, kWSmem, done);
+    const cudaError_t e = smem_limit_once(k_window<IN, R>, L::SMEM, done);
     if (e != cudaSuccess) return e;
     const dim3 grid((g.W + kTW - 1) / kTW, (g.H + kWTH - 1) / kWTH), block(kTW, 8);
-    k_window<IN><<<grid, block, kWSmem, s>>>(g, static_cast<const char*>(disp), dp, o, dmap);
+    k_window<IN, R><<<grid, block, L::SMEM, s>>>(g, static_cast<const char*>(disp), dp, o, dmap);
     return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t launch_window_r(const Geo& g, const void* disp, size_t dp, const FrameOut& o, cudaStream_t s) {
+    switch (g.in_dtype) {
+        case SN_IN_F32: return launch_window_in<SN_IN_F32, R>(g, disp, dp, o, s);
+        case SN_IN_F16: return launch_window_in<SN_IN_F16, R>(g, disp, dp, o, s);
+        default: return launch_window_in<SN_IN_U16X256, R>(g, disp, dp, o, s);
+    }
 }
 
 }  // namespace
 
+bool window_supported(const Geo& g) {
+    return g.support == SN_SUPPORT_FIXED && g.r_d == 2 && g.r_a >= 2 && g.r_a <= 7;
+}
+
 cudaError_t launch_window(const Geo& g, const void* disp, size_t dp, const FrameOut& o, cudaStream_t s) {
-    switch (g.in_dtype) {
-        case SN_IN_F32: return launch_window_in<SN_IN_F32>(g, disp, dp, o, s);
-        case SN_IN_F16: return launch_window_in<SN_IN_F16>(g, disp, dp, o, s);
-        default: return launch_window_in<SN_IN_U16X256>(g, disp, dp, o, s);
+    switch (g.r_a) {
+        case 2: return launch_window_r<2>(g, disp, dp, o, s);
+        case 3: return launch_window_r<3>(g, disp, dp, o, s);
+        case 4: return launch_window_r<4>(g, disp, dp, o, s);
+        case 5: return launch_window_r<5>(g, disp, dp, o, s);
+        case 6: return launch_window_r<6>(g, disp, dp, o, s);
+        case 7: return launch_window_r<7>(g, disp, dp, o, s);
+        default: return cudaErrorInvalidValue;
     }
 }
 

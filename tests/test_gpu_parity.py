@@ -142,6 +142,32 @@ def test_ragged_random(P, H, W, support):
     compare_frame(g, ref)
 
 
+@pytest.mark.parametrize("r", [2, 3, 5, 6, 7])
+def test_fixed_window_radii_full_size(P, r):
+    # every radius of the convolution-form window kernel (r_a 2..7 with the
+    # 5x5 denoise): FP32 input on the box-and-curve scene, 16-bit input on
+    # the driving scene
+    s = make_scene("mixed_1482x994", frame=2)
+    g, ref = chain(P, s.disp, s.camera, support=0, r_affine=r)
+    compare_frame(g, ref)
+    s = make_scene("driving_2048x1024", frame=5)
+    g16, ref16 = chain(P, s.disp_u16, s.camera, support=0, r_affine=r, in_dtype=P.sn.SN_IN_U16X256)
+    compare_frame(g16, ref16)
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (5, 7), (17, 33), (40, 65)])
+@pytest.mark.parametrize("r", [2, 7])
+def test_ragged_fixed_window_radii(P, H, W, r):
+    rng = np.random.default_rng(H * 977 + W + r)
+    base = rng.integers(4000, 4400, (H, W))
+    blocks = rng.integers(0, 3, (H // 3 + 1, W // 3 + 1)).repeat(3, 0).repeat(3, 1)[:H, :W]
+    D = (base * (1 + 0.25 * blocks)).astype(np.int32)
+    D[rng.random((H, W)) < 0.2] = 0
+    cam = Camera(300.0, 300.0, W / 2, H / 2, 0.1)
+    g, ref = chain(P, codes_to_f32(D), cam, support=0, r_affine=r)
+    compare_frame(g, ref)
+
+
 def _fallback_frame(rng, H=96, W=160):
     """Integer codes with the denoise fallback's windows placed on purpose:
     isolated pixels, one-row and one-column strips, diagonals (singular
@@ -240,8 +266,13 @@ def test_constant_and_planes(P):
     dict(support=2, dirs=16, steps=30, st_t=0.05),
     dict(support=2, dirs=5, steps=4, st_t=1.0),
     dict(support=0, r_affine=1),
+    dict(support=0, r_affine=2),
+    dict(support=0, r_affine=3),
+    dict(support=0, r_affine=5),
+    dict(support=0, r_affine=6),
     dict(support=0, r_affine=7),
     dict(support=0, r_affine=15),
+    dict(support=0, r_affine=7, r_denoise=3),
     dict(r_denoise=1, k_range=0.01),
     dict(r_denoise=4, k_range=0.2),
     dict(r_denoise=3, k_range=1.0, k_cd=1.0),
