@@ -583,20 +583,27 @@ def accuracy_frontier(scenes, args, dist, world, hbm_peak, plain_value, gt_plain
         f = time_form(scenes, args, params, lambda s: s.disp, FRAME_ALGO_BYTES, dist, world, hbm_peak)
         pts[name] = {"value": f["value"], "gt_error_deg": f["gt_error_deg"]["mean"],
                      "pixels": f["gt_error_deg"]["pixels"], "params": f["params"]}
-    out = {"plain": pts,
-           "rule": "a plain setting counts as at least as accurate when its mean error is no higher and it "
-                   "gives normals at no fewer than 99 % of the learned form's pixels (ST, which drops most "
-                   "pixels of the driving scene as edges, does not qualify)"}
+    out = {"plain": pts, "rule": FRONTIER_RULE}
     for lk in ("learned_f32", "learned_u16_snorm16"):
-        e, v = forms[lk]["gt_error_deg"]["mean"], forms[lk]["value"]
-        npx = forms[lk]["gt_error_deg"]["pixels"]
-        ok = {k: p for k, p in pts.items() if p["gt_error_deg"] <= e and p["pixels"] >= 0.99 * npx}
-        best = max(ok, key=lambda k: ok[k]["value"]) if ok else None
-        out[lk] = {"value": v, "gt_error_deg": e,
-                   "fastest_plain_as_accurate": best,
-                   "vs_that_plain": v / ok[best]["value"] if best else None,
-                   "vs_default_plain": v / plain_value}
+        f = forms[lk]
+        out[lk] = compare_at_equal_error(pts, f["value"], f["gt_error_deg"]["mean"], f["gt_error_deg"]["pixels"])
+        out[lk]["vs_default_plain"] = f["value"] / plain_value
     return out
+
+
+FRONTIER_RULE = ("a plain setting counts as at least as accurate when its mean error is no higher and it gives "
+                 "normals at no fewer than 99 % of the learned form's pixels (ST, which drops most pixels of the "
+                 "driving scene as edges, does not qualify)")
+
+
+def compare_at_equal_error(plain, value, err, pixels):
+    """The learned form (value MPix/s, mean error err over `pixels` normals)
+    against the fastest plain setting at least as accurate (FRONTIER_RULE):
+    {value, gt_error_deg, fastest_plain_as_accurate, vs_that_plain}."""
+    ok = {k: p for k, p in plain.items() if p["gt_error_deg"] <= err and p["pixels"] >= 0.99 * pixels}
+    best = max(ok, key=lambda k: ok[k]["value"]) if ok else None
+    return {"value": value, "gt_error_deg": err, "fastest_plain_as_accurate": best,
+            "vs_that_plain": value / ok[best]["value"] if best else None}
 
 
 def time_comparator(scenes, args, which, r, world):

@@ -72,3 +72,21 @@ def test_reference_arm_other_ranks_do_nothing(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     args = bench.argparse.Namespace(steps=1, warmup=0, gpus=2)
     assert bench.run_reference(args) is None        # returns at once: no oracle work
+
+
+def test_compare_at_equal_error_picks_fastest_as_accurate_plain():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    plain = {
+        "fast_but_worse": {"value": 30000.0, "gt_error_deg": 20.0, "pixels": 1000},
+        "accurate_slow": {"value": 2000.0, "gt_error_deg": 11.0, "pixels": 1000},
+        "accurate_fast": {"value": 8000.0, "gt_error_deg": 12.0, "pixels": 995},
+        "accurate_few_pixels": {"value": 50000.0, "gt_error_deg": 5.0, "pixels": 400},
+    }
+    r = bench.compare_at_equal_error(plain, 12000.0, 13.0, 1000)
+    # the cheaper-but-worse setting and the one that drops most pixels do not count
+    assert r["fastest_plain_as_accurate"] == "accurate_fast"
+    assert r["vs_that_plain"] == pytest.approx(1.5)
+    none = bench.compare_at_equal_error(plain, 12000.0, 1.0, 1000)
+    assert none["fastest_plain_as_accurate"] is None and none["vs_that_plain"] is None
