@@ -382,6 +382,10 @@ def run_ours(args):
     stage_calls = time_stage_calls(scenes, args) if world == 1 and not args.only_headline else None
     # every method's ground-truth error on the box-and-curve scene (1482x994)
     errors_mixed = scene_errors("mixed_1482x994") if world == 1 and not args.only_headline else None
+    # the same frontier on the box-and-curve scene (the paper's box scenes),
+    # where depth edges rather than far-range noise decide the error
+    frontier_mixed = (scene_frontier("mixed_1482x994", args, hbm_peak)
+                      if world == 1 and not args.only_headline else None)
     # mixed-resolution batch of 64 frames, one graph launch per step
     mixed = run_mixed_batch(args) if world == 1 and not args.no_mixed else None
 
@@ -442,6 +446,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "forms": forms,
             "accuracy_frontier": frontier,
+            "accuracy_frontier_mixed_1482x994": frontier_mixed,
             "comparators": comparators,
             "stage_calls": stage_calls,
             "gt_error_by_method_mixed_1482x994": errors_mixed,
@@ -594,6 +599,28 @@ def accuracy_frontier(scenes, args, dist, world, hbm_peak, plain_value, gt_plain
 FRONTIER_RULE = ("a plain setting counts as at least as accurate when its mean error is no higher and it gives "
                  "normals at no fewer than 99 % of the learned form's pixels (ST, which drops most pixels of the "
                  "driving scene as edges, does not qualify)")
+
+
+def scene_frontier(scene_name, args, hbm_peak, n_distinct=4):
+    """accuracy_frontier on another scene: every plain setting (the default
+    CD s10 d8, CD s30 d16, ST s10 d8, fixed 9x9 and FRONTIER) and the learned
+    form timed on n_distinct seeded frames of it, errors against its ground
+    truth, and the learned form against the fastest plain setting as accurate."""
+    from scenes import make_scene
+    scenes = [make_scene(scene_name, frame=300 + i) for i in range(n_distinct)]
+    settings = {"cd_s10_d8": {}, "cd_s30_d16": dict(dirs=16, steps=30), "st_s10_d8": dict(support=2, st_t=0.1),
+                "fixed_9x9": dict(support=0, r_affine=4), **FRONTIER}
+    pts = {}
+    for name, params in settings.items():
+        f = time_form(scenes, args, params, lambda s: s.disp, FRAME_ALGO_BYTES, None, 1, hbm_peak)
+        pts[name] = {"value": f["value"], "gt_error_deg": f["gt_error_deg"]["mean"],
+                     "pixels": f["gt_error_deg"]["pixels"]}
+    lf = time_form(scenes, args, dict(learned=1), lambda s: s.disp, FRAME_ALGO_BYTES, None, 1, hbm_peak)
+    out = {"scene": scene_name, "frames": n_distinct, "plain": pts, "rule": FRONTIER_RULE,
+           "learned_f32": compare_at_equal_error(pts, lf["value"], lf["gt_error_deg"]["mean"],
+                                                 lf["gt_error_deg"]["pixels"])}
+    out["learned_f32"]["vs_default_plain"] = lf["value"] / pts["cd_s10_d8"]["value"]
+    return out
 
 
 def compare_at_equal_error(plain, value, err, pixels):
