@@ -168,6 +168,38 @@ def test_ragged_fixed_window_radii(P, H, W, r):
     compare_frame(g, ref)
 
 
+def _extreme_codes(kind, H=72, W=100):
+    """Integer codes at the ends of the 17-bit range: 'high' is a tilted
+    plane of codes within 200 of the largest (131071) with 5 % invalid
+    pixels (window sums at their largest); 'mixed' puts codes 1..4 beside
+    codes near the largest in random blocks (the widest spreads)."""
+    rng = np.random.default_rng(7 if kind == "high" else 11)
+    u = np.arange(W)[None, :]
+    v = np.arange(H)[:, None]
+    if kind == "high":
+        D = 131071 - ((u + 2 * v) % 200)
+    else:
+        blocks = rng.integers(0, 2, (H // 4 + 1, W // 4 + 1)).repeat(4, 0).repeat(4, 1)[:H, :W]
+        D = np.where(blocks > 0, 131071 - rng.integers(0, 64, (H, W)), rng.integers(1, 5, (H, W)))
+    D = D.astype(np.int32)
+    D[rng.random((H, W)) < 0.05] = 0
+    return D
+
+
+@pytest.mark.parametrize("kind", ["high", "mixed"])
+@pytest.mark.parametrize("params", [dict(support=1), dict(support=2), dict(support=0, r_affine=2),
+                                    dict(support=0, r_affine=4), dict(support=0, r_affine=5),
+                                    dict(support=0, r_affine=6), dict(support=0, r_affine=7)])
+def test_extreme_codes(P, kind, params):
+    # the packed window sums and the star walk's integer sums at the largest
+    # codes, and the covered-depth and range gates across the widest spreads
+    D = _extreme_codes(kind)
+    H, W = D.shape
+    cam = Camera(500.0, 500.0, W / 2, H / 2, 0.12)
+    g, ref = chain(P, codes_to_f32(D), cam, **params)
+    compare_frame(g, ref)
+
+
 def _fallback_frame(rng, H=96, W=160):
     """Integer codes with the denoise fallback's windows placed on purpose:
     isolated pixels, one-row and one-column strips, diagonals (singular
