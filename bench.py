@@ -580,20 +580,27 @@ def accuracy_frontier(scenes, args, dist, world, hbm_peak, plain_value, gt_plain
     (CD s10 d8) and the forms already timed (CD s30 d16, fixed 9x9), and the
     learned forms' throughput against the fastest plain setting whose error
     is no worse than theirs (the comparison at equal angular error)."""
-    pts = {"cd_s10_d8": {"value": plain_value, "gt_error_deg": gt_plain["mean"], "pixels": gt_plain["pixels"]}}
+    pts = {"cd_s10_d8": frontier_point(plain_value, gt_plain)}
     for k in ("cd_s30_d16_f32", "fixed_9x9_f32", "st_s10_d8_f32"):
-        pts[k[:-4]] = {"value": forms[k]["value"], "gt_error_deg": forms[k]["gt_error_deg"]["mean"],
-                       "pixels": forms[k]["gt_error_deg"]["pixels"]}
+        pts[k[:-4]] = frontier_point(forms[k]["value"], forms[k]["gt_error_deg"])
     for name, params in FRONTIER.items():
         f = time_form(scenes, args, params, lambda s: s.disp, FRAME_ALGO_BYTES, dist, world, hbm_peak)
-        pts[name] = {"value": f["value"], "gt_error_deg": f["gt_error_deg"]["mean"],
-                     "pixels": f["gt_error_deg"]["pixels"], "params": f["params"]}
+        pts[name] = frontier_point(f["value"], f["gt_error_deg"])
     out = {"plain": pts, "rule": FRONTIER_RULE}
     for lk in ("learned_f32", "learned_u16_snorm16"):
         f = forms[lk]
         out[lk] = compare_at_equal_error(pts, f["value"], f["gt_error_deg"]["mean"], f["gt_error_deg"]["pixels"])
         out[lk]["vs_default_plain"] = f["value"] / plain_value
+        out[lk]["edge_band_error_deg"] = frontier_point(f["value"], f["gt_error_deg"])["edge_band_error_deg"]
     return out
+
+
+def frontier_point(value, gt):
+    """One setting on the frontier: MPix/s, mean error, normals counted, and
+    the mean error near surface edges and elsewhere."""
+    return {"value": value, "gt_error_deg": gt["mean"], "pixels": gt["pixels"],
+            "edge_band_error_deg": gt.get(f"mean_within_{EDGE_BAND}px_of_a_surface_edge"),
+            "elsewhere_error_deg": gt.get("mean_elsewhere")}
 
 
 FRONTIER_RULE = ("a plain setting counts as at least as accurate when its mean error is no higher and it gives "
@@ -613,12 +620,12 @@ def scene_frontier(scene_name, args, hbm_peak, n_distinct=4):
     pts = {}
     for name, params in settings.items():
         f = time_form(scenes, args, params, lambda s: s.disp, FRAME_ALGO_BYTES, None, 1, hbm_peak)
-        pts[name] = {"value": f["value"], "gt_error_deg": f["gt_error_deg"]["mean"],
-                     "pixels": f["gt_error_deg"]["pixels"]}
+        pts[name] = frontier_point(f["value"], f["gt_error_deg"])
     lf = time_form(scenes, args, dict(learned=1), lambda s: s.disp, FRAME_ALGO_BYTES, None, 1, hbm_peak)
     out = {"scene": scene_name, "frames": n_distinct, "plain": pts, "rule": FRONTIER_RULE,
            "learned_f32": compare_at_equal_error(pts, lf["value"], lf["gt_error_deg"]["mean"],
                                                  lf["gt_error_deg"]["pixels"])}
+    out["learned_f32"]["edge_band_error_deg"] = frontier_point(lf["value"], lf["gt_error_deg"])["edge_band_error_deg"]
     out["learned_f32"]["vs_default_plain"] = lf["value"] / pts["cd_s10_d8"]["value"]
     return out
 
@@ -884,7 +891,7 @@ def gt_error_deg(outs, scenes):
     frame of each distinct scene (read back after the timed region), and the
     fraction of valid pixels the learned gate certified."""
     import torch
-    errs, cert = [], []
+    errs, cert, near = [], [], []
     for s, out in zip(scenes, outs):
         m = out.mask.cpu().numpy()
         if out.normals.dtype == torch.int16:
@@ -895,10 +902,36 @@ def gt_error_deg(outs, scenes):
         a, b = n[ok], s.gt_normal[ok].astype(np.float64)
         ang = np.degrees(np.arctan2(np.linalg.norm(np.cross(a, b), axis=-1), (a * b).sum(-1)))
         errs.append(ang)
+        near.append(near_edge(s.prim, EDGE_BAND)[ok])
         cert.append(((m & 8) > 0).sum() / max(((m & 1) > 0).sum(), 1))
-    e = np.concatenate(errs)
+    e, ne = np.concatenate(errs), np.concatenate(near)
     return {"mean": float(e.mean()), "median": float(np.median(e)), "pixels": int(e.size),
+            f"mean_within_{EDGE_BAND}px_of_a_surface_edge": float(e[ne].mean()) if ne.any() else None,
+            "mean_elsewhere": float(e[~ne].mean()) if (~ne).any() else None,
+            "edge_band_pixels": int(ne.sum()),
             "certified": float(np.mean(cert)), "scenes": len(errs)}
+
+
+EDGE_BAND = 7  # the widest fixed window's radius
+
+
+def near_edge(prim, r):
+    """Pixels within r (Chebyshev distance) of a change of the generator's
+    primitive id (a surface edge, including the edge to the background)."""
+    e = np.zeros(prim.shape, bool)
+    e[:, 1:] |= prim[:, 1:] != prim[:, :-1]
+    e[:, :-1] |= prim[:, 1:] != prim[:, :-1]
+    e[1:, :] |= prim[1:, :] != prim[:-1, :]
+    e[:-1, :] |= prim[1:, :] != prim[:-1, :]
+    for axis in (0, 1):  # dilation by a (2r + 1)-wide box, one axis at a time
+        d = e.copy()
+        for k in range(1, r + 1):
+            d[tuple(slice(k, None) if a == axis else slice(None) for a in range(2))] |= \
+                e[tuple(slice(None, -k) if a == axis else slice(None) for a in range(2))]
+            d[tuple(slice(None, -k) if a == axis else slice(None) for a in range(2))] |= \
+                e[tuple(slice(k, None) if a == axis else slice(None) for a in range(2))]
+        e = d
+    return e
 
 
 SERVING_CAMERAS = [("planes_640x480", 120.0)] * 2 + [("mixed_1482x994", 30.0)] * 4 + \

@@ -90,3 +90,16 @@ def test_compare_at_equal_error_picks_fastest_as_accurate_plain():
     assert r["vs_that_plain"] == pytest.approx(1.5)
     none = bench.compare_at_equal_error(plain, 12000.0, 1.0, 1000)
     assert none["fastest_plain_as_accurate"] is None and none["vs_that_plain"] is None
+
+
+def test_near_edge_band():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    prim = np.zeros((20, 30), np.int32)
+    prim[:, 12:] = 1                       # one vertical edge between columns 11 and 12
+    prim[15:, :] = 2                       # one horizontal edge between rows 14 and 15
+    e = bench.near_edge(prim, 3)
+    assert np.array_equal(np.where(e[0])[0], np.arange(8, 16))        # columns 11, 12 +- 3
+    assert np.array_equal(np.where(e[:, 0])[0], np.arange(11, 19))    # rows 14, 15 +- 3
+    assert not e[5, 0] and not e[5, 29]
