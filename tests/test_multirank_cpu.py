@@ -90,6 +90,14 @@ def test_compare_at_equal_error_picks_fastest_as_accurate_plain():
     assert r["vs_that_plain"] == pytest.approx(1.5)
     none = bench.compare_at_equal_error(plain, 12000.0, 1.0, 1000)
     assert none["fastest_plain_as_accurate"] is None and none["vs_that_plain"] is None
+    # also near edges: only settings no worse there either
+    for k, e in (("fast_but_worse", 30.0), ("accurate_slow", 9.0), ("accurate_fast", 25.0),
+                 ("accurate_few_pixels", 1.0)):
+        plain[k]["edge_band_error_deg"] = e
+    r = bench.compare_at_equal_error(plain, 12000.0, 13.0, 1000, edge_err=10.0)
+    assert r["fastest_plain_as_accurate"] == "accurate_fast"
+    assert r["fastest_plain_as_accurate_also_near_edges"] == "accurate_slow"
+    assert r["vs_that_plain_also_near_edges"] == pytest.approx(6.0)
 
 
 def test_near_edge_band():
