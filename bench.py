@@ -592,6 +592,7 @@ def accuracy_frontier(scenes, args, dist, world, hbm_peak, plain_value, gt_plain
         f = forms[lk]
         fp = frontier_point(f["value"], f["gt_error_deg"])
         out[lk] = compare_at_equal_error(pts, fp["value"], fp["gt_error_deg"], fp["pixels"], fp["edge_band_error_deg"])
+        out[lk]["elsewhere_error_deg"] = fp["elsewhere_error_deg"]
         out[lk]["vs_default_plain"] = f["value"] / plain_value
     return out
 
@@ -628,6 +629,7 @@ def scene_frontier(scene_name, args, hbm_peak, n_distinct=4):
     out = {"scene": scene_name, "frames": n_distinct, "plain": pts, "rule": FRONTIER_RULE,
            "learned_f32": compare_at_equal_error(pts, fp["value"], fp["gt_error_deg"], fp["pixels"],
                                                  fp["edge_band_error_deg"])}
+    out["learned_f32"]["elsewhere_error_deg"] = fp["elsewhere_error_deg"]
     out["learned_f32"]["vs_default_plain"] = lf["value"] / pts["cd_s10_d8"]["value"]
     return out
 

@@ -41,8 +41,12 @@
  *   R11 normal valid iff centre valid, >= 3 support pixels, det > 0;
  *       FP64 flag iff 1024 det < alpha gamma.
  *
- * Parity unpinned: the denoised value on degenerate (rank < 3) windows falls
- * back to the raw centre value; no passage of the paper fixes it.
+ * The denoised value on degenerate (rank < 3) windows, or where the fitted
+ * intercept is not positive, falls back to the raw centre value: no passage
+ * of the paper fixes it, so it is this oracle's reading; the CPU tests pin
+ * it with hand-built singular windows (isolated pixel, one row, one column,
+ * a diagonal) and a determined fit whose least-squares intercept is
+ * negative, each checked against numpy's rank and lstsq.
  */
 #include <math.h>
 #include <omp.h>
