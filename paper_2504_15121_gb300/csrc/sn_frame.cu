@@ -39,10 +39,11 @@ __host__ __device__ constexpr int tma_raw_bytes() {
     return tma_bw<IN, R, kTW + 2 * R>() * (frame_th(VAR) + 2 * R) * tma_esize<IN>();
 }
 
-// VAR: 0 fixed window, 1 star table, 2 compile-time M = 8, s = 10 star,
-// 4 star table with the ST stop, 5 = 2 with the ST stop instead of the
-// covered-depth test (the learned form has its own kernel, k_learned).  R: halo
-// radius at compile time (0 = runtime).
+// VAR: 0 fixed window of a runtime radius (radii 2..7 with the 5x5 denoise
+// have their own kernel, k_window), 1 star table, 2 compile-time M = 8,
+// s = 10 star, 4 star table with the ST stop, 5 = 2 with the ST stop instead
+// of the covered-depth test (the learned form has its own kernels, k_gate and
+// k_learned).  R: halo radius at compile time (0 = runtime).
 // RD: denoise radius (0 = runtime).
 template <int IN, int VAR, int R, int RD>
 __global__ void __launch_bounds__(kTW* frame_th(VAR), 1024 / (kTW * frame_th(VAR)))

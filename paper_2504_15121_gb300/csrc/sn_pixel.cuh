@@ -22,9 +22,9 @@ constexpr int kTW = kFrameTW, kTH = kFrameTH, kThreads = kTW * kTH;
 // Tile height of each variant.  The compile-time M = 8, s = 10 star takes
 // 32 x 8 tiles, 4 CTAs of 256 threads per SM (more independent CTAs hide the
 // barrier and staging stalls better than 2 CTAs of 512: 130 vs 139 us per
-// 2048x1024 frame); the variants with larger halos (star tables up to s = 30,
-// ST) and the learned one (whose network halo is amortised over more pixels)
-// keep 32 x 16.
+// 2048x1024 frame); the variants with larger halos (star tables up to
+// s = 30, the table-driven ST, fixed windows of a runtime radius) keep
+// 32 x 16.
 __host__ __device__ constexpr int frame_th(int var) { return var == 2 || var == 5 ? 8 : kTH; }
 
 // distinct pixels of an M = 8 diagonal ray of s steps: round(s / sqrt 2),
@@ -249,27 +249,14 @@ __device__ __forceinline__ void star_table_st(const int2* c, const uint8_t* ec, 
     }
 }
 
-// Fixed (2R + 1)^2 window on the packed tile; RA > 0 fixes the radius (and
-// the row stride STRIDE) at compile time, so the window unrolls.
-template <int RA = 0, int STRIDE = 0>
+// Fixed (2R + 1)^2 window on the packed tile, sample by sample.
 __device__ __forceinline__ void fixed_packed(const int2* c, int stride, int R, int Dc, AffSums& s) {
     aff_zero(s);
-    if constexpr (RA > 0) {
-#pragma unroll
-        for (int ov = -RA; ov <= RA; ov++) {
-#pragma unroll
-            for (int ou = -RA; ou <= RA; ou++) {
-                const int Di = c[ov * STRIDE + ou].x;
-                if (Di > 0 && (ou | ov) != 0) aff_add(s, ou, ov, Di - Dc);
-            }
-        }
-    } else {
-        for (int ov = -R; ov <= R; ov++) {
-            const int2* row = c + ov * stride;
-            for (int ou = -R; ou <= R; ou++) {
-                const int Di = row[ou].x;
-                if (Di > 0 && (ou | ov) != 0) aff_add(s, ou, ov, Di - Dc);
-            }
+    for (int ov = -R; ov <= R; ov++) {
+        const int2* row = c + ov * stride;
+        for (int ou = -R; ou <= R; ou++) {
+            const int Di = row[ou].x;
+            if (Di > 0 && (ou | ov) != 0) aff_add(s, ou, ov, Di - Dc);
         }
     }
 }
@@ -446,13 +433,13 @@ __device__ __forceinline__ void plain_pixel(const Geo& g, const StarTable* T, co
         star8<10, kTW + 2 * R>(c, Dc, __int_as_float(cc.y), make_thr(g, Dc), s);
     } else if constexpr (VAR == 1) {
         star_table(c, TWR, Dc, __int_as_float(cc.y), make_thr(g, Dc), *T, g.dirs, g.steps, g.star_pm, s);
-    } else if constexpr (R > 0) {
-        fixed_packed<R, kTW + 2 * R>(c, TWR, R, Dc, s);  // compile-time 9x9 (R = r_a = 4 >= r_d)
     } else {
+        // fixed windows of a runtime radius (radii 2..7 with the 5x5 denoise
+        // take the convolution-form kernel instead)
         fixed_packed(c, TWR, g.r_a, Dc, s);
     }
     bool fp64;
-    if (solve_normal_dc<VAR == 2 || VAR == 3 || VAR == 5>(
+    if (solve_normal_dc<VAR == 2 || VAR == 5>(
             s, Dc, dcf, [=] { return fit ? (double)num / (double)det : 0.0; }, r.dtil, x, y, g, r.n, fp64))
         r.m |= SN_MASK_NORMAL | (fp64 ? SN_MASK_FP64 : 0);
     pix_points(g, x, y, r);
