@@ -58,6 +58,11 @@ sn_status sn_gate_trainer_state(sn_gate_trainer *t, float *theta, float *m, floa
 sn_status sn_gate_trainer_resume(sn_gate_trainer *t, const float *theta, const float *m, const float *v,
                                  long long step);
 
+/* Waits for `stream`, then reads and clears the trainer's device error word:
+ * SN_ETIMEOUT if a bounded wait of a tensor-core GEMM gave up since the last
+ * check (the gradients and steps of those calls are undefined), else SN_OK. */
+sn_status sn_gate_trainer_check_device(sn_gate_trainer *t, sn_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -347,25 +347,6 @@ __device__ __forceinline__ short snorm16(float v) {
     return (short)__float2int_rn(32767.0f * fminf(fmaxf(v, -1.0f), 1.0f));
 }
 
-// ---------------------------------------------------------------- tensor cores
-// ldmatrix x4: four 8x8 b16 matrices; lane l gives the address of row l % 8
-// of matrix l / 8 (16-byte aligned rows in shared memory).
-__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void* p) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(a));
-}
-
-// D (16x8, fp32) += A (16x16, bf16, row) x B (16x8, bf16, col)
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 // ---------------------------------------------------------------- learned gate
 // Gate features of one pixel from the log2 of its own and its right / lower
 // neighbours' codes, read from `tab` (FP32 log2 of every code, NaN for code

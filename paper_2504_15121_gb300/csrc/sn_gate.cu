@@ -7,8 +7,8 @@
 // convolution 8 -> 16 with ReLU, a 3x3 convolution 16 -> 16 with ReLU, a
 // 1x1 layer 16 -> 1 and a sigmoid.  Training works on 6x6 patches of
 // integer disparity codes (centre at [2][2]).  Every contraction is a BF16
-// tensor-core GEMM with FP32 accumulation (mma.sync m16n8k16); the master
-// weights and the optimiser state are FP32.
+// tcgen05 GEMM with FP32 accumulation in tensor memory; the master weights
+// and the optimiser state are FP32.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -17,66 +17,134 @@
 
 #include "sn_device.cuh"
 #include "sn_gate_internal.h"
+#include "sn_umma.cuh"
 
 namespace sn {
 
 // ------------------------------------------------------------------ GEMM
-// C[M][N] (fp32, ldc) = sum_k A(m, k) B(k, n); A(m, k) = A[m sam + k sak],
-// B(k, n) = B[k sbk + n sbn] (bf16 element strides).  Block tile 64 x 16,
-// 4 warps, each warp 16 rows x 16 columns (two m16n8k16 products per k-step).
+// C (FP32; element (m, n) at C[m scm + n scn]) = sum_k A(m, k) B(k, n), with
+// A(m, k) = A[m sam + k sak] and B(k, n) = B[k sbk + n sbn] (BF16, element
+// strides).  One CTA of 128 threads per 128 x 16 tile of C.  Per K-step of
+// 16 the threads gather the A tile (128 x 16) and the B tile (16 x 16) into
+// shared memory in the tensor core's K-major layout (core matrices of 8 rows
+// x 16 bytes; the two K halves kTM or kTN rows apart), one thread issues a
+// tcgen05.mma (M = 128, N = 16, K = 16, accumulator in 32 TMEM columns) and
+// commits it to an mbarrier, and one thread waits for it (bounded) before
+// the next step overwrites the tiles.  The accumulator comes back by
+// tcgen05.ld: warp w holds rows 32 w .. 32 w + 31.
 namespace {
 
-constexpr int kGM = 64, kGN = 16, kGK = 16, kLd = 24;  // smem row stride (bf16), conflict-free ldmatrix
+constexpr int kTM = 128, kTN = 16;
+constexpr uint32_t kGemmIdesc = umma::idesc_bf16<kTM, kTN>();
+
+__device__ __forceinline__ uint4 pack8(const unsigned short (&v)[16], int h) {
+    return make_uint4(v[8 * h] | ((unsigned)v[8 * h + 1] << 16), v[8 * h + 2] | ((unsigned)v[8 * h + 3] << 16),
+                      v[8 * h + 4] | ((unsigned)v[8 * h + 5] << 16), v[8 * h + 6] | ((unsigned)v[8 * h + 7] << 16));
+}
 
 __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const __nv_bfloat16* __restrict__ A, long long sam,
                                               long long sak, const __nv_bfloat16* __restrict__ B, long long sbk,
-                                              long long sbn, float* __restrict__ C, long long ldc) {
-    __shared__ __align__(16) __nv_bfloat16 As[kGM][kLd];
-    __shared__ __align__(16) __nv_bfloat16 Bs[kGN][kLd];  // [n][k]
-    const int m0 = blockIdx.x * kGM, n0 = blockIdx.y * kGN;
+                                              long long sbn, float* __restrict__ C, long long scm, long long scn,
+                                              int* err) {
+    __shared__ __align__(128) uint4 As[2 * kTM];  // [k half][row]: 8 BF16 each
+    __shared__ __align__(128) uint4 Bs[2 * kTN];  // [k half][n]
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    float acc0[4] = {0, 0, 0, 0}, acc1[4] = {0, 0, 0, 0};
-    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-    for (int k0 = 0; k0 < K; k0 += kGK) {
-        for (int i = tid; i < kGM * kGK; i += 128) {
-            const int r = i / kGK, k = i % kGK;
-            const int m = m0 + r, kk = k0 + k;
-            As[r][k] = (m < M && kk < K) ? A[(long long)m * sam + (long long)kk * sak] : zero;
+    const int m0 = blockIdx.x * kTM, n0 = blockIdx.y * kTN;
+    const unsigned short* Au = reinterpret_cast<const unsigned short*>(A);
+    const unsigned short* Bu = reinterpret_cast<const unsigned short*>(B);
+    if (warp == 0) umma::tmem_alloc(&tslot, 32);
+    if (tid == 0) umma::mbar_init(&bar, 1);
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
+    const uint32_t tmem = tslot;
+    bool ok = true;
+    int steps = 0;
+    for (int k0 = 0; k0 < K; k0 += 16, steps++) {
+        unsigned short v[16];
+        const int m = m0 + tid;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const int kk = k0 + k;
+            v[k] = (m < M && kk < K) ? Au[(long long)m * sam + (long long)kk * sak] : (unsigned short)0;
         }
-        for (int i = tid; i < kGN * kGK; i += 128) {
-            const int c = i / kGK, k = i % kGK;
-            const int n = n0 + c, kk = k0 + k;
-            Bs[c][k] = (n < N && kk < K) ? B[(long long)kk * sbk + (long long)n * sbn] : zero;
+        As[tid] = pack8(v, 0);
+        As[kTM + tid] = pack8(v, 1);
+        if (tid < kTN) {
+            const int n = n0 + tid;
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                const int kk = k0 + k;
+                v[k] = (n < N && kk < K) ? Bu[(long long)kk * sbk + (long long)n * sbn] : (unsigned short)0;
+            }
+            Bs[tid] = pack8(v, 0);
+            Bs[kTN + tid] = pack8(v, 1);
         }
+        umma::fence_proxy_async();  // the tiles, written by the generic proxy, are read by the tensor core
+        umma::fence_before();
         __syncthreads();
-        unsigned a[4], b[4];
-        ldsm_x4(a, &As[warp * 16 + (lane & 15)][(lane >> 4) * 8]);
-        ldsm_x4(b, &Bs[(lane & 7) + ((lane >> 4) << 3)][((lane >> 3) & 1) * 8]);
-        mma_bf16(acc0, a, b[0], b[1]);
-        mma_bf16(acc1, a, b[2], b[3]);
-        __syncthreads();
+        umma::fence_after();
+        if (tid == 0) {
+            const uint64_t ad = umma::desc(umma::smem_addr(As), kTM * 16, 128);
+            const uint64_t bd = umma::desc(umma::smem_addr(Bs), kTN * 16, 128);
+            umma::mma<kGemmIdesc>(tmem, ad, bd, k0 > 0);
+            umma::commit(&bar);
+            ok = umma::mbar_wait_ns(&bar, steps & 1, umma::kWaitNs);
+            if (!ok) {
+                // gave up: report, and drain the MMA before the tiles or the
+                // TMEM are given back
+                atomicOr(err, 1);
+                umma::mbar_wait_ns(&bar, steps & 1, umma::kDrainNs);
+            }
+        }
+        ok = __syncthreads_and(ok);
+        umma::fence_after();
+        if (!ok) break;
     }
-    const int g = lane >> 2, t = lane & 3;
-    const int r0 = m0 + warp * 16 + g;
-    for (int h = 0; h < 2; h++) {
-        const int r = r0 + 8 * h;
-        if (r >= M) continue;
-        const int c0 = n0 + 2 * t, c1 = n0 + 8 + 2 * t;
-        if (c0 < N) C[(long long)r * ldc + c0] = acc0[2 * h];
-        if (c0 + 1 < N) C[(long long)r * ldc + c0 + 1] = acc0[2 * h + 1];
-        if (c1 < N) C[(long long)r * ldc + c1] = acc1[2 * h];
-        if (c1 + 1 < N) C[(long long)r * ldc + c1 + 1] = acc1[2 * h + 1];
+    if (ok) {
+        float c[16];
+        if (K > 0) {
+            uint32_t r[16];
+            umma::ld16(tmem + ((uint32_t)(warp * 32) << 16), r);
+            umma::wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; j++) c[j] = __uint_as_float(r[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; j++) c[j] = 0.0f;
+        }
+        const int m = m0 + warp * 32 + lane;
+        if (m < M) {
+#pragma unroll
+            for (int j = 0; j < 16; j++)
+                if (n0 + j < N) C[(long long)m * scm + (long long)(n0 + j) * scn] = c[j];
+        }
+    }
+    umma::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        umma::fence_after();
+        umma::tmem_dealloc(tmem, 32);
     }
 }
 
 }  // namespace
 
 cudaError_t gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, long long sam, long long sak,
-                      const __nv_bfloat16* B, long long sbk, long long sbn, float* C, long long ldc,
+                      const __nv_bfloat16* B, long long sbk, long long sbn, float* C, long long ldc, int* err,
                       cudaStream_t s) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    const dim3 grid((M + kGM - 1) / kGM, (N + kGN - 1) / kGN);
-    k_gemm<<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc);
+    // the tensor core's M is 128: a narrow product (M < 64) is computed as
+    // its transpose, C^T = B^T A^T
+    if (M < 64 && N > M) {
+        const dim3 grid((N + kTM - 1) / kTM, (M + kTN - 1) / kTN);
+        k_gemm<<<grid, 128, 0, s>>>(N, M, K, B, sbn, sbk, A, sak, sam, C, 1, ldc, err);
+    } else {
+        const dim3 grid((M + kTM - 1) / kTM, (N + kTN - 1) / kTN);
+        k_gemm<<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, 1, err);
+    }
     return cudaGetLastError();
 }
 
@@ -247,6 +315,7 @@ struct sn_gate_trainer {
     __nv_bfloat16 *F = nullptr, *A1 = nullptr, *A2 = nullptr, *dZ = nullptr, *dH1 = nullptr;
     float *C1 = nullptr, *C2 = nullptr, *dA2 = nullptr, *dW1g = nullptr, *dW2g = nullptr;
     const float* log2tab = nullptr;  // FP32 log2 of every code (the library's table)
+    int* err = nullptr;              // device error word: a GEMM's bounded MMA wait gave up
 };
 
 namespace {
@@ -260,10 +329,10 @@ cudaError_t gate_pass(sn_gate_trainer* t, const int* Dp, const float* y, int B, 
     k_features<<<blocks((long long)B * 25), 256, 0, s>>>(B, Dp, t->log2tab, t->F);
     k_im2col1<<<blocks((long long)B * 9 * 80), 256, 0, s>>>(B, t->F, t->A1);
     // C1 [B*9][16] = A1 [B*9][80] x W1g^T
-    if ((e = gemm_bf16(B * 9, 16, 80, t->A1, 80, 1, t->w.W1g, 1, 80, t->C1, 16, s)) != cudaSuccess) return e;
+    if ((e = gemm_bf16(B * 9, 16, 80, t->A1, 80, 1, t->w.W1g, 1, 80, t->C1, 16, t->err, s)) != cudaSuccess) return e;
     k_act1<<<blocks((long long)B * 144), 256, 0, s>>>((long long)B * 144, t->C1, t->w.b1, t->A2);
     // C2 [B][16] = A2 [B][144] x W2g^T
-    if ((e = gemm_bf16(B, 16, 144, t->A2, 144, 1, t->w.W2g, 1, 144, t->C2, 16, s)) != cudaSuccess) return e;
+    if ((e = gemm_bf16(B, 16, 144, t->A2, 144, 1, t->w.W2g, 1, 144, t->C2, 16, t->err, s)) != cudaSuccess) return e;
     if (y) {
         cudaMemsetAsync(t->grad, 0, sizeof(float) * kGateParams, s);
         cudaMemsetAsync(t->loss, 0, sizeof(float), s);
@@ -272,13 +341,13 @@ cudaError_t gate_pass(sn_gate_trainer* t, const int* Dp, const float* y, int B, 
                                          t->grad + kOffW3, t->grad + kOffB2, t->grad + kOffB3, t->loss);
     if (!y) return cudaGetLastError();
     // dW2g [16][144] = dZ^T [16][B] x A2 [B][144]
-    if ((e = gemm_bf16(16, 144, B, t->dZ, 1, 16, t->A2, 144, 1, t->dW2g, 144, s)) != cudaSuccess) return e;
+    if ((e = gemm_bf16(16, 144, B, t->dZ, 1, 16, t->A2, 144, 1, t->dW2g, 144, t->err, s)) != cudaSuccess) return e;
     // dA2 [B][144] = dZ [B][16] x W2g [16][144]
-    if ((e = gemm_bf16(B, 144, 16, t->dZ, 16, 1, t->w.W2g, 144, 1, t->dA2, 144, s)) != cudaSuccess) return e;
+    if ((e = gemm_bf16(B, 144, 16, t->dZ, 16, 1, t->w.W2g, 144, 1, t->dA2, 144, t->err, s)) != cudaSuccess) return e;
     k_act1_bwd<<<blocks((long long)B * 144), 256, 0, s>>>((long long)B * 144, t->dA2, t->C1, t->w.b1, t->dH1,
                                                           t->grad + kOffB1);
     // dW1g [16][80] = dH1^T [16][B*9] x A1 [B*9][80]
-    if ((e = gemm_bf16(16, 80, B * 9, t->dH1, 1, 16, t->A1, 80, 1, t->dW1g, 80, s)) != cudaSuccess) return e;
+    if ((e = gemm_bf16(16, 80, B * 9, t->dH1, 1, 16, t->A1, 80, 1, t->dW1g, 80, t->err, s)) != cudaSuccess) return e;
     k_pack_grad<<<blocks(kW1N + kW2N), 256, 0, s>>>(t->dW1g, t->dW2g, t->grad);
     return cudaGetLastError();
 }
@@ -309,6 +378,8 @@ sn_status sn_gate_trainer_create(int max_batch, const float* theta0, sn_gate_tra
     if (e == cudaSuccess) e = alloc(&t->v, P);
     if (e == cudaSuccess) e = alloc(&t->grad, P);
     if (e == cudaSuccess) e = alloc(&t->loss, 1);
+    if (e == cudaSuccess) e = alloc(&t->err, 1);
+    if (e == cudaSuccess) e = cudaMemset(t->err, 0, sizeof(int));
     if (e == cudaSuccess) e = sn::gate_alloc(t->w);
     if (e == cudaSuccess) e = alloc(&t->F, B * 25 * 8);
     if (e == cudaSuccess) e = alloc(&t->A1, B * 9 * 80);
@@ -341,6 +412,7 @@ sn_status sn_gate_trainer_destroy(sn_gate_trainer* t) {
     cudaFree(t->v);
     cudaFree(t->grad);
     cudaFree(t->loss);
+    cudaFree(t->err);
     sn::gate_free(t->w);
     cudaFree(t->F);
     cudaFree(t->A1);
@@ -401,6 +473,18 @@ sn_status sn_gate_trainer_resume(sn_gate_trainer* t, const float* theta, const f
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     t->step = step;
     return e == cudaSuccess ? SN_OK : SN_ECUDA;
+}
+
+sn_status sn_gate_trainer_check_device(sn_gate_trainer* t, sn_stream stream) {
+    if (!t) return SN_EINVAL;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, t->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && h) e = cudaMemsetAsync(t->err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return SN_ECUDA;
+    return h ? SN_ETIMEOUT : SN_OK;
 }
 
 }  // extern "C"

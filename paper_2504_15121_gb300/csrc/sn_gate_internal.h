@@ -34,8 +34,11 @@ struct GateDev {
 cudaError_t gate_alloc(GateDev& w);
 void gate_free(GateDev& w);
 cudaError_t gate_layout(const float* theta, const GateDev& w, cudaStream_t s);
+// C [M][N] (FP32, rows ldc apart) = A B with A(m, k) = A[m sam + k sak],
+// B(k, n) = B[k sbk + n sbn] on the tcgen05 tensor cores; err: device word
+// that a kernel whose bounded MMA wait gave up sets (its C is undefined).
 cudaError_t gemm_bf16(int M, int N, int K, const __nv_bfloat16* A, long long sam, long long sak,
-                      const __nv_bfloat16* B, long long sbk, long long sbn, float* C, long long ldc,
+                      const __nv_bfloat16* B, long long sbk, long long sbn, float* C, long long ldc, int* err,
                       cudaStream_t s);
 void k_adam_launch(int n, float* theta, float* m, float* v, const float* g, float lr, float b1c, float b2c,
                    cudaStream_t s);

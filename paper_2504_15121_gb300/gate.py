@@ -37,14 +37,15 @@ for _name, _args, _res in [
         ("sn_gate_trainer_grad", [_vp, _vp, _vp, _i, _vp, _vp, _vp, _vp], _i),
         ("sn_gate_trainer_step", [_vp, _vp, _vp, _i, _f, _vp, _vp], _i),
         ("sn_gate_trainer_state", [_vp, _vp, _vp, _vp, C.POINTER(C.c_longlong)], _i),
-        ("sn_gate_trainer_resume", [_vp, _vp, _vp, _vp, C.c_longlong], _i)]:
+        ("sn_gate_trainer_resume", [_vp, _vp, _vp, _vp, C.c_longlong], _i),
+        ("sn_gate_trainer_check_device", [_vp, _vp], _i)]:
     _fn = getattr(lib, _name)
     _fn.argtypes = _args
     _fn.restype = _res
 
 EXPORTS = ("sn_gate_param_count", "sn_gate_trainer_create", "sn_gate_trainer_destroy",
            "sn_gate_trainer_grad", "sn_gate_trainer_step", "sn_gate_trainer_state",
-           "sn_gate_trainer_resume")
+           "sn_gate_trainer_resume", "sn_gate_trainer_check_device")
 N_PARAMS = lib.sn_gate_param_count()
 
 
@@ -137,6 +138,11 @@ class Trainer:
         _check(lib.sn_gate_trainer_step(self.h, _ptr(patches), _ptr(y), B, float(lr), _ptr(self.loss_buf),
                                         _stream()), "sn_gate_trainer_step")
         return self.loss_buf
+
+    def check_device(self):
+        """Raises SnError (SN_ETIMEOUT) if a bounded tensor-core wait of the
+        trainer's GEMMs gave up since the last check (waits for the stream)."""
+        _check(lib.sn_gate_trainer_check_device(self.h, _stream()), "sn_gate_trainer_check_device")
 
     def state(self):
         th, m, v = (np.zeros(N_PARAMS, np.float32) for _ in range(3))
@@ -254,6 +260,7 @@ def train(X, y, epochs=4, batch=4096, lr=3e-3, seed=0, theta0=None, log=print, c
             losses.append(trainer.step(Xd[idx].contiguous(), yd[idx].contiguous(), rate).clone())
             k += 1
         ep_loss = float(torch.stack(losses).mean())
+        trainer.check_device()
         hist.append(ep_loss)
         log(f"epoch {ep} loss {ep_loss:.4f} ({time.time() - t0:.1f} s)")
         if checkpoint:
