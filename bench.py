@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--only-headline", action="store_true",
                     help="time the headline chain only (no other forms, comparators, stage calls, scene errors, "
                          "mixed batch, end to end, CPU baseline or serving): short runs for profilers")
+    ap.add_argument("--scene", default=WORKLOAD,
+                    help="the headline chain's scene (profiling another config, e.g. mixed_1482x994); the line "
+                         "then names it in its config")
     ap.add_argument("--params", default="",
                     help="sn_params overrides of the headline pipeline, e.g. support=0,r_affine=4 or learned=1 "
                          "(for profiling another form; the line then names them in its config)")
@@ -169,10 +172,10 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def make_inputs(n_distinct: int, rank: int):
+def make_inputs(n_distinct: int, rank: int, scene: str = WORKLOAD):
     """The seeded scenes of one rank: replicas take disjoint frame numbers."""
     from scenes import make_scene
-    return [make_scene(WORKLOAD, frame=rank * n_distinct + i) for i in range(n_distinct)]
+    return [make_scene(scene, frame=rank * n_distinct + i) for i in range(n_distinct)]
 
 
 def max_over_ranks(x: float, dist) -> float:
@@ -222,7 +225,44 @@ def cpu_baseline(scenes, seconds: float):
             "sample": f"{n} whole {WORKLOAD} frames (FP32 input, full chain), {dt:.1f} s",
             "single_thread": {"value": v1, "unit": "MPix/s", "cores": 1,
                               "sample": f"{n1} whole frames, {dt1:.1f} s"},
-            "host": f"{cores} cores, {os.uname().machine}"}
+            "per_config": oracle_per_config(cores),
+            "host": f"{cores} cores, {os.uname().machine}, {cpu_model()}"}
+
+
+def oracle_per_config(cores, reps=5):
+    """The oracle's full chain on one frame of each of the three plain
+    scenes (320x240, 1482x994, 2048x1024): median of `reps` runs on all
+    host cores and on one core (ms per frame and MPix/s)."""
+    import oracle
+    from scenes import make_scene
+    out = {}
+    for name in ("planes_320x240", "mixed_1482x994", WORKLOAD):
+        s = make_scene(name, frame=0)
+        row = {}
+        for threads in (cores, 1):
+            oracle.set_threads(threads)
+            ts = []
+            for _ in range(reps if threads > 1 or s.W * s.H < 10 ** 6 else 1):
+                t0 = time.perf_counter()
+                oracle.run_frame(s.disp, s.camera)
+                ts.append(time.perf_counter() - t0)
+            ms = 1e3 * float(np.median(ts))
+            row["all_cores" if threads > 1 else "one_core"] = {"ms": ms, "mpix_s": s.W * s.H / ms / 1e3,
+                                                              "runs": len(ts)}
+        out[name] = row
+    oracle.set_threads(cores)
+    return out
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 # ---------------------------------------------------------------- reference arm
@@ -282,7 +322,7 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_2504_15121_gb300 import Pipeline, sn
 
-    scenes = make_inputs(args.distinct, rank)
+    scenes = make_inputs(args.distinct, rank, args.scene)
     s0 = scenes[0]
     W, H, cam = s0.W, s0.H, s0.camera
     overrides = parse_params(args.params)
@@ -412,7 +452,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {
-                "workload": f"{WORKLOAD}: plain chain, FP32 disparity in, FP32 normals/points out, "
+                "workload": f"{args.scene}: plain chain, FP32 disparity in, FP32 normals/points out, "
                             f"star-fill CD s10 d8 k0.1, 5x5 denoise; {F} frames per step "
                             f"({args.distinct} distinct seeded scenes) spread over {args.streams} CUDA streams",
                 "frames_per_step": F, "W": W, "H": H, "streams": args.streams,
