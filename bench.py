@@ -254,12 +254,17 @@ def oracle_per_config(cores, reps=5):
     return out
 
 
+ARM_PARTS = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1"}
+
+
 def cpu_model():
+    """The host CPU's model name (x86) or Arm core part."""
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
-                if line.lower().startswith(("model name", "cpu part", "hardware")):
-                    return line.split(":", 1)[1].strip()
+                if line.lower().startswith(("model name", "cpu part")):
+                    v = line.split(":", 1)[1].strip()
+                    return ARM_PARTS.get(v.lower(), v)
     except OSError:
         pass
     return "unknown"
