@@ -314,20 +314,30 @@ __global__ void __launch_bounds__(kThreads, 2)
                 reinterpret_cast<float*>(reinterpret_cast<char*>(qout) + (size_t)y * qp)[x] = v;
             }
         } else {
-            // lattice columns b of tile column c: |x0 - kLatO + 2 b - (x0 + c)| <= kLatM
+            // lattice columns b of tile column c: |x0 - kLatO + 2 b - (x0 + c)| <= kLatM,
+            // i.e. b from lo(c) = (c - kLatM + kLatO + 1) >> 1, kLatM (c even) or
+            // kLatM + 1 (c odd) of them (kLatM odd, kLatO even); the last one is
+            // read for every c (in range) and kept only for odd c
+            static_assert(kLatM % 2 == 1 && ((kTW - 1 - kLatM + kLatO + 1) >> 1) + kLatM < kLatW &&
+                              ((kTH - 1 - kLatM + kLatO + 1) >> 1) + kLatM < kLatH,
+                          "lattice window of kLatM or kLatM + 1 points");
             for (int e = tid; e < kLatH * kTW; e += kThreads) {
                 const int a = e / kTW, c = e - a * kTW;
-                const float* q0 = qs + a * kLatW;
-                float m = q0[(c - kLatM + kLatO + 1) >> 1];
-                for (int bb = ((c - kLatM + kLatO + 1) >> 1) + 1; bb <= (c + kLatM + kLatO) >> 1; bb++)
-                    m = fminf(m, q0[bb]);
-                qrow[e] = m;
+                const float* q0 = qs + a * kLatW + ((c - kLatM + kLatO + 1) >> 1);
+                float m = q0[0];
+#pragma unroll
+                for (int k = 1; k < kLatM; k++) m = fminf(m, q0[k]);
+                const float last = q0[kLatM];
+                qrow[e] = (c & 1) ? fminf(m, last) : m;
             }
             __syncthreads();
             if (inside) {
-                float m = qrow[((row - kLatM + kLatO + 1) >> 1) * kTW + lane];
-                for (int a = ((row - kLatM + kLatO + 1) >> 1) + 1; a <= (row + kLatM + kLatO) >> 1; a++)
-                    m = fminf(m, qrow[a * kTW + lane]);
+                const float* q1 = qrow + ((row - kLatM + kLatO + 1) >> 1) * kTW + lane;
+                float m = q1[0];
+#pragma unroll
+                for (int k = 1; k < kLatM; k++) m = fminf(m, q1[k * kTW]);
+                const float last = q1[kLatM * kTW];
+                if (row & 1) m = fminf(m, last);
                 o.mask[(size_t)y * o.mp + x] = (ok && m >= gv.tau) ? (uint8_t)SN_MASK_LEARNED : (uint8_t)0;
             }
         }
