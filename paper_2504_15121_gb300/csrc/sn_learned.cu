@@ -360,21 +360,28 @@ __global__ void __launch_bounds__(kThreads, 2)
         {
             uint4* F = feat;
             constexpr int kRowsPerPass = kThreads / kFW;
-            const int fx = tid % kFW;
+            constexpr int kPasses = (kFH + kRowsPerPass - 1) / kRowsPerPass;
+            // the right neighbour's entries of the last map column read one
+            // code past the row, which the code region holds (kLW = kFW + 1,
+            // kLH = kFH + 1), and are then zeroed
+            static_assert(kLW == kFW + 1 && kLH == kFH + 1, "codes one past the map");
+            const int fx = tid % kFW, fy0 = tid / kFW;
+            const bool has_right = fx + 1 < kFW;
             if (tid < kRowsPerPass * kFW) {
-                for (int fy = tid / kFW; fy < kFH; fy += kRowsPerPass) {
-                    const int e = fy * kLW + fx;
-                    const float Lc = L[e], Lr = L[e + 1];
-                    uint4 v;
-                    v.x = bf16x2(nan_to_zero(Lr - Lc), nan_to_zero(L[e + kLW] - Lc));
-                    v.y = Lc == Lc ? 0x3F80u : 0u;  // BF16 1.0 where the code is valid
-                    v.z = 0u;
-                    v.w = 0u;
-                    if (fx + 1 < kFW) {
-                        v.z = bf16x2(nan_to_zero(L[e + 2] - Lr), nan_to_zero(L[e + kLW + 1] - Lr));
-                        v.w = Lr == Lr ? 0x3F80u : 0u;
+#pragma unroll
+                for (int k = 0; k < kPasses; k++) {
+                    const int fy = fy0 + k * kRowsPerPass;
+                    if (fy < kFH) {
+                        const int e = fy * kLW + fx;
+                        const float Lc = L[e], Lr = L[e + 1];
+                        uint4 v;
+                        v.x = bf16x2(nan_to_zero(Lr - Lc), nan_to_zero(L[e + kLW] - Lc));
+                        v.y = Lc == Lc ? 0x3F80u : 0u;  // BF16 1.0 where the code is valid
+                        const unsigned z = bf16x2(nan_to_zero(L[e + 2] - Lr), nan_to_zero(L[e + kLW + 1] - Lr));
+                        v.z = has_right ? z : 0u;
+                        v.w = has_right && Lr == Lr ? 0x3F80u : 0u;
+                        F[fy * kFW + fx] = v;
                     }
-                    F[fy * kFW + fx] = v;
                 }
             }
         }
@@ -401,7 +408,10 @@ __global__ void __launch_bounds__(kThreads, 2)
         umma::fence_after();
         if (ok && i + 1 < n) load_L(i + 1);
         if (ok) {
-            for (int t = warp >> 2; t < kMT1; t += kThreads / 128) {
+#pragma unroll
+            for (int k = 0; k < (kMT1 + kThreads / 128 - 1) / (kThreads / 128); k++) {
+                const int t = (warp >> 2) + k * (kThreads / 128);
+                if (t >= kMT1) break;  // warp-uniform
                 uint32_t r[16];
                 umma::ld16(tmem + tlane + 16 * t, r);
                 umma::wait_ld();
