@@ -505,7 +505,10 @@ __global__ void __launch_bounds__(kThreads, 2)
         // ---- row pass: for every entry (tile rows -kFastR .. kTH - 1 + kFastR)
         // over |u| <= 2 and |u| <= kFastR: (count + 2^16 sum u) of the valid
         // samples, their sum u^2, the sums of D and of u D (D = 0 where invalid)
-        for (int e = tid; e < kRS; e += kThreads) {
+#pragma unroll
+        for (int pass = 0; pass < (kRS + kThreads - 1) / kThreads; pass++) {
+            const int e = tid + pass * kThreads;
+            if (kRS % kThreads != 0 && e >= kRS) break;
             const int2* p = tile + (e / kTW + kLR - kFastR) * kLTWR + e % kTW + kLR;
             int A = 0, B = 0, Q0 = 0, Q1 = 0;
 #pragma unroll
