@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     // the gate bit the gate kernel left in the mask
     const bool cand = inside && (o.mask[(size_t)y * o.mp + x] & SN_MASK_LEARNED);
     if (tid == 0) *cnt = 0;
-    stage_tile<IN, kLR, kTH, kThreads>(tile, smem + kCOffRS, &dmap, true, disp, dp, x0, y0, g, kStageRcp);
+    stage_tile<IN, kLR, kTH, kThreads, false>(tile, smem + kCOffRS, &dmap, true, disp, dp, x0, y0, g, kStageRcp);
     const int2* c = tile + (row + kLR) * kLTWR + lane + kLR;
     const int Dc = c[0].x;  // 0 outside the image
     const bool gated = cand && Dc > 0;

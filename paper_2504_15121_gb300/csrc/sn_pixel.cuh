@@ -521,7 +521,7 @@ enum StageY { kStageZero = 0, kStageRcp = 1, kStagePacked = 2 };
 // then a conversion pass.  If `use_tma` is off or `raw` is not 128-byte
 // aligned, the tile is loaded with plain loads instead.  Ends with a block
 // barrier.
-template <int IN, int R, int TH, int NT>
+template <int IN, int R, int TH, int NT, bool UNROLL = true>
 __device__ __forceinline__ void stage_tile(int2* tile, unsigned char* raw, const CUtensorMap* dmap, bool use_tma,
                                            const char* disp, size_t dp, int x0, int y0, const Geo& g, int ymode) {
     constexpr int TW = kTW + 2 * R, N = TW * (TH + 2 * R), BW = tma_bw<IN, R, TW>();
@@ -553,7 +553,12 @@ __device__ __forceinline__ void stage_tile(int2* tile, unsigned char* raw, const
         ok = __syncthreads_and(ok);
     }
     ok = tma && ok;
-    for (int i = tid; i < N; i += NT) {
+    // UNROLL: the passes unrolled (the conversion loop of a kernel with
+    // registers to spare); else a plain strided loop
+#pragma unroll(UNROLL ? (N + NT - 1) / NT : 1)
+    for (int pass = 0; pass < (N + NT - 1) / NT; pass++) {
+        const int i = tid + pass * NT;
+        if (N % NT != 0 && i >= N) break;
         const int ly = i / TW, lx = i - ly * TW;
         const int b = ly * BW + lx + tma_xpad<IN, R>() - R;
         int D = 0;
