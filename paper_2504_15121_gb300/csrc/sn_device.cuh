@@ -13,6 +13,15 @@ namespace sn {
 constexpr int kFindLimit = 1 << 22;   // > any parent chain of a 16384^2 frame
 constexpr int kUnionLimit = 1 << 20;  // retries of one lock-free union
 
+// Reciprocal with at most 1 ulp error (PTX rcp.approx, flushing denormals);
+// every input here is a positive normal number (codes 1..131071, positive
+// disparities, 256 det with det >= 1).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // ---------------------------------------------------------------- ingest
 // D = rint(256 d) (ties to even) if d is finite, d > 0 and 1 <= D <= 131071,
 // else 0 (invalid).  256 d is exact in binary floating point, so the
@@ -320,7 +329,7 @@ __device__ __forceinline__ bool solve_normal_dc(const AffSums& s, int Dc, float 
         return true;
     }
     {
-        const float inv = 1.0f / (256.0f * fdet);
+        const float inv = rcp_approx(256.0f * fdet);
         const float gu = fmaf(-dcf, fcu, i64_to_f32(nu_i)) * inv;
         const float gv = fmaf(-dcf, fcv, i64_to_f32(nv_i)) * inv;
         const float mx = gu;

@@ -59,14 +59,6 @@ __device__ __forceinline__ Thr make_thr(const Geo& g, int Dc) {
     return t;
 }
 
-// Reciprocal with at most 1 ulp error (PTX rcp.approx); the inputs are
-// integer codes 1..131071, never denormal.
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
 // Exact decision from the two extreme reciprocals: w is within 1 ulp of 1/D
 // and D < 2^17, so rint(1/w) recovers D exactly.
 __device__ __noinline__ bool cd_stop_from_w(float wlo, float whi, int Dc, int K) {
@@ -371,7 +363,7 @@ __device__ __forceinline__ void pix_zero(PixOut& r) {
 }
 
 __device__ __forceinline__ void pix_points(const Geo& g, int x, int y, PixOut& r) {
-    const float inv = 1.0f / r.dtil;
+    const float inv = rcp_approx(r.dtil);  // dtil > 0 for every pixel that gets a point
     r.P[0] = g.B * ((float)x - g.cx) * inv;
     r.P[1] = g.B_fx_over_fy * ((float)y - g.cy) * inv;
     r.P[2] = g.fxB * inv;
@@ -414,8 +406,11 @@ __device__ __forceinline__ void plain_pixel(const Geo& g, const StarTable* T, co
     r.m = SN_MASK_VALID;
     long long num, det;
     const bool fit = denoise_exact<RD>(c, TWR, g.r_d, Dc, g.K_range, num, det);
-    // a 5x5 det is below 2^24 (exact in FP32)
-    const float dcf = fit ? i64_to_f32(num) / (RD == 2 ? (float)(int)det : i64_to_f32(det)) : 0.0f;
+    // a 5x5 det is below 2^24 (exact in FP32); the intercept's fraction
+    // needs no correctly rounded division (its error is below the outputs'
+    // tolerances by orders of magnitude)
+    const float dcf =
+        fit ? (RD == 2 ? i64_to_f32(num) * rcp_approx((float)(int)det) : i64_to_f32(num) / i64_to_f32(det)) : 0.0f;
     if (fit) r.m |= SN_MASK_DENOISED;
     r.dtil = ((float)Dc + dcf) * (1.0f / 256.0f);
     AffSums s;
@@ -477,7 +472,7 @@ __device__ __forceinline__ void fast_pixel(const Geo& g, int Dc, const WinSums& 
     r.m = SN_MASK_VALID | SN_MASK_LEARNED;
     long long num, det;
     const bool fit = denoise_from_sums(w2, Dc, num, det);
-    const float dcf = fit ? i64_to_f32(num) / (float)(int)det : 0.0f;
+    const float dcf = fit ? i64_to_f32(num) * rcp_approx((float)(int)det) : 0.0f;
     if (fit) r.m |= SN_MASK_DENOISED;
     r.dtil = ((float)Dc + dcf) * (1.0f / 256.0f);
     AffSums s;

@@ -106,7 +106,7 @@ __device__ __forceinline__ void window_affine(const Geo& g, int Dc, bool fit, lo
                                               const WinSums& wa, int x, int y, PixOut& r) {
     pix_zero(r);
     r.m = SN_MASK_VALID;
-    const float dcf = fit ? i64_to_f32(num) / (float)(int)det : 0.0f;  // 5x5: det below 2^24
+    const float dcf = fit ? i64_to_f32(num) * rcp_approx((float)(int)det) : 0.0f;  // 5x5: det below 2^24
     if (fit) r.m |= SN_MASK_DENOISED;
     r.dtil = ((float)Dc + dcf) * (1.0f / 256.0f);
     AffSums s;
