@@ -200,6 +200,27 @@ def test_extreme_codes(P, kind, params):
     compare_frame(g, ref)
 
 
+def test_covered_depth_at_the_threshold(P):
+    # k_cd = 0.1 (K = 6554): with Dc = Dmin = 29491 the stop test
+    # (Dmax - Dmin) Dc 2^16 > K Dmin Dmax holds from Dmax = 32769 on and is an
+    # equality at Dmax = 32768, so rays meeting such samples sit exactly on the
+    # threshold, inside every FP32 rounding band: the exact test must decide
+    K = int(round(0.1 * 65536))
+    assert (32768 - 29491) * 29491 * 65536 == K * 29491 * 32768
+    assert (32769 - 29491) * 29491 * 65536 > K * 29491 * 32769
+    rng = np.random.default_rng(17)
+    H, W = 64, 96
+    D = np.full((H, W), 29491, np.int32)
+    sites = rng.random((H, W))
+    D[sites < 0.03] = 32768
+    D[(sites >= 0.03) & (sites < 0.06)] = 32769
+    D[(sites >= 0.06) & (sites < 0.08)] = 0
+    cam = Camera(400.0, 400.0, W / 2, H / 2, 0.1)
+    for params in (dict(support=1), dict(support=1, dirs=16, steps=12)):
+        g, ref = chain(P, codes_to_f32(D), cam, **params)
+        compare_frame(g, ref)
+
+
 def _fallback_frame(rng, H=96, W=160):
     """Integer codes with the denoise fallback's windows placed on purpose:
     isolated pixels, one-row and one-column strips, diagonals (singular
