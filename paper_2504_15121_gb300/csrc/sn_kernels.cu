@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(256)
 // index of its component; roots are counted.  A thread takes kFlatPix
 // pixels of one column of a kTW x kTH tile (their label loads overlap, and
 // a label equal to the previous pixel's reuses its root).
-constexpr int kFlatPix = 4;
+constexpr int kFlatPix = 8;
 __global__ void __launch_bounds__(kTW * kTH / kFlatPix)
     k_ccl_flatten(const Geo g, int* labels, size_t lpe, int* count) {
     const int x = blockIdx.x * kTW + threadIdx.x;
