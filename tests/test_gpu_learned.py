@@ -111,6 +111,27 @@ def test_learned_gate_and_chain(P, name, frame):
     assert e_learned <= e_plain + 0.05
 
 
+@pytest.mark.parametrize("dtype", ["f16", "u16"])
+def test_learned_16bit_inputs(P, dtype):
+    # the gate and chain kernels' 16-bit TMA boxes: q within the oracle's
+    # bounds and the gated chain against the oracle, from FP16 and uint16 input
+    from paper_2504_15121_gb300 import gate as G
+    theta = G.load_weights().astype(np.float64)
+    s = make_scene("driving_2048x1024", frame=3)
+    arr, dt = (s.disp_f16, P.sn.SN_IN_F16) if dtype == "f16" else (s.disp_u16, P.sn.SN_IN_U16X256)
+    pipe = P.Pipeline(s.camera, s.W, s.H, learned=1, in_dtype=dt)
+    try:
+        g = run_gpu(pipe, arr)
+        q = gpu_q(P, pipe, arr)
+    finally:
+        pipe.close()
+    gpu_gate = (g["mask"] & oracle.M_LEARNED) > 0
+    D = oracle.ingest(arr)
+    undecided = check_gate(theta, D, q, gpu_gate, f"driving {dtype}")
+    assert undecided <= 1e-3 * (D > 0).sum()
+    compare_frame(g, oracle.run_frame(arr, s.camera, gate=gpu_gate))
+
+
 def test_learned_needs_weights_and_default_star(P):
     sn = P.sn
     s = make_scene("planes_320x240", frame=0)

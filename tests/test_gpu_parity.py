@@ -153,6 +153,9 @@ def test_fixed_window_radii_full_size(P, r):
     s = make_scene("driving_2048x1024", frame=5)
     g16, ref16 = chain(P, s.disp_u16, s.camera, support=0, r_affine=r, in_dtype=P.sn.SN_IN_U16X256)
     compare_frame(g16, ref16)
+    if r in (2, 7):  # FP16 input (the box's other 16-bit element type)
+        gh, refh = chain(P, s.disp_f16, s.camera, support=0, r_affine=r, in_dtype=P.sn.SN_IN_F16)
+        compare_frame(gh, refh)
 
 
 @pytest.mark.parametrize("H,W", [(1, 1), (5, 7), (17, 33), (40, 65)])
