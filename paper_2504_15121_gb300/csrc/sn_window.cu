@@ -10,10 +10,10 @@
 // range gate (the usual case: one surface), the gated fit takes exactly the
 // valid samples, whose sums the separable passes give.  The test needs the
 // window's smallest and largest valid code (also separable).  The other
-// valid pixels are compacted into a list and take the gated fit sample by
-// sample (denoise_exact), then the same window sums for the affine fit.
-// Both routes give the same integers as the direct fits, hence the same
-// outputs bit for bit.
+// valid pixels take the gated fit sample by sample (denoise_exact) in
+// place: compacting them onto a list measured slower, its block barrier
+// costing more than the divergence it saves.  Both routes give the same
+// integers as the direct fits, hence the same outputs bit for bit.
 #include <atomic>
 
 #include <cuda.h>  // CUtensorMap
@@ -41,9 +41,7 @@ struct Win {
     static constexpr size_t OFF_RSA = align128z(sizeof(int2) * TW * THR);  // the full window's row sums
     static constexpr size_t OFF_RS5 = OFF_RSA + sizeof(int4) * RS;
     static constexpr size_t OFF_MM = OFF_RS5 + sizeof(int4) * RS;
-    static constexpr size_t OFF_LIST = OFF_MM + sizeof(int2) * RS;
-    static constexpr size_t OFF_CNT = OFF_LIST + sizeof(int) * kTW * kWTH;
-    static constexpr size_t SMEM = align128z(OFF_CNT + 16);
+    static constexpr size_t SMEM = align128z(OFF_MM + sizeof(int2) * RS);
     // sums of u^2 E stay packed up to R = 5 (sum u^2 D <= 110 * 2^17 < 2^24)
     static constexpr bool PACKED_UU = R <= 5;
     // moments bounded as for the M = 8, s = 10 star (1024 alpha gamma < 2^31)
@@ -135,12 +133,9 @@ __global__ void __launch_bounds__(kWNT, 4)
     int4* rsa = reinterpret_cast<int4*>(smem + L::OFF_RSA);
     int4* rs5 = reinterpret_cast<int4*>(smem + L::OFF_RS5);
     int2* mm5 = reinterpret_cast<int2*>(smem + L::OFF_MM);
-    int* list = reinterpret_cast<int*>(smem + L::OFF_LIST);
-    int* cnt = reinterpret_cast<int*>(smem + L::OFF_CNT);
     const int lane = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * kTW + lane;
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kWTH;
-    if (tid == 0) *cnt = 0;
     // the raw TMA box (and its mbarrier) lies where the full window's row sums go
     stage_tile<IN, L::HR, kWTH, kWNT>(tile, smem + L::OFF_RSA, &dmap, true, disp, dp, x0, y0, g, kStagePacked);
 
@@ -184,17 +179,14 @@ __global__ void __launch_bounds__(kWNT, 4)
     }
     __syncthreads();
 
-    // ---- each thread's two pixels: the fast route where the 5x5 gate
-    // passes every valid sample, else onto the list
-    bool need[2];
+    // ---- each thread's two pixels: the window sums where the 5x5 gate
+    // passes every valid sample, else the gate sample by sample
 #pragma unroll
     for (int k = 0; k < 2; k++) {
         const int row = ty + 8 * k, x = x0 + lane, y = y0 + row;
         const int e0 = (row + L::HR) * kTW + lane;
         const int Dc = tile[(row + L::HR) * L::TW + lane + L::HR].x;  // 0 outside the image
-        const bool inside = x < g.W && y < g.H;
-        need[k] = false;
-        if (!inside) continue;
+        if (x >= g.W || y >= g.H) continue;
         PixOut r;
         if (Dc <= 0) {
             pix_zero(r);
@@ -213,40 +205,16 @@ __global__ void __launch_bounds__(kWNT, 4)
             mx = max(mx, m.y);
         }
         // the centre is valid, so mn + 1 is the window's smallest valid code
-        if ((int)mn + 1 < Dc - lo || mx > Dc + thr) {
-            need[k] = true;
-            continue;
-        }
-        const WinSums w2 = column_sums<2>(rs5, e0);
         long long num, det;
-        const bool fit = denoise_from_sums(w2, Dc, num, det);
+        bool fit;
+        if ((int)mn + 1 < Dc - lo || mx > Dc + thr)
+            fit = denoise_exact<2>(tile + (row + L::HR) * L::TW + lane + L::HR, L::TW, 2, Dc, g.K_range, num, det);
+        else
+            fit = denoise_from_sums(column_sums<2>(rs5, e0), Dc, num, det);
         window_affine<L::SOLVE32>(g, Dc, fit, num, det, column_sums<R>(rsa, e0), x, y, r);
         emit(g, o, x, y, r);
     }
 
-    // ---- the others, compacted so that whole warps take the sample-by-sample gate
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const unsigned m = __ballot_sync(0xffffffffu, need[k]);
-        int base = 0;
-        if (lane == 0 && m) base = atomicAdd(cnt, __popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (need[k]) list[base + __popc(m & ((1u << lane) - 1u))] = (ty + 8 * k) * kTW + lane;
-    }
-    __syncthreads();
-    const int nl = *cnt;
-    for (int i = tid; i < nl; i += kWNT) {
-        const int p = list[i];
-        const int px = p % kTW, py = p / kTW;
-        const int2* c = tile + (py + L::HR) * L::TW + px + L::HR;
-        const int Dc = c[0].x;
-        long long num, det;
-        const bool fit = denoise_exact<2>(c, L::TW, 2, Dc, g.K_range, num, det);
-        PixOut r;
-        window_affine<L::SOLVE32>(g, Dc, fit, num, det, column_sums<R>(rsa, (py + L::HR) * kTW + px), x0 + px,
-                                  y0 + py, r);
-        emit(g, o, x0 + px, y0 + py, r);
-    }
 }
 
 template <int IN, int R>
