@@ -213,6 +213,7 @@ sn_status prepare_constants(const sn_camera* cam, int W, int H, const sn_params*
     if (!build_star(p->dirs, p->steps, *t)) return SN_ENOTSUP;
     memset(g, 0, sizeof(*g));
     g->W = W;
+    g->w_rcp = w_reciprocal(W);
     g->H = H;
     g->in_dtype = p->in_dtype;
     g->r_d = p->r_denoise;
@@ -358,6 +359,7 @@ sn_status sn_create(const sn_camera* cam, int W, int H, const sn_params* pin, sn
     g.dB = cam->baseline;
     sn::set_st(g, cam, p.st_t);
     g.walk_limit = sn::kWalkLimitDefault;
+    g.w_rcp = sn::w_reciprocal(W);
 
     cudaError_t e = cudaMalloc(&c->ws.err, 2 * sizeof(int));
     if (e == cudaSuccess) {

@@ -74,9 +74,10 @@ __device__ __forceinline__ bool pair_edge(int a, int b, int K) {
 __device__ __forceinline__ int pair_thr(int D, int K) {
     return (int)(((unsigned long long)(unsigned)K * (unsigned)D) >> 16);
 }
-__device__ __forceinline__ bool pair_edge_t(int a, int ta, int b, int tb) {
-    return a > 0 && b > 0 && abs(a - b) <= min(ta, tb);
-}
+// With t = -1 for an invalid code (pair_thr_v) the test needs no validity
+// check: min(t_a, t_b) = -1 < 0 <= |a - b| whenever either code is invalid.
+__device__ __forceinline__ int pair_thr_v(int D, int K) { return D > 0 ? pair_thr(D, K) : -1; }
+__device__ __forceinline__ bool pair_edge_v(int a, int ta, int b, int tb) { return abs(a - b) <= min(ta, tb); }
 
 // covered-depth stop: (nmax - nmin) Dc 2^16 > K nmin nmax
 __device__ __forceinline__ bool cd_stop(int nmin, int nmax, int Dc, int K) {
@@ -401,12 +402,15 @@ __device__ __forceinline__ void union_s(int* L, int a, int b, int* err) {
     atomicOr(err, kErrUnionLimit);
 }
 
+// Address of label i = v W + u (row v, column u) in a buffer of pitch
+// pitch_elems; the row comes from the multiply by ceil(2^64 / W) (Geo::w_rcp).
 struct LabelIndex {
     int W;
+    unsigned long long w_rcp;
     size_t pitch_elems;
     __device__ __forceinline__ size_t addr(int i) const {
-        const int v = i / W;
-        return (size_t)v * pitch_elems + (size_t)(i - v * W);
+        const unsigned v = W == 1 ? (unsigned)i : (unsigned)__umul64hi((unsigned long long)(unsigned)i, w_rcp);
+        return (size_t)(unsigned)i + (size_t)v * (pitch_elems - (size_t)W);
     }
 };
 

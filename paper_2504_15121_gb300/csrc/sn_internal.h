@@ -40,6 +40,10 @@ struct Geo {
     double st_F, st_t;
     float st_Ff, st_tf;
     int walk_limit;  // parent steps of one union-find walk in the component passes
+    // ceil(2^64 / W) for W >= 2: for any 0 <= i < 2^32 the quotient i / W is
+    // the high word of the 128-bit product i w_rcp (the rounding error
+    // i (w_rcp W - 2^64) / (W 2^64) stays below i / 2^64 < 1 / W); 0 for W = 1
+    unsigned long long w_rcp;
     // Moments of each star ray's prefixes (device, may be null): entry
     // (j (steps + 1) + k) 6 + q holds, over the entries of ray j before step
     // k that only this ray reaches, the sum of 1, u, v, u^2, u v, v^2 (q = 0..5)
@@ -84,6 +88,10 @@ struct Marks {
 // Guard band factors (1 + e, 1 - e) of the FP32 reciprocal covered-depth test
 // for K = rint(2^16 k).
 void cd_band(int K, float* hi, float* lo);
+
+// ceil(2^64 / W) (UINT64_MAX / W + 1 equals it whether or not W divides
+// 2^64), 0 for W < 2.
+inline unsigned long long w_reciprocal(int W) { return W < 2 ? 0ull : ~0ull / (unsigned long long)W + 1ull; }
 
 // Checks camera, size and parameters and fills the kernel constants without
 // touching the device.

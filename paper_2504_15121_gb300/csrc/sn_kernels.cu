@@ -127,23 +127,23 @@ template <int IN>
 __global__ void __launch_bounds__(kCclTile * 8)
     k_ccl_local(const Geo g, const char* __restrict__ disp, size_t dp, int* __restrict__ labels,
                 size_t lpe, int* __restrict__ count, const __grid_constant__ CUtensorMap dmap, int use_tma) {
-    // Each warp labels rows ty, ty + 8, ty + 16, ty + 24 of the 32 x 32 tile:
-    // the pixels joined to their left neighbour form runs, labelled by the
-    // run's first lane (from a ballot of left edges); then vertical edges join
-    // the runs of adjacent rows in a shared-memory union-find (an edge implied
-    // by its left neighbour's is skipped).
+    // Warp w labels rows 4 w .. 4 w + 3 of the 32 x 32 tile, lane = column,
+    // codes and pair thresholds in registers: the pixels joined to their left
+    // neighbour form runs, labelled by the run's first lane (from a ballot of
+    // left edges); then vertical edges join the runs of adjacent rows in a
+    // shared-memory union-find (an edge implied by its left neighbour's is
+    // skipped).  A warp's first row meets the row above through shared memory.
     constexpr int kRows = kCclTile / 8;
-    __shared__ int Ds[kCclTile * kCclTile];
     __shared__ int Ls[kCclTile * kCclTile];
-    __shared__ int Ts[kCclTile * kCclTile];  // pair_thr of every code
-    __shared__ unsigned Lrow[kCclTile];
+    __shared__ int2 Last[8][kCclTile];  // (D, t) of each warp's last row
+    __shared__ unsigned Lrow[8];         // left-edge ballot of each warp's last row
     // the tile's raw disparities by one TMA copy (zero outside the image;
     // the box starts on a 32-element column, a 16-byte boundary)
     constexpr int kES = IN == SN_IN_F32 ? 4 : 2;
     __shared__ __align__(128) unsigned char raw[kCclTile * kCclTile * kES];
     __shared__ uint64_t sbar;
     const int x0 = blockIdx.x * kCclTile, y0 = blockIdx.y * kCclTile;
-    const int lane = threadIdx.x, tid = threadIdx.y * kCclTile + lane;
+    const int lane = threadIdx.x, w = threadIdx.y, tid = w * kCclTile + lane;
     if (count && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) *count = 0;
     const bool tma = use_tma && (umma::smem_addr(raw) & 127u) == 0;
     // one thread issues the copy and waits for it (sleeping between polls);
@@ -165,23 +165,27 @@ __global__ void __launch_bounds__(kCclTile * 8)
         ok = __syncthreads_and(ok);
     }
     ok = tma && ok;
+    // codes and thresholds (pair_thr_v: -1 for an invalid code, so that the
+    // pair test needs no validity check)
+    int D[kRows], T[kRows];
 #pragma unroll
     for (int k = 0; k < kRows; k++) {
-        const int r = threadIdx.y + 8 * k, i = r * kCclTile + lane;
-        int D = 0;
+        const int r = kRows * w + k, i = r * kCclTile + lane;
+        int d = 0;
         if (ok) {
             if constexpr (IN == SN_IN_F32)
-                D = code_from_float(reinterpret_cast<const float*>(raw)[i]);
+                d = code_from_float(reinterpret_cast<const float*>(raw)[i]);
             else if constexpr (IN == SN_IN_F16)
-                D = code_from_float(__half2float(reinterpret_cast<const __half*>(raw)[i]));
+                d = code_from_float(__half2float(reinterpret_cast<const __half*>(raw)[i]));
             else
-                D = reinterpret_cast<const unsigned short*>(raw)[i];
+                d = reinterpret_cast<const unsigned short*>(raw)[i];
         } else if (!tma) {
-            D = load_code<IN>(disp, dp, x0 + lane, y0 + r, g.W, g.H);
+            d = load_code<IN>(disp, dp, x0 + lane, y0 + r, g.W, g.H);
         }
-        Ds[i] = D;
-        Ts[i] = pair_thr(D, g.K_pair);
+        D[k] = d;
+        T[k] = pair_thr_v(d, g.K_pair);
     }
+    Last[w][lane] = make_int2(D[kRows - 1], T[kRows - 1]);
     __syncthreads();
     const unsigned upto = 0xffffffffu >> (31 - lane);
     int run[kRows];
@@ -189,33 +193,38 @@ __global__ void __launch_bounds__(kCclTile * 8)
     unsigned Lb[kRows], Ub[kRows];
 #pragma unroll
     for (int k = 0; k < kRows; k++) {
-        const int r = threadIdx.y + 8 * k, i = r * kCclTile + lane;
-        const int D = Ds[i], t = Ts[i];
-        const bool eL = lane > 0 && pair_edge_t(D, t, Ds[i - 1], Ts[i - 1]);
-        eU[k] = r > 0 && pair_edge_t(D, t, Ds[i - kCclTile], Ts[i - kCclTile]);
+        const int r = kRows * w + k;
+        const int Dl = __shfl_up_sync(0xffffffffu, D[k], 1), Tl = __shfl_up_sync(0xffffffffu, T[k], 1);
+        const bool eL = lane > 0 && pair_edge_v(D[k], T[k], Dl, Tl);
+        if (k > 0) {
+            eU[k] = pair_edge_v(D[k], T[k], D[k - 1], T[k - 1]);
+        } else {
+            const int2 up = w > 0 ? Last[w - 1][lane] : make_int2(0, -1);
+            eU[k] = pair_edge_v(D[k], T[k], up.x, up.y);
+        }
         Lb[k] = __ballot_sync(0xffffffffu, eL);
         Ub[k] = __ballot_sync(0xffffffffu, eU[k]);
         run[k] = r * kCclTile + (31 - __clz(~Lb[k] & upto));
-        Ls[i] = D > 0 ? run[k] : -1;
-        if (lane == 0) Lrow[r] = Lb[k];
+        Ls[r * kCclTile + lane] = D[k] > 0 ? run[k] : -1;
     }
+    if (lane == 0) Lrow[w] = Lb[kRows - 1];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kRows; k++) {
         if (!eU[k]) continue;
-        const int r = threadIdx.y + 8 * k;
-        const unsigned Lup = Lrow[r - 1];
+        const int r = kRows * w + k;
+        const unsigned Lup = k > 0 ? Lb[k - 1] : Lrow[w > 0 ? w - 1 : 0];  // eU[0] is false in row 0
         const bool implied = lane > 0 && ((Ub[k] >> (lane - 1)) & 1u) && ((Lb[k] >> lane) & 1u) && ((Lup >> lane) & 1u);
         if (!implied) union_s(Ls, run[k], (r - 1) * kCclTile + (31 - __clz(~Lup & upto)), g.err);
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kRows; k++) {
-        const int r = threadIdx.y + 8 * k;
+        const int r = kRows * w + k;
         const int x = x0 + lane, y = y0 + r;
         if (x >= g.W || y >= g.H) continue;
         int out = -1;
-        if (Ds[r * kCclTile + lane] > 0) {
+        if (D[k] > 0) {
             const int root = find_s(Ls, run[k]);
             out = (y0 + root / kCclTile) * g.W + x0 + (root % kCclTile);
         }
@@ -224,33 +233,32 @@ __global__ void __launch_bounds__(kCclTile * 8)
 }
 
 // Pass 2: join components across tile borders (global atomicMin union).
-// Tiles are tw x th pixels; thread t handles one 4-neighbour pair that
-// straddles a vertical (x = k tw) or horizontal (y = k th) tile border.  The
-// 32 pairs of a warp lie along one border: of the pairs with an edge that
-// join the same two labels only the first unites them.
+// Tiles are tw x th pixels.  Row b of the grid takes the vertical border
+// x = (b + 1) tw for b < nbx - 1, else the horizontal border
+// y = (b - nbx + 2) th; thread s of the row takes the border's 4-neighbour
+// pair at row (column) s.  The 32 pairs of a warp lie along one border: of
+// the pairs with an edge that join the same two labels only the first
+// unites them.
 template <int IN>
 __global__ void __launch_bounds__(256)
     k_ccl_merge(const Geo g, const char* __restrict__ disp, size_t dp, int* labels, size_t lpe,
-                int nbx, int nby, int tw, int th) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long nV = (long long)(nbx - 1) * g.H;
+                int nbx, int tw, int th) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    const bool vertical = b < nbx - 1;
+    const int len = vertical ? g.H : g.W;
+    if ((int)(blockIdx.x * blockDim.x) >= len) return;  // the whole block lies past the border's end
     const int lane = threadIdx.x & 31;
-    bool act = false;
-    int px = 0, py = 0, qx = 0, qy = 0;
-    if (t < nV) {
-        const int k = (int)(t / g.H) + 1;
-        py = qy = (int)(t - (long long)(k - 1) * g.H);
-        qx = k * tw;
+    int px, py, qx, qy;
+    if (vertical) {
+        qx = (b + 1) * tw;
         px = qx - 1;
-        act = true;
-    } else if (t - nV < (long long)(nby - 1) * g.W) {
-        const long long t2 = t - nV;
-        const int k = (int)(t2 / g.W) + 1;
-        px = qx = (int)(t2 - (long long)(k - 1) * g.W);
-        qy = k * th;
+        py = qy = s;
+    } else {
+        qy = (b - nbx + 2) * th;
         py = qy - 1;
-        act = true;
+        px = qx = s;
     }
+    bool act = s < len;
     int lp = 0, lq = 0;
     unsigned long long key = ~0ull - (unsigned)lane;  // unique for lanes without an edge
     if (act) {
@@ -265,7 +273,7 @@ __global__ void __launch_bounds__(256)
     }
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     if (act && lp != lq && (int)(__ffs(peers) - 1) == lane) {
-        const LabelIndex li{g.W, lpe};
+        const LabelIndex li{g.W, g.w_rcp, lpe};
         union_g(labels, li, lp, lq, g.err, g.walk_limit);
     }
 }
@@ -286,7 +294,7 @@ __global__ void __launch_bounds__(kTW * kTH / kFlatPix)
         const int y = y0 + i * kStep;
         l[i] = (x < g.W && y < g.H) ? __ldcg(labels + (size_t)y * lpe + x) : -1;
     }
-    const LabelIndex li{g.W, lpe};
+    const LabelIndex li{g.W, g.w_rcp, lpe};
     int roots = 0, prev_l = -1, prev_r = -1;
 #pragma unroll
     for (int i = 0; i < kFlatPix; i++) {
@@ -370,16 +378,17 @@ cudaError_t launch_ccl_merge_flatten(const Geo& g, const void* disp, size_t dp, 
     const int nbx = (g.W + tw - 1) / tw, nby = (g.H + th - 1) / th;
     const size_t lpe = lp / sizeof(int32_t);
     const char* d = static_cast<const char*>(disp);
-    const long long pairs = (long long)(nbx - 1) * g.H + (long long)(nby - 1) * g.W;
-    const unsigned mblocks = (unsigned)((pairs + 255) / 256);
-    if (pairs > 0) {
+    const int borders = (nbx - 1) + (nby - 1);
+    const int longest = g.W > g.H ? g.W : g.H;
+    const dim3 mg((unsigned)((longest + 255) / 256), (unsigned)borders);
+    if (borders > 0) {
         switch (g.in_dtype) {
-            case SN_IN_F32: k_ccl_merge<SN_IN_F32><<<mblocks, 256, 0, s>>>(g, d, dp, labels, lpe, nbx, nby, tw, th); break;
-            case SN_IN_F16: k_ccl_merge<SN_IN_F16><<<mblocks, 256, 0, s>>>(g, d, dp, labels, lpe, nbx, nby, tw, th); break;
-            default: k_ccl_merge<SN_IN_U16X256><<<mblocks, 256, 0, s>>>(g, d, dp, labels, lpe, nbx, nby, tw, th); break;
+            case SN_IN_F32: k_ccl_merge<SN_IN_F32><<<mg, 256, 0, s>>>(g, d, dp, labels, lpe, nbx, tw, th); break;
+            case SN_IN_F16: k_ccl_merge<SN_IN_F16><<<mg, 256, 0, s>>>(g, d, dp, labels, lpe, nbx, tw, th); break;
+            default: k_ccl_merge<SN_IN_U16X256><<<mg, 256, 0, s>>>(g, d, dp, labels, lpe, nbx, tw, th); break;
         }
     }
-    mk.after(s, pairs > 0);
+    mk.after(s, borders > 0);
     k_ccl_flatten<<<grid2(g), dim3(kTW, kTH / kFlatPix), 0, s>>>(g, labels, lpe, count);
     mk.after(s);
     return cudaGetLastError();
