@@ -374,11 +374,18 @@ __device__ __forceinline__ void gate_feature(const float* __restrict__ tab, int 
 // Parent arrays hold row-major pixel indices; parent[i] <= i always, so a
 // root is the smallest index of its tree.
 
-__device__ __forceinline__ int find_s(volatile int* L, int x) {
+// Root of x in a shared-memory parent array, with path halving: every node
+// passed is re-pointed at its grandparent, an ancestor, so concurrent unions
+// and finds stay correct (a parent only ever decreases towards the root).
+// A tile holds 1024 entries, so no walk is longer than the loop's bound.
+__device__ __forceinline__ int find_s_halve(volatile int* L, int x) {
     for (int it = 0; it < 4096; it++) {
         const int p = L[x];
         if (p == x) return x;
-        x = p;
+        const int gp = L[p];
+        if (gp == p) return p;
+        L[x] = gp;
+        x = gp;
     }
     return x;
 }
@@ -387,8 +394,8 @@ __device__ __forceinline__ int find_s(volatile int* L, int x) {
 // below the smaller one with atomicMin and retry on interference
 __device__ __forceinline__ void union_s(int* L, int a, int b, int* err) {
     for (int it = 0; it < kUnionLimit; it++) {
-        a = find_s(L, a);
-        b = find_s(L, b);
+        a = find_s_halve(L, a);
+        b = find_s_halve(L, b);
         if (a == b) return;
         if (a < b) {
             const int t = a;

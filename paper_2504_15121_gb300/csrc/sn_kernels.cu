@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kCclTile * 8)
         if (x >= g.W || y >= g.H) continue;
         int out = -1;
         if (D[k] > 0) {
-            const int root = find_s(Ls, run[k]);
+            const int root = find_s_halve(Ls, run[k]);
             out = (y0 + root / kCclTile) * g.W + x0 + (root % kCclTile);
         }
         labels[(size_t)y * lpe + x] = out;
