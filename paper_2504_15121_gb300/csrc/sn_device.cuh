@@ -262,20 +262,40 @@ __device__ __forceinline__ float i64_to_f32(long long x) {
 
 // FP64 solve for supports that trip the conditioning flag (rare; FP64 is a
 // slow pipe on this GPU, so nothing of it runs on the common path).
-static __device__ __noinline__ void solve_normal_f64(long long nu_i, long long nv_i, long long cu, long long cv,
-                                              long long det, int Dc, double dcd, int x, int y, const Geo& g,
-                                              float n[3]) {
+__device__ __forceinline__ float3 normal_f64(long long nu_i, long long nv_i, long long cu, long long cv, long long det,
+                                             int Dc, double dcd, int x, int y, double fx, double fy, double cx,
+                                             double cy) {
     const double dd = ((double)Dc + dcd) * (1.0 / 256.0);
     const double inv = 1.0 / (256.0 * (double)det);
     const double gu = ((double)nu_i - dcd * (double)cu) * inv;
     const double gv = ((double)nv_i - dcd * (double)cv) * inv;
     const double mx = gu;
-    const double my = gv * g.dfy / g.dfx;
-    const double mz = (dd - gu * ((double)x - g.dcx) - gv * ((double)y - g.dcy)) / g.dfx;
+    const double my = gv * fy / fx;
+    const double mz = (dd - gu * ((double)x - cx) - gv * ((double)y - cy)) / fx;
     const double r = 1.0 / sqrt(mx * mx + my * my + mz * mz);
-    n[0] = (float)(-mx * r);
-    n[1] = (float)(-my * r);
-    n[2] = (float)(-mz * r);
+    return make_float3((float)(-mx * r), (float)(-my * r), (float)(-mz * r));
+}
+
+// How a kernel reaches normal_f64.  Which form lets the compiler schedule
+// the common path best differs by kernel and was measured: out of line with
+// the constants by reference and the normal through a pointer (the plain
+// frame and stage kernels), out of line by value (the window kernel, the
+// learned chain's certified pixels), inline (the learned chain's star walk).
+enum F64Call { kF64ByRef, kF64ByValue, kF64Inline };
+
+static __device__ __noinline__ void normal_f64_ref(long long nu_i, long long nv_i, long long cu, long long cv,
+                                                   long long det, int Dc, double dcd, int x, int y, const Geo& g,
+                                                   float n[3]) {
+    const float3 v = normal_f64(nu_i, nv_i, cu, cv, det, Dc, dcd, x, y, g.dfx, g.dfy, g.dcx, g.dcy);
+    n[0] = v.x;
+    n[1] = v.y;
+    n[2] = v.z;
+}
+
+static __device__ __noinline__ float3 normal_f64_val(long long nu_i, long long nv_i, long long cu, long long cv,
+                                                     long long det, int Dc, double dcd, int x, int y, double fx,
+                                                     double fy, double cx, double cy) {
+    return normal_f64(nu_i, nv_i, cu, cv, det, Dc, dcd, x, y, fx, fy, cx, cy);
 }
 
 // Solves the 2x2 system of pass 2 and turns (g_u, g_v) into the
@@ -288,7 +308,7 @@ static __device__ __noinline__ void solve_normal_f64(long long nu_i, long long n
 // |Su|, |Sv| <= 222, Suu, Svv <= 1330 and |Suv| <= 560: det <= 1,768,900,
 // 1024 det, alpha gamma and the first-moment cofactors fit in 32 bits (the
 // data cofactors nu, nv still need 64).
-template <bool STAR8 = false, class AnchorF64>
+template <bool STAR8 = false, int F64 = kF64ByValue, class AnchorF64>
 __device__ __forceinline__ bool solve_normal_dc(const AffSums& s, int Dc, float dcf, AnchorF64 anchor_f64,
                                                 float dtil, int x, int y, const Geo& g, float n[3],
                                                 bool& fp64) {
@@ -326,7 +346,17 @@ __device__ __forceinline__ bool solve_normal_dc(const AffSums& s, int Dc, float 
         fcv = i64_to_f32(cv);
     }
     if (fp64) {
-        solve_normal_f64(nu_i, nv_i, cu, cv, det, Dc, anchor_f64(), x, y, g, n);
+        if constexpr (F64 == kF64ByRef) {
+            normal_f64_ref(nu_i, nv_i, cu, cv, det, Dc, anchor_f64(), x, y, g, n);
+        } else {
+            const float3 v =
+                F64 == kF64ByValue
+                    ? normal_f64_val(nu_i, nv_i, cu, cv, det, Dc, anchor_f64(), x, y, g.dfx, g.dfy, g.dcx, g.dcy)
+                    : normal_f64(nu_i, nv_i, cu, cv, det, Dc, anchor_f64(), x, y, g.dfx, g.dfy, g.dcx, g.dcy);
+            n[0] = v.x;
+            n[1] = v.y;
+            n[2] = v.z;
+        }
         return true;
     }
     {
@@ -349,7 +379,7 @@ template <bool STAR8 = false>
 __device__ __forceinline__ bool solve_normal(const AffSums& s, int Dc, float dtil, int x, int y,
                                              const Geo& g, float n[3], bool& fp64) {
     const float dcf = dtil * 256.0f - (float)Dc;
-    return solve_normal_dc<STAR8>(
+    return solve_normal_dc<STAR8, kF64ByRef>(
         s, Dc, dcf, [=] { return (double)dtil * 256.0 - (double)Dc; }, dtil, x, y, g, n, fp64);
 }
 

@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int p = list[i];
         const int px = p % kTW, py = p / kTW;
         PixOut r;
-        plain_pixel<2, kLR, 2>(g, nullptr, tile + (py + kLR) * kLTWR + px + kLR, kLTWR, x0 + px, y0 + py, r);
+        plain_pixel<2, kLR, 2, kF64Inline>(g, nullptr, tile + (py + kLR) * kLTWR + px + kLR, kLTWR, x0 + px, y0 + py, r);
         emit(g, o, x0 + px, y0 + py, r);
     }
 }

@@ -61,7 +61,7 @@ __device__ __forceinline__ Thr make_thr(const Geo& g, int Dc) {
 
 // Exact decision from the two extreme reciprocals: w is within 1 ulp of 1/D
 // and D < 2^17, so rint(1/w) recovers D exactly.
-__device__ __noinline__ bool cd_stop_from_w(float wlo, float whi, int Dc, int K) {
+__device__ __forceinline__ bool cd_stop_from_w(float wlo, float whi, int Dc, int K) {
     const int Dmax = __float2int_rn(rcp_approx(wlo));
     const int Dmin = __float2int_rn(rcp_approx(whi));
     return cd_stop(Dmin, Dmax, Dc, K);
@@ -100,9 +100,12 @@ __device__ __noinline__ void ray8_exact_tail(const int2* __restrict__ c, int Dc,
 // after the walk they give the spread of that step.  Only if it lies inside
 // the rounding band does the exact test decide (and possibly continue the
 // ray).  The data enters as A = sum t D over the included pixels; the
-// moments of the included prefix 1..n are closed forms.
-template <int SU, int SV, int L, int STRIDE>
-__device__ __forceinline__ void ray8(const int2* __restrict__ c, int Dc, float wc, const Thr& th, AffSums& s) {
+// moments of the included prefix 1..n are closed forms.  With TAIL false a
+// ray that would need the exact test only raises `unsure` (the caller then
+// walks the star again with TAIL true).
+template <int SU, int SV, int L, int STRIDE, bool TAIL>
+__device__ __forceinline__ void ray8(const int2* __restrict__ c, int Dc, float wc, const Thr& th, AffSums& s,
+                                     bool& unsure) {
     int2 e[L];
 #pragma unroll
     for (int t = 1; t <= L; t++) e[t - 1] = c[(SV * t) * STRIDE + SU * t];
@@ -122,7 +125,11 @@ __device__ __forceinline__ void ray8(const int2* __restrict__ c, int Dc, float w
             n++;
         }
     }
-    if (n < L && !(whi - wlo > th.hi)) ray8_exact_tail<SU, SV, L, STRIDE>(c, Dc, th.K, &n, &A);
+    if constexpr (TAIL) {
+        if (n < L && !(whi - wlo > th.hi)) ray8_exact_tail<SU, SV, L, STRIDE>(c, Dc, th.K, &n, &A);
+    } else {
+        unsure |= n < L && !(whi - wlo > th.hi);
+    }
     const int T1 = (n * (n + 1)) >> 1;
     const int T2 = (n * (n + 1) * (2 * n + 1)) / 6;
     const int Ad = A - Dc * T1;
@@ -140,18 +147,34 @@ __device__ __forceinline__ void ray8(const int2* __restrict__ c, int Dc, float w
     if (SU != 0 && SV != 0) s.Suv += SU * SV * T2;
 }
 
+template <int S, int STRIDE, bool TAIL>
+__device__ __forceinline__ bool star8_rays(const int2* c, int Dc, float wc, const Thr& th, AffSums& s) {
+    constexpr int LD = diag_len(S);
+    bool unsure = false;
+    aff_zero(s);
+    ray8<1, 0, S, STRIDE, TAIL>(c, Dc, wc, th, s, unsure);
+    ray8<1, 1, LD, STRIDE, TAIL>(c, Dc, wc, th, s, unsure);
+    ray8<0, 1, S, STRIDE, TAIL>(c, Dc, wc, th, s, unsure);
+    ray8<-1, 1, LD, STRIDE, TAIL>(c, Dc, wc, th, s, unsure);
+    ray8<-1, 0, S, STRIDE, TAIL>(c, Dc, wc, th, s, unsure);
+    ray8<-1, -1, LD, STRIDE, TAIL>(c, Dc, wc, th, s, unsure);
+    ray8<0, -1, S, STRIDE, TAIL>(c, Dc, wc, th, s, unsure);
+    ray8<1, -1, LD, STRIDE, TAIL>(c, Dc, wc, th, s, unsure);
+    return unsure;
+}
+
+// The star again with the exact tails (a spread inside the rounding band:
+// rare), out of line so that the common walk has no call in it.
+template <int S, int STRIDE>
+__device__ __noinline__ AffSums star8_exact(const int2* c, int Dc, float wc, Thr th) {
+    AffSums s;
+    star8_rays<S, STRIDE, true>(c, Dc, wc, th, s);
+    return s;
+}
+
 template <int S, int STRIDE>
 __device__ __forceinline__ void star8(const int2* c, int Dc, float wc, const Thr& th, AffSums& s) {
-    constexpr int LD = diag_len(S);
-    aff_zero(s);
-    ray8<1, 0, S, STRIDE>(c, Dc, wc, th, s);
-    ray8<1, 1, LD, STRIDE>(c, Dc, wc, th, s);
-    ray8<0, 1, S, STRIDE>(c, Dc, wc, th, s);
-    ray8<-1, 1, LD, STRIDE>(c, Dc, wc, th, s);
-    ray8<-1, 0, S, STRIDE>(c, Dc, wc, th, s);
-    ray8<-1, -1, LD, STRIDE>(c, Dc, wc, th, s);
-    ray8<0, -1, S, STRIDE>(c, Dc, wc, th, s);
-    ray8<1, -1, LD, STRIDE>(c, Dc, wc, th, s);
+    if (star8_rays<S, STRIDE, false>(c, Dc, wc, th, s)) s = star8_exact<S, STRIDE>(c, Dc, wc, th);
 }
 
 // Any star table (union of rays, see StarTable), on the packed tile.  With
@@ -396,7 +419,8 @@ __device__ __forceinline__ void emit(const Geo& g, const FrameOut& o, int x, int
 // The plain per-pixel chain: range-gated denoise, support (fixed window or
 // star-fill), two-pass fit, normal, point.  c points at the pixel in the tile;
 // T (the star table) is read only by the table-driven variants 1 and 4.
-template <int VAR, int R, int RD>
+// F64: how the rare FP64 solve is reached (F64Call).
+template <int VAR, int R, int RD, int F64 = kF64ByRef>
 __device__ __forceinline__ void plain_pixel(const Geo& g, const StarTable* T, const int2* c, int TWR, int x, int y,
                                             PixOut& r, const uint8_t* ec = nullptr) {
     pix_zero(r);
@@ -434,7 +458,7 @@ __device__ __forceinline__ void plain_pixel(const Geo& g, const StarTable* T, co
         fixed_packed(c, TWR, g.r_a, Dc, s);
     }
     bool fp64;
-    if (solve_normal_dc<VAR == 2 || VAR == 5>(
+    if (solve_normal_dc<VAR == 2 || VAR == 5, F64>(
             s, Dc, dcf, [=] { return fit ? (double)num / (double)det : 0.0; }, r.dtil, x, y, g, r.n, fp64))
         r.m |= SN_MASK_NORMAL | (fp64 ? SN_MASK_FP64 : 0);
     pix_points(g, x, y, r);
