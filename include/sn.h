@@ -267,6 +267,16 @@ sn_status sn_gate_q(sn_ctx *ctx, const void *disp, size_t disp_pitch, float *q, 
  * SN_EINVAL for a NULL pointer or n < 131072, SN_ECUDA on a CUDA error. */
 sn_status sn_gate_log2_table(float *out, int n);
 
+/* The FP32 reciprocal 1/D of every disparity code D = 0..131071 as the
+ * kernels compute it (the 1/D of the (D, 1/D) tiles that the covered-depth
+ * stop of Sec. III-D reads, and the depths F / D of the ST edge test: PTX
+ * rcp.approx; +inf for D = 0, the invalid code), copied to HOST memory `out`
+ * (n >= 131072 floats), so that tests can check the error bound the
+ * kernels' exact-decision bands assume.  A one-time kernel and a
+ * synchronisation on the current device.  SN_EINVAL for a NULL pointer or
+ * n < 131072, SN_ECUDA on a CUDA error. */
+sn_status sn_rcp_table(float *out, int n);
+
 /* sn_run_frame on HOST buffers: copies the disparity (in->disp, host) to
  * the device, runs sn_run_frame, and copies normals, points, labels, mask
  * and, if out->num_components is not NULL, the component count (host

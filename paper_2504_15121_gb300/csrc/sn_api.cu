@@ -283,6 +283,11 @@ const char* sn_status_string(sn_status s) {
 
 const char* sn_last_error(const sn_ctx* c) { return c ? c->msg : "null context"; }
 
+sn_status sn_rcp_table(float* out, int n) {
+    if (!out || n < sn::kDMax + 1) return SN_EINVAL;
+    return sn::rcp_codes(out) == cudaSuccess ? SN_OK : SN_ECUDA;
+}
+
 int sn_star_offsets(int dirs, int steps, int8_t* ou, int8_t* ov) {
     if (dirs < 1 || dirs > sn::kMaxDirs || steps < 1 || steps > sn::kMaxSteps || !ou || !ov) return -1;
     star_offsets(dirs, steps, ou, ov);

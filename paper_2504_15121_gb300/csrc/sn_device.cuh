@@ -197,16 +197,19 @@ __device__ __forceinline__ void star_support(const int* c, int TWR, int Dc, int 
 // and its 4-neighbours' codes: an invalid neighbour makes an edge; otherwise
 // the pixel is an edge iff |((z_l + z_r) + (z_u + z_d)) - 4 z_c| > t with
 // z = F / D, F = 256 fx B, as evaluated in FP64 in exactly that order.  The
-// FP32 evaluation (each z within 2^-23 relative, each sum one rounding)
-// differs from that value by less than 2^-21.4 S, S the sum of the terms'
-// magnitudes, and |L| - t rounds within 2^-24 (S + t); outside the band
-// 2^-19 (S + t) it decides, inside the FP64 expression does (IEEE
-// round-to-nearest operations, no contraction).
+// FP32 evaluation takes z = F rcp(D) with F rounded to FP32 and the 1-ulp
+// reciprocal (2^-23 relative at every code, checked by the tests), so each z
+// lies within about 2^-22 of F / D relatively; with one rounding per sum
+// (4 z_c is exact) the FP32 L differs from the exact value by less than
+// 7 2^-24 S, S the sum of the terms' magnitudes, and |L| - t rounds within
+// 2^-24 (S + t): together below 2^-21 (S + t).  Outside the band
+// 2^-19 (S + t) the FP32 value decides, inside it the FP64 expression does
+// (IEEE round-to-nearest operations, no contraction).
 __device__ __forceinline__ bool st_edge(const Geo& g, int Dc, int Dl, int Dr, int Du, int Dd) {
     if (Dc <= 0 || Dl <= 0 || Dr <= 0 || Du <= 0 || Dd <= 0) return true;
     const float F = g.st_Ff;
-    const float zc = F * __frcp_rn((float)Dc), zl = F * __frcp_rn((float)Dl), zr = F * __frcp_rn((float)Dr);
-    const float zu = F * __frcp_rn((float)Du), zd = F * __frcp_rn((float)Dd);
+    const float zc = F * rcp_approx((float)Dc), zl = F * rcp_approx((float)Dl), zr = F * rcp_approx((float)Dr);
+    const float zu = F * rcp_approx((float)Du), zd = F * rcp_approx((float)Dd);
     const float S = zl + zr + zu + zd + 4.0f * zc;
     const float L = ((zl + zr) + (zu + zd)) - 4.0f * zc;
     const float dev = fabsf(L) - g.st_tf;

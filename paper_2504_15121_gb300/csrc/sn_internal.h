@@ -93,6 +93,10 @@ void cd_band(int K, float* hi, float* lo);
 // 2^64), 0 for W < 2.
 inline unsigned long long w_reciprocal(int W) { return W < 2 ? 0ull : ~0ull / (unsigned long long)W + 1ull; }
 
+// The FP32 reciprocal of every code 0..kDMax as the kernels compute it,
+// copied to host memory (kDMax + 1 floats).
+cudaError_t rcp_codes(float* host_out);
+
 // Checks camera, size and parameters and fills the kernel constants without
 // touching the device.
 sn_status prepare_constants(const sn_camera* cam, int W, int H, const sn_params* p, Geo* g, StarTable* t);

@@ -309,6 +309,30 @@ __global__ void __launch_bounds__(kTW * kTH / kFlatPix)
     if (count && roots) atomicAdd(count, roots);
 }
 
+// ---------------------------------------------------------------- the reciprocal of every code
+// rcp_approx of D = 1..kDMax as the kernels stage it (+inf for the invalid
+// code 0), for the tests that check its error bound.
+__global__ void k_rcp_codes(float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= kDMax) out[i] = i == 0 ? __int_as_float(0x7f800000) : rcp_approx((float)i);
+}
+
+cudaError_t rcp_codes(float* host_out) {
+    float* d = nullptr;
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&d, sizeof(float) * (kDMax + 1));
+    if (e == cudaSuccess) {
+        k_rcp_codes<<<(kDMax + 1 + 255) / 256, 256, 0, st>>>(d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, d, sizeof(float) * (kDMax + 1), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (d) cudaFree(d);
+    if (st) cudaStreamDestroy(st);
+    return e;
+}
+
 // ---------------------------------------------------------------- launchers
 static dim3 grid2(const Geo& g) { return dim3((g.W + kTW - 1) / kTW, (g.H + kTH - 1) / kTH); }
 

@@ -96,6 +96,7 @@ def _load():
         "sn_noalloc_check_device": ([vp], i),
         "sn_gate_q": ([vp, vp, sz, vp, sz, vp], i),
         "sn_gate_log2_table": ([vp, i], i),
+        "sn_rcp_table": ([vp, i], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -112,7 +113,8 @@ EXPORTS = ("sn_version", "sn_default_params", "sn_create", "sn_destroy", "sn_den
            "sn_load_gate_weights", "sn_star_offsets", "sn_check_device", "sn_status_string",
            "sn_last_error", "sn_set_profiling", "sn_stage_count", "sn_stage_name",
            "sn_stage_times", "sn_launch_count", "sn_normals_noalloc", "sn_noalloc_check_device", "sn_cross_normals",
-           "sn_pca_normals", "sn_set_walk_limit", "sn_run_frame_host", "sn_gate_q", "sn_gate_log2_table")
+           "sn_pca_normals", "sn_set_walk_limit", "sn_run_frame_host", "sn_gate_q", "sn_gate_log2_table",
+           "sn_rcp_table")
 
 
 # ---------------------------------------------------------------- helpers
@@ -345,6 +347,14 @@ def sn_gate_log2_table():
     import numpy as np
     out = np.empty(131072, np.float32)
     _check(None, lib.sn_gate_log2_table(out.ctypes.data_as(C.c_void_p), out.size))
+    return out
+
+
+def sn_rcp_table():
+    """The kernels' FP32 reciprocal of every code (numpy float32 [131072], +inf at 0)."""
+    import numpy as np
+    out = np.empty(131072, np.float32)
+    _check(None, lib.sn_rcp_table(out.ctypes.data_as(C.c_void_p), out.size))
     return out
 
 

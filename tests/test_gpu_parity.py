@@ -203,6 +203,19 @@ def test_extreme_codes(P, kind, params):
     compare_frame(g, ref)
 
 
+def test_reciprocal_of_every_code_within_one_ulp(P):
+    # the covered-depth band and the ST edge band both assume that the
+    # kernels' FP32 1/D lies within 2^-23 of 1/D relatively, for every code
+    r = P.sn.sn_rcp_table()
+    assert np.isposinf(r[0])
+    D = np.arange(1, r.size, dtype=np.float64)
+    rel = np.abs(r[1:].astype(np.float64) * D - 1.0)  # r D is exact in FP64
+    ulps = np.abs(r[1:].astype(np.float64) - 1.0 / D) / np.spacing(r[1:]).astype(np.float64)
+    print(f"rcp over codes 1..131071: max relative error {rel.max():.3e} ({np.log2(rel.max()):.2f} in log2), "
+          f"max {ulps.max():.3f} ulp")
+    assert rel.max() <= 2.0 ** -23
+
+
 def test_covered_depth_at_the_threshold(P):
     # k_cd = 0.1 (K = 6554): with Dc = Dmin = 29491 the stop test
     # (Dmax - Dmin) Dc 2^16 > K Dmin Dmax holds from Dmax = 32769 on and is an
