@@ -350,7 +350,13 @@ __device__ __forceinline__ bool solve_normal_dc(const AffSums& s, int Dc, float 
     }
     if (fp64) {
         if constexpr (F64 == kF64ByRef) {
-            normal_f64_ref(nu_i, nv_i, cu, cv, det, Dc, anchor_f64(), x, y, g, n);
+            // through a temporary, so that only the rare path addresses memory
+            // (handing n itself over kept the caller's normal in local memory)
+            float t[3];
+            normal_f64_ref(nu_i, nv_i, cu, cv, det, Dc, anchor_f64(), x, y, g, t);
+            n[0] = t[0];
+            n[1] = t[1];
+            n[2] = t[2];
         } else {
             const float3 v =
                 F64 == kF64ByValue

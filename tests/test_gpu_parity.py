@@ -129,9 +129,14 @@ def test_snorm16_output(P):
 
 
 # ------------------------------------------------------------ tiny and ragged
-@pytest.mark.parametrize("H,W", [(1, 1), (1, 7), (7, 1), (5, 7), (17, 33), (40, 65), (9, 129)])
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 7), (7, 1), (5, 7), (17, 33), (40, 65), (9, 129),
+                                 (70, 1), (300, 20), (20, 600)])
 @pytest.mark.parametrize("support", [1, 0, 2])
 def test_ragged_random(P, H, W, support):
+    # (70, 1), (300, 20): component tiles in one column, borders only
+    # between rows (a width of 1 takes the label addressing's own branch);
+    # (20, 600): borders only between columns, shorter than one block of the
+    # border merge, whose further blocks along the border exit at once
     rng = np.random.default_rng(H * 1000 + W)
     base = rng.integers(4000, 4400, (H, W))
     blocks = rng.integers(0, 3, (H // 3 + 1, W // 3 + 1)).repeat(3, 0).repeat(3, 1)[:H, :W]
