@@ -33,7 +33,10 @@
 //     packed FP32 dot product, the sigmoid;
 //   * output: the gate bit (minimum of q over the pixel's lattice points
 //     >= tau) as SN_MASK_LEARNED in the frame's mask buffer, or q (sn_gate_q).
-// k_learned (the chain; 32 x 16 tiles, two CTAs per SM) stages the tile and
+// k_learned (the chain; 32 x 16 tiles, 256 threads of two pixels each, four
+// CTAs per SM: short CTAs hide its barriers better than 512 threads at two
+// per SM, although the star walk of the uncertified pixels then spills a
+// few registers) stages the tile and
 // a halo of 10 by TMA as (D, 1/D), reads the gate bits, and fits certified
 // valid pixels on the full 13 x 13 affine and the un-gated 5 x 5 denoise
 // window: a row pass per entry (count + 2^16 sum u of the valid samples, sum
@@ -118,10 +121,13 @@ constexpr size_t kCOffTile = 0;
 constexpr size_t kCOffRS = align128z(sizeof(int2) * kTileN);
 constexpr size_t kCOffRS5 = kCOffRS + 16 * (size_t)kRS;
 constexpr size_t kCOffList = kCOffRS5 + 16 * (size_t)kRS;
-constexpr size_t kCOffCnt = kCOffList + sizeof(int) * kThreads;
+constexpr size_t kCOffCnt = kCOffList + sizeof(int) * kThreads;  // room for every pixel of the tile
 constexpr size_t kCSmem = align128z(kCOffCnt + 16);
 static_assert(tma_bw<SN_IN_F32, kLR, kLTWR>() * kLTHR * 4 + 8 <= 2 * 16 * kRS, "raw box inside the row sums");
-static_assert(2 * (kCSmem + 1024) <= 228 * 1024, "two chain CTAs per SM");
+// 32 x 8 threads, two pixels each (tile rows ty and ty + 8), four CTAs per SM
+constexpr int kCThreads = kTW * 8;
+static_assert(kTH == 16, "two pixel rows per thread");
+static_assert(4 * (kCSmem + 1024) <= 228 * 1024, "four chain CTAs per SM");
 
 // log2 of every code (FP32, correctly rounded from the FP64 value; NaN for
 // code 0, the invalid pixel), read by the features of the inference and the
@@ -480,7 +486,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 // ---------------------------------------------------------------- the chain kernel
 template <int IN>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kCThreads, 4)
     k_learned(const Geo g, const char* __restrict__ disp, size_t dp, const FrameOut o,
               const __grid_constant__ CUtensorMap dmap) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -489,26 +495,34 @@ __global__ void __launch_bounds__(kThreads, 2)
     int4* rs5 = reinterpret_cast<int4*>(smem + kCOffRS5);
     int* list = reinterpret_cast<int*>(smem + kCOffList);
     int* cnt = reinterpret_cast<int*>(smem + kCOffCnt);
-    const int lane = threadIdx.x, row = threadIdx.y;
-    const int tid = row * kTW + lane;
+    const int lane = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kTW + lane;
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
-    const int x = x0 + lane, y = y0 + row;
-    const bool inside = x < g.W && y < g.H;
-    // the gate bit the gate kernel left in the mask
-    const bool cand = inside && (o.mask[(size_t)y * o.mp + x] & SN_MASK_LEARNED);
+    const int x = x0 + lane;
+    // the gate bits the gate kernel left in the mask, for rows ty and ty + 8
+    // (bit k of cand: row ty + 8 k)
+    unsigned cand = 0u;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int y = y0 + ty + 8 * k;
+        if (x < g.W && y < g.H && (o.mask[(size_t)y * o.mp + x] & SN_MASK_LEARNED)) cand |= 1u << k;
+    }
     if (tid == 0) *cnt = 0;
-    stage_tile<IN, kLR, kTH, kThreads, false>(tile, smem + kCOffRS, &dmap, true, disp, dp, x0, y0, g, kStageRcp);
-    const int2* c = tile + (row + kLR) * kLTWR + lane + kLR;
-    const int Dc = c[0].x;  // 0 outside the image
-    const bool gated = cand && Dc > 0;
-    if (__syncthreads_or(gated)) {
+    stage_tile<IN, kLR, kTH, kCThreads, false>(tile, smem + kCOffRS, &dmap, true, disp, dp, x0, y0, g, kStageRcp);
+    // the centre codes (0 outside the image): gated = certified and valid
+    auto centre = [&](int k) { return tile[(ty + 8 * k + kLR) * kLTWR + lane + kLR].x; };
+    unsigned gated = 0u;
+#pragma unroll
+    for (int k = 0; k < 2; k++)
+        if ((cand >> k & 1u) && centre(k) > 0) gated |= 1u << k;
+    if (__syncthreads_or(gated != 0u)) {
         // ---- row pass: for every entry (tile rows -kFastR .. kTH - 1 + kFastR)
         // over |u| <= 2 and |u| <= kFastR: (count + 2^16 sum u) of the valid
         // samples, their sum u^2, the sums of D and of u D (D = 0 where invalid)
-#pragma unroll
-        for (int pass = 0; pass < (kRS + kThreads - 1) / kThreads; pass++) {
-            const int e = tid + pass * kThreads;
-            if (kRS % kThreads != 0 && e >= kRS) break;
+#pragma unroll 1
+        for (int pass = 0; pass < (kRS + kCThreads - 1) / kCThreads; pass++) {
+            const int e = tid + pass * kCThreads;
+            if (kRS % kCThreads != 0 && e >= kRS) break;
             const int2* p = tile + (e / kTW + kLR - kFastR) * kLTWR + e % kTW + kLR;
             int A = 0, B = 0, Q0 = 0, Q1 = 0;
 #pragma unroll
@@ -536,70 +550,78 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         __syncthreads();
     }
-    if (gated) {
-        // ---- column pass over 2 kFastR + 1 and 5 rows: with P = count +
-        // 2^16 sum u per row, sum P = n + 2^16 Su, sum v P = Sv + 2^16 Suv,
-        // sum v^2 P = Svv + 2^16 (sum v^2 u), each low field within 16 bits
-        int SA = 0, SAv = 0, SAv2 = 0, SB = 0, SQ1 = 0, SQ0v = 0;
+#pragma unroll 1
+    for (int k = 0; k < 2; k++) {
+        const int row = ty + 8 * k, y = y0 + row;
+        if (gated >> k & 1u) {
+            // ---- column pass over 2 kFastR + 1 and 5 rows: with P = count +
+            // 2^16 sum u per row, sum P = n + 2^16 Su, sum v P = Sv + 2^16 Suv,
+            // sum v^2 P = Svv + 2^16 (sum v^2 u), each low field within 16 bits
+            int SA = 0, SAv = 0, SAv2 = 0, SB = 0, SQ1 = 0, SQ0v = 0;
 #pragma unroll
-        for (int j = -kFastR; j <= kFastR; j++) {
-            const int4 a = rs[(row + kFastR + j) * kTW + lane];
-            SA += a.x;
-            SAv += j * a.x;
-            SAv2 += (j * j) * a.x;
-            SB += a.y;
-            SQ1 += a.w;
-            SQ0v += j * a.z;
-        }
-        int TA = 0, TAv = 0, TAv2 = 0, TB = 0, TQ0 = 0, TQ0v = 0, TQ1 = 0;
+            for (int j = -kFastR; j <= kFastR; j++) {
+                const int4 a = rs[(row + kFastR + j) * kTW + lane];
+                SA += a.x;
+                SAv += j * a.x;
+                SAv2 += (j * j) * a.x;
+                SB += a.y;
+                SQ1 += a.w;
+                SQ0v += j * a.z;
+            }
+            int TA = 0, TAv = 0, TAv2 = 0, TB = 0, TQ0 = 0, TQ0v = 0, TQ1 = 0;
 #pragma unroll
-        for (int j = -2; j <= 2; j++) {
-            const int4 a = rs5[(row + kFastR + j) * kTW + lane];
-            TA += a.x;
-            TAv += j * a.x;
-            TAv2 += (j * j) * a.x;
-            TB += a.y;
-            TQ0 += a.z;
-            TQ0v += j * a.z;
-            TQ1 += a.w;
+            for (int j = -2; j <= 2; j++) {
+                const int4 a = rs5[(row + kFastR + j) * kTW + lane];
+                TA += a.x;
+                TAv += j * a.x;
+                TAv2 += (j * j) * a.x;
+                TB += a.y;
+                TQ0 += a.z;
+                TQ0v += j * a.z;
+                TQ1 += a.w;
+            }
+            WinSums wa, w2;
+            wa.n = SA & 0xFFFF;
+            wa.Su = (SA - wa.n) >> 16;
+            wa.Sv = (int)(short)(SAv & 0xFFFF);
+            wa.Suv = (SAv - wa.Sv) >> 16;
+            wa.Svv = SAv2 & 0xFFFF;
+            wa.Suu = SB;
+            wa.SD = 0;  // not used by the affine fit
+            wa.SuD = SQ1;
+            wa.SvD = SQ0v;
+            w2.n = TA & 0xFFFF;
+            w2.Su = (TA - w2.n) >> 16;
+            w2.Sv = (int)(short)(TAv & 0xFFFF);
+            w2.Suv = (TAv - w2.Sv) >> 16;
+            w2.Svv = TAv2 & 0xFFFF;
+            w2.Suu = TB;
+            w2.SD = TQ0;
+            w2.SuD = TQ1;
+            w2.SvD = TQ0v;
+            PixOut r;
+            fast_pixel(g, centre(k), w2, wa, x, y, r);
+            emit(g, o, x, y, r);
+        } else if (x < g.W && y < g.H && centre(k) <= 0) {
+            PixOut r;
+            pix_zero(r);
+            emit(g, o, x, y, r);
         }
-        WinSums wa, w2;
-        wa.n = SA & 0xFFFF;
-        wa.Su = (SA - wa.n) >> 16;
-        wa.Sv = (int)(short)(SAv & 0xFFFF);
-        wa.Suv = (SAv - wa.Sv) >> 16;
-        wa.Svv = SAv2 & 0xFFFF;
-        wa.Suu = SB;
-        wa.SD = 0;  // not used by the affine fit
-        wa.SuD = SQ1;
-        wa.SvD = SQ0v;
-        w2.n = TA & 0xFFFF;
-        w2.Su = (TA - w2.n) >> 16;
-        w2.Sv = (int)(short)(TAv & 0xFFFF);
-        w2.Suv = (TAv - w2.Sv) >> 16;
-        w2.Svv = TAv2 & 0xFFFF;
-        w2.Suu = TB;
-        w2.SD = TQ0;
-        w2.SuD = TQ1;
-        w2.SvD = TQ0v;
-        PixOut r;
-        fast_pixel(g, Dc, w2, wa, x, y, r);
-        emit(g, o, x, y, r);
-    } else if (inside && Dc <= 0) {
-        PixOut r;
-        pix_zero(r);
-        emit(g, o, x, y, r);
     }
     // ---- the uncertified valid pixels, compacted so that whole warps walk star rays
-    const bool need = inside && Dc > 0 && !gated;
-    const unsigned m = __ballot_sync(0xffffffffu, need);
-    int base = 0;
-    if (lane == 0 && m) base = atomicAdd(cnt, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (need) list[base + __popc(m & ((1u << lane) - 1u))] = tid;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int y = y0 + ty + 8 * k;
+        const bool need = x < g.W && y < g.H && centre(k) > 0 && !(gated >> k & 1u);
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(cnt, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (need) list[base + __popc(m & ((1u << lane) - 1u))] = (ty + 8 * k) * kTW + lane;
+    }
     __syncthreads();
     const int nl = *cnt;
-    for (int i = tid; i < nl; i += kThreads) {
+    for (int i = tid; i < nl; i += kCThreads) {
         const int p = list[i];
         const int px = p % kTW, py = p / kTW;
         PixOut r;
@@ -643,7 +665,7 @@ cudaError_t launch_chain(const Geo& g, const void* disp, size_t dp, const FrameO
     static std::atomic<unsigned long long> done{0};
     const cudaError_t e = smem_limit_once(k_learned<IN>, kCSmem, done);
     if (e != cudaSuccess) return e;
-    const dim3 grid((g.W + kTW - 1) / kTW, (g.H + kTH - 1) / kTH), block(kTW, kTH);
+    const dim3 grid((g.W + kTW - 1) / kTW, (g.H + kTH - 1) / kTH), block(kTW, kCThreads / kTW);
     k_learned<IN><<<grid, block, kCSmem, s>>>(g, static_cast<const char*>(disp), dp, o, dmap);
     return cudaGetLastError();
 }
