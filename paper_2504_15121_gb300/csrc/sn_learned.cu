@@ -1,8 +1,8 @@
 // Learned form of the frame kernel (sn_run_frame on a learned context) and
 // the gate's probability map (sn_gate_q): two kernels.
 //
-// k_gate (the network; persistent, one CTA of 512 threads per SM, all 512
-// TMEM columns) walks its share of the frame's 32 x 16 pixel tiles in a
+// k_gate (the network; persistent, two CTAs of 512 threads per SM, 256 TMEM
+// columns each) walks its share of the frame's 32 x 16 pixel tiles in a
 // software pipeline over two buffers, so that the tensor cores, the TMA
 // copies and the CUDA-core phases of different tiles overlap:
 //   iteration i:  features of tile i                (CUDA cores)
