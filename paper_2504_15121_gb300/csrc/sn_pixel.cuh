@@ -130,8 +130,10 @@ __device__ __forceinline__ void ray8(const int2* __restrict__ c, int Dc, float w
     } else {
         unsure |= n < L && !(whi - wlo > th.hi);
     }
+    // T1 = sum t, T2 = sum t^2 over t = 1..n: T2 = T1 (2n + 1) / 3, an exact
+    // multiple of 3, divided by multiplying with the inverse of 3 modulo 2^32
     const int T1 = (n * (n + 1)) >> 1;
-    const int T2 = (n * (n + 1) * (2 * n + 1)) / 6;
+    const int T2 = (int)((unsigned)(T1 * (2 * n + 1)) * 0xAAAAAAABu);
     const int Ad = A - Dc * T1;
     s.N += n;
     if (SU != 0) {
@@ -305,18 +307,20 @@ __device__ __forceinline__ bool denoise_exact(const int2* c, int stride, int rd_
     int n = 0, Su = 0, Sv = 0, Suu = 0, Suv = 0, Svv = 0, b0 = 0, b1 = 0, b2 = 0;
     if constexpr (RD == 2) {
         // 5x5: record the passing samples in a bit mask and take the moments
-        // from population counts of column, row and product classes
+        // from population counts of column, row and product classes; the data
+        // sums collect D itself (sum D < 25 2^17) and drop Dc once at the end
         unsigned m = 0;
+        const int off = lo - Dc;  // D - Dc + lo = D + off
 #pragma unroll
         for (int ov = -2; ov <= 2; ov++) {
 #pragma unroll
             for (int ou = -2; ou <= 2; ou++) {
-                const int dd = c[ov * stride + ou].x - Dc;
-                if ((unsigned)(dd + lo) <= span) {
+                const int D = c[ov * stride + ou].x;
+                if ((unsigned)(D + off) <= span) {
                     m |= 1u << ((ov + 2) * 5 + (ou + 2));
-                    b0 += dd;
-                    b1 += ou * dd;
-                    b2 += ov * dd;
+                    b0 += D;
+                    b1 += ou * D;
+                    b2 += ov * D;
                 }
             }
         }
@@ -332,6 +336,9 @@ __device__ __forceinline__ bool denoise_exact(const int2* c, int stride, int rd_
         Suv = (popc_and(m, mask5(2, 1)) - popc_and(m, mask5(2, -1))) +
               2 * (popc_and(m, mask5(2, 2)) - popc_and(m, mask5(2, -2))) +
               4 * (popc_and(m, mask5(2, 4)) - popc_and(m, mask5(2, -4)));
+        b0 -= n * Dc;
+        b1 -= Su * Dc;
+        b2 -= Sv * Dc;
     } else {
 #pragma unroll
         for (int ov = -R; ov <= R; ov++) {
