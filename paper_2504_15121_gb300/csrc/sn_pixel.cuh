@@ -134,17 +134,18 @@ __device__ __forceinline__ void ray8(const int2* __restrict__ c, int Dc, float w
     // multiple of 3, divided by multiplying with the inverse of 3 modulo 2^32
     const int T1 = (n * (n + 1)) >> 1;
     const int T2 = (int)((unsigned)(T1 * (2 * n + 1)) * 0xAAAAAAABu);
-    const int Ad = A - Dc * T1;
+    // the data sums take A = sum t D itself; the star subtracts Dc times the
+    // first moments once, after its last ray
     s.N += n;
     if (SU != 0) {
         s.Su += SU * T1;
         s.Suu += T2;
-        s.Bu += SU * Ad;
+        s.Bu += SU * A;
     }
     if (SV != 0) {
         s.Sv += SV * T1;
         s.Svv += T2;
-        s.Bv += SV * Ad;
+        s.Bv += SV * A;
     }
     if (SU != 0 && SV != 0) s.Suv += SU * SV * T2;
 }
@@ -162,6 +163,9 @@ __device__ __forceinline__ bool star8_rays(const int2* c, int Dc, float wc, cons
     ray8<-1, -1, LD, STRIDE, TAIL>(c, Dc, wc, th, s, unsure);
     ray8<0, -1, S, STRIDE, TAIL>(c, Dc, wc, th, s, unsure);
     ray8<1, -1, LD, STRIDE, TAIL>(c, Dc, wc, th, s, unsure);
+    // sum u (D - Dc) = sum u D - Dc sum u (|sum u D| < 6 x 55 x 2^17 < 2^31)
+    s.Bu -= Dc * s.Su;
+    s.Bv -= Dc * s.Sv;
     return unsure;
 }
 
