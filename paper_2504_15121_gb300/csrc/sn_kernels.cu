@@ -120,29 +120,33 @@ __global__ void __launch_bounds__(kTW* kTH)
 }
 
 // ---------------------------------------------------------------- components
-// Pass 1: union-find inside each 32 x 32 tile (shared memory); every pixel
+// Tile-local tiles of kCclTile = 32 columns by kCclTH rows; each warp labels
+// kCclRows consecutive rows.
+constexpr int kCclTH = 64, kCclRows = 4, kCclWarps = kCclTH / kCclRows;
+static_assert(kCclTH % kCclRows == 0 && kCclTile * kCclTH <= 4096, "finds bounded by the tile size");
+// Pass 1: union-find inside each 32 x kCclTH tile (shared memory); every pixel
 // receives the global index of its tile-local root (the smallest index of
 // its tile-local component).
 template <int IN>
-__global__ void __launch_bounds__(kCclTile * 8)
+__global__ void __launch_bounds__(kCclTile * kCclWarps)
     k_ccl_local(const Geo g, const char* __restrict__ disp, size_t dp, int* __restrict__ labels,
                 size_t lpe, int* __restrict__ count, const __grid_constant__ CUtensorMap dmap, int use_tma) {
-    // Warp w labels rows 4 w .. 4 w + 3 of the 32 x 32 tile, lane = column,
+    // Warp w labels rows 4 w .. 4 w + 3 of the 32 x kCclTH tile, lane = column,
     // codes and pair thresholds in registers: the pixels joined to their left
     // neighbour form runs, labelled by the run's first lane (from a ballot of
     // left edges); then vertical edges join the runs of adjacent rows in a
     // shared-memory union-find (an edge implied by its left neighbour's is
     // skipped).  A warp's first row meets the row above through shared memory.
-    constexpr int kRows = kCclTile / 8;
-    __shared__ int Ls[kCclTile * kCclTile];
-    __shared__ int2 Last[8][kCclTile];  // (D, t) of each warp's last row
+    constexpr int kRows = kCclRows;
+    __shared__ int Ls[kCclTile * kCclTH];
+    __shared__ int2 Last[kCclWarps][kCclTile];  // (D, t) of each warp's last row
     __shared__ unsigned Lrow[8];         // left-edge ballot of each warp's last row
     // the tile's raw disparities by one TMA copy (zero outside the image;
     // the box starts on a 32-element column, a 16-byte boundary)
     constexpr int kES = IN == SN_IN_F32 ? 4 : 2;
-    __shared__ __align__(128) unsigned char raw[kCclTile * kCclTile * kES];
+    __shared__ __align__(128) unsigned char raw[kCclTile * kCclTH * kES];
     __shared__ uint64_t sbar;
-    const int x0 = blockIdx.x * kCclTile, y0 = blockIdx.y * kCclTile;
+    const int x0 = blockIdx.x * kCclTile, y0 = blockIdx.y * kCclTH;
     const int lane = threadIdx.x, w = threadIdx.y, tid = w * kCclTile + lane;
     if (count && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) *count = 0;
     const bool tma = use_tma && (umma::smem_addr(raw) & 127u) == 0;
@@ -420,12 +424,12 @@ cudaError_t launch_ccl_merge_flatten(const Geo& g, const void* disp, size_t dp, 
 
 cudaError_t launch_components(const Geo& g, const void* disp, size_t dp, int32_t* labels, size_t lp,
                               int32_t* count, cudaStream_t s, Marks& mk) {
-    const int nbx = (g.W + kCclTile - 1) / kCclTile, nby = (g.H + kCclTile - 1) / kCclTile;
+    const int nbx = (g.W + kCclTile - 1) / kCclTile, nby = (g.H + kCclTH - 1) / kCclTH;
     const size_t lpe = lp / sizeof(int32_t);
     const char* d = static_cast<const char*>(disp);
-    const dim3 lg(nbx, nby), lb(kCclTile, 8);
+    const dim3 lg(nbx, nby), lb(kCclTile, kCclWarps);
     CUtensorMap dmap{};
-    const int tma = encode_disp_map(&dmap, disp, dp, g.W, g.H, g.in_dtype, kCclTile, kCclTile) == cudaSuccess;
+    const int tma = encode_disp_map(&dmap, disp, dp, g.W, g.H, g.in_dtype, kCclTile, kCclTH) == cudaSuccess;
     switch (g.in_dtype) {
         case SN_IN_F32: k_ccl_local<SN_IN_F32><<<lg, lb, 0, s>>>(g, d, dp, labels, lpe, count, dmap, tma); break;
         case SN_IN_F16: k_ccl_local<SN_IN_F16><<<lg, lb, 0, s>>>(g, d, dp, labels, lpe, count, dmap, tma); break;
@@ -434,7 +438,7 @@ cudaError_t launch_components(const Geo& g, const void* disp, size_t dp, int32_t
     mk.after(s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_ccl_merge_flatten(g, disp, dp, labels, lp, count, kCclTile, kCclTile, s, mk);
+    return launch_ccl_merge_flatten(g, disp, dp, labels, lp, count, kCclTile, kCclTH, s, mk);
 }
 
 }  // namespace sn
