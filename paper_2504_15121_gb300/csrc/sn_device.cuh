@@ -281,9 +281,10 @@ __device__ __forceinline__ float3 normal_f64(long long nu_i, long long nv_i, lon
 
 // How a kernel reaches normal_f64.  Which form lets the compiler schedule
 // the common path best differs by kernel and was measured: out of line with
-// the constants by reference and the normal through a pointer (the plain
-// frame and stage kernels), out of line by value (the window kernel, the
-// learned chain's certified pixels), inline (the learned chain's star walk).
+// the constants by reference and the normal through a pointer to a
+// temporary (the plain frame and stage kernels), out of line by value (the
+// window kernel, the learned chain's certified pixels), inline (the learned
+// chain's star walk).
 enum F64Call { kF64ByRef, kF64ByValue, kF64Inline };
 
 static __device__ __noinline__ void normal_f64_ref(long long nu_i, long long nv_i, long long cu, long long cv,
@@ -416,7 +417,8 @@ __device__ __forceinline__ void gate_feature(const float* __restrict__ tab, int 
 // Root of x in a shared-memory parent array, with path halving: every node
 // passed is re-pointed at its grandparent, an ancestor, so concurrent unions
 // and finds stay correct (a parent only ever decreases towards the root).
-// A tile holds 1024 entries, so no walk is longer than the loop's bound.
+// A tile holds at most 4096 entries, so no walk is longer than the loop's
+// bound.
 __device__ __forceinline__ int find_s_halve(volatile int* L, int x) {
     for (int it = 0; it < 4096; it++) {
         const int p = L[x];

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kCclTile * kCclWarps)
     constexpr int kRows = kCclRows;
     __shared__ int Ls[kCclTile * kCclTH];
     __shared__ int2 Last[kCclWarps][kCclTile];  // (D, t) of each warp's last row
-    __shared__ unsigned Lrow[8];         // left-edge ballot of each warp's last row
+    __shared__ unsigned Lrow[kCclWarps];  // left-edge ballot of each warp's last row
     // the tile's raw disparities by one TMA copy (zero outside the image;
     // the box starts on a 32-element column, a 16-byte boundary)
     constexpr int kES = IN == SN_IN_F32 ? 4 : 2;
